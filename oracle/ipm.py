@@ -1,0 +1,198 @@
+"""Primal-dual interior-point method with PCG on the condensed KKT system.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Notation follows the paper: variables (beta, z, s1, s2, y1, y2, nu1, nu2) of the
+slack QP Eq. (slackproblem); at every iterate we keep y = nu (the KKT rows
+y_i - nu_i = 0 of Eq. (kkt) are linear, so a Newton step keeps them).
+
+Paper passages followed, in the order the method applies them
+-------------------------------------------------------------
+* Sec. 3.3, duality measure mu = (nu1^T s1 + nu2^T s2) / 2n.
+* Sec. 3.3, barrier system Eq. (kktmu): S_i V_i e = mu e replaces the
+  complementarity rows; we target sigma * mu (path following).
+* Sec. 3.4, Eq. (defsigma): Sigma_i = S_i^{-1} V_i.
+* Sec. 3.4, Eq. (condensedkkt): K = [[G + Lambda1, Lambda2], [Lambda2, Lambda1]],
+  Lambda1 = Sigma1 + Sigma2, Lambda2 = Sigma1 - Sigma2, G = M_perp^T M_perp.
+* Sec. 3.5: P = [[I + Lambda1, Lambda2], [Lambda2, Lambda1]], Eq. (defBD),
+  Prop. exprbd (D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2) and Eq. (invprecond1):
+  P^{-1} = [[Lambda1 D^{-1}, -Lambda2 D^{-1}], [-D^{-1} Lambda2, B^{-1}]],
+  B^{-1} = D^{-1} (I + Lambda1).
+* Sec. 3.5 / Sec. 5: conjugate gradients on K with preconditioner P.
+
+Our readings (the paper leaves them to MadNLP or prints them with typos)
+----------------------------------------------------------------------
+* Right-hand side.  The Newton system is derived from minus the residual
+  F(w) of Eq. (kktmu) with y = nu:
+      r_d  = G beta - c - nu1 + nu2        (c = M_perp^T b; row 1 of Eq. (kkt))
+      r_z  = lambda e - nu1 - nu2          (row 2)
+      r_p1 = z + beta - s1,  r_p2 = z - beta - s2     (rows 5, 6)
+      r_c1 = s1 nu1 - sigma mu,  r_c2 = s2 nu2 - sigma mu
+  Eliminating ds and dnu gives K [dbeta; dz] = [rho_b; rho_c] with
+      rho_b = -r_d - r_c1/s1 - Sigma1 r_p1 + r_c2/s2 + Sigma2 r_p2
+      rho_c = -r_z - r_c1/s1 - Sigma1 r_p1 - r_c2/s2 - Sigma2 r_p2
+  and back-substitution ds1 = dz + dbeta + r_p1, ds2 = dz - dbeta + r_p2,
+  dnu_i = -r_ci/s_i - Sigma_i ds_i.  The matrix is exactly the paper's K;
+  the paper's printed r_1 and r_6 carry sign typos, which we do not follow.
+* Start: beta = 0, z = zeta e with zeta = max(1, ||c||_inf), s1 = s2 = z,
+  nu1 = nu2 = lambda/2 e (feasible in every linear row except row 1).
+* Step: one common step alpha = min(1, tau * alpha_max) for all variables,
+  alpha_max the largest step keeping (s, nu) >= 0; tau = 0.995.  sigma = 0.1,
+  raised to 0.5 for the next iteration after a step alpha < 0.1.
+* Stop when the relative duality gap (``Problem.certificate``) is <= gap_tol.
+* PCG: x0 = 0, stop when sqrt(r^T z) <= cg_tol * sqrt(r0^T z0) (relative,
+  the default) or sqrt(r^T z) <= cg_tol (absolute, as the paper's 1e-12 rule),
+  or after max_cg iterations.
+"""
+
+import numpy as np
+
+
+# ---- the barrier diagonals and the preconditioner (Sec. 3.4-3.5) -------------------
+
+def sigmas(s1, nu1, s2, nu2):
+    """Sigma_1 = S_1^{-1} V_1 and Sigma_2 = S_2^{-1} V_2 (Eq. (defsigma))."""
+    return nu1 / s1, nu2 / s2
+
+
+def K_apply(G, Sig1, Sig2, p_beta, p_z):
+    """[G + Lambda1, Lambda2; Lambda2, Lambda1] [p_beta; p_z] (Eq. (condensedkkt))."""
+    L1, L2 = Sig1 + Sig2, Sig1 - Sig2
+    return G(p_beta) + L1 * p_beta + L2 * p_z, L2 * p_beta + L1 * p_z
+
+
+def P_apply(Sig1, Sig2, p_beta, p_z):
+    """P [p_beta; p_z] with P = [I + Lambda1, Lambda2; Lambda2, Lambda1]."""
+    L1, L2 = Sig1 + Sig2, Sig1 - Sig2
+    return p_beta + L1 * p_beta + L2 * p_z, L2 * p_beta + L1 * p_z
+
+
+def Pinv_apply(Sig1, Sig2, r_beta, r_z):
+    """P^{-1} [r_beta; r_z] by the closed form Eq. (invprecond1) with Prop. exprbd."""
+    L1, L2 = Sig1 + Sig2, Sig1 - Sig2
+    D = Sig1 + Sig2 + 4.0 * Sig1 * Sig2
+    Binv = (1.0 + L1) / D
+    return (L1 / D) * r_beta - (L2 / D) * r_z, -(L2 / D) * r_beta + Binv * r_z
+
+
+# ---- preconditioned conjugate gradients (Sec. 3.5) --------------------------------
+
+def pcg(apply_K, apply_Pinv, rhs, tol, max_iter, relative=True):
+    """Solve K x = rhs; vectors are pairs (beta-part, z-part).
+
+    Returns (x, iterations, final sqrt(r^T z)).
+    """
+    def dot(a, b):
+        return a[0] @ b[0] + a[1] @ b[1]
+
+    x = (np.zeros_like(rhs[0]), np.zeros_like(rhs[1]))
+    r = (rhs[0].copy(), rhs[1].copy())
+    zv = apply_Pinv(*r)
+    p = (zv[0].copy(), zv[1].copy())
+    rho = dot(r, zv)
+    stop = tol * np.sqrt(max(rho, 0.0)) if relative else tol
+    it = 0
+    while it < max_iter and np.sqrt(max(rho, 0.0)) > stop:
+        q = apply_K(*p)
+        alpha = rho / dot(p, q)
+        x = (x[0] + alpha * p[0], x[1] + alpha * p[1])
+        r = (r[0] - alpha * q[0], r[1] - alpha * q[1])
+        zv = apply_Pinv(*r)
+        rho_new = dot(r, zv)
+        p = (zv[0] + (rho_new / rho) * p[0], zv[1] + (rho_new / rho) * p[1])
+        rho = rho_new
+        it += 1
+    return x, it, np.sqrt(max(rho, 0.0))
+
+
+# ---- Newton system ------------------------------------------------------------------
+
+def residuals(prob, Gbeta, w, sigma):
+    """r_d, r_z, r_p1, r_p2, r_c1, r_c2 and mu at w = (beta, z, s1, s2, nu1, nu2)."""
+    beta, z, s1, s2, nu1, nu2 = w
+    mu = (nu1 @ s1 + nu2 @ s2) / (2 * prob.n)
+    r_d = Gbeta - prob.c - nu1 + nu2
+    r_z = prob.lam - nu1 - nu2
+    r_p1 = z + beta - s1
+    r_p2 = z - beta - s2
+    r_c1 = s1 * nu1 - sigma * mu
+    r_c2 = s2 * nu2 - sigma * mu
+    return (r_d, r_z, r_p1, r_p2, r_c1, r_c2), mu
+
+
+def condensed_rhs(res, w):
+    """[rho_b; rho_c] of the condensed system (module docstring)."""
+    r_d, r_z, r_p1, r_p2, r_c1, r_c2 = res
+    _, _, s1, s2, nu1, nu2 = w
+    Sig1, Sig2 = sigmas(s1, nu1, s2, nu2)
+    rho_b = -r_d - r_c1 / s1 - Sig1 * r_p1 + r_c2 / s2 + Sig2 * r_p2
+    rho_c = -r_z - r_c1 / s1 - Sig1 * r_p1 - r_c2 / s2 - Sig2 * r_p2
+    return rho_b, rho_c
+
+
+def back_substitute(res, w, dbeta, dz):
+    """ds1, ds2, dnu1, dnu2 from the eliminated rows."""
+    _, _, r_p1, r_p2, r_c1, r_c2 = res
+    _, _, s1, s2, nu1, nu2 = w
+    Sig1, Sig2 = sigmas(s1, nu1, s2, nu2)
+    ds1 = dz + dbeta + r_p1
+    ds2 = dz - dbeta + r_p2
+    dnu1 = -r_c1 / s1 - Sig1 * ds1
+    dnu2 = -r_c2 / s2 - Sig2 * ds2
+    return ds1, ds2, dnu1, dnu2
+
+
+def max_step(vals, dirs):
+    """Largest alpha in (0, inf] with vals + alpha * dirs >= 0 (inf if none binds)."""
+    amax = np.inf
+    for v, d in zip(vals, dirs):
+        neg = d < 0
+        if np.any(neg):
+            amax = min(amax, float(np.min(-v[neg] / d[neg])))
+    return amax
+
+
+def starting_point(prob):
+    """beta = 0, z = s1 = s2 = zeta e, nu1 = nu2 = lambda/2 e."""
+    n = prob.n
+    zeta = max(1.0, float(np.abs(prob.c).max()))
+    beta = np.zeros(n)
+    z = np.full(n, zeta)
+    nu = np.full(n, 0.5 * prob.lam)
+    return [beta, z, z.copy(), z.copy(), nu, nu.copy()]
+
+
+def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative=True,
+          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None):
+    """Run the IPM; returns a dict with the point, counts and the certificate."""
+    w = [np.array(v, dtype=np.float64, copy=True) for v in (w0 or starting_point(prob))]
+    sigma = sigma0
+    cg_counts = []
+    status = "maxiter"
+    for it in range(max_ipm + 1):
+        beta = w[0]
+        Gbeta = prob.G(beta)
+        P, D, gap = prob.certificate(beta)
+        if log is not None:
+            log.append(dict(it=it, primal=P, dual=D, gap=gap))
+        if gap <= gap_tol:
+            status = "converged"
+            break
+        if it == max_ipm:
+            break
+        res, mu = residuals(prob, Gbeta, w, sigma)
+        Sig1, Sig2 = sigmas(w[2], w[4], w[3], w[5])
+        rhs = condensed_rhs(res, w)
+        (dbeta, dz), ncg, _ = pcg(lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b),
+                                  lambda a, b: Pinv_apply(Sig1, Sig2, a, b),
+                                  rhs, cg_tol, max_cg, cg_relative)
+        cg_counts.append(ncg)
+        ds1, ds2, dnu1, dnu2 = back_substitute(res, w, dbeta, dz)
+        amax = max_step(w[2:], (ds1, ds2, dnu1, dnu2))
+        alpha = min(1.0, tau * amax)
+        for v, d in zip(w, (dbeta, dz, ds1, ds2, dnu1, dnu2)):
+            v += alpha * d
+        sigma = sigma_slow if alpha < 0.1 else sigma0
+    P, D, gap = prob.certificate(w[0])
+    return dict(status=status, point=w, beta=w[0], primal=P, dual=D, gap=gap,
+                ipm_iters=len(cg_counts), cg_counts=cg_counts)

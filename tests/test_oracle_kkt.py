@@ -1,0 +1,190 @@
+"""Pins for the oracle's masked operators, KKT algebra and Newton step (no GPU).
+
+The references are dense matrices and numpy.linalg routines on tiny grids, the
+identities the paper proves (Prop. exprbd, Eq. (invprecond1), Eq. (precond1)),
+and a finite-difference Jacobian of the barrier system Eq. (kktmu), which pins
+the residuals, the condensed right-hand side and the back-substitution.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import ipm
+from oracle.lasso import Problem
+
+SMALL = [(8,), (12,), (4, 6), (4, 4, 4), (2, 4, 6)]
+
+
+def _problem(dims, seed=0, missing=0.3, lam=0.1):
+    rng = np.random.default_rng(seed)
+    n = int(np.prod(dims))
+    mask = np.ones(n, bool)
+    mask[rng.choice(n, size=max(1, int(missing * n)), replace=False)] = False
+    return Problem(dims, mask.reshape(dims), rng.standard_normal(dims), lam)
+
+
+def _dense(op, n):
+    return np.stack([np.ravel(op(e)) for e in np.eye(n)], axis=1)
+
+
+def _interior_point(n, rng):
+    s1, s2 = rng.uniform(0.1, 2.0, n), rng.uniform(0.1, 2.0, n)
+    nu1, nu2 = rng.uniform(0.1, 2.0, n), rng.uniform(0.1, 2.0, n)
+    return s1, nu1, s2, nu2
+
+
+@pytest.mark.parametrize("dims", SMALL)
+def test_masked_operators_against_dense_rows(dims):
+    prob = _problem(dims)
+    n = prob.n
+    A = _dense(prob.A, n)
+    Mp = A[prob.mask.reshape(-1)]                     # M_perp = A_{observed rows}, Eq. (MMperp)
+    rng = np.random.default_rng(5)
+    beta = rng.standard_normal(n)
+    b = rng.standard_normal(Mp.shape[0])
+    assert np.abs(prob.Mperp(beta) - Mp @ beta).max() < 1e-13
+    assert np.abs(prob.MperpT(b) - Mp.T @ b).max() < 1e-13
+    assert np.abs(prob.c - Mp.T @ prob.b).max() < 1e-13   # Eq. (xi): M_perp^T b = A^T b_hat
+
+
+@pytest.mark.parametrize("dims", SMALL)
+def test_G_is_orthogonal_projector(dims):
+    prob = _problem(dims)
+    G = _dense(prob.G, prob.n)
+    assert np.abs(G - G.T).max() < 1e-13
+    assert np.abs(G @ G - G).max() < 1e-13
+    assert abs(np.trace(G) - prob.mask.sum()) < 1e-10
+
+
+def test_objective_and_certificate_against_dense():
+    prob = _problem((4, 6), lam=0.3)
+    Mp = _dense(prob.A, prob.n)[prob.mask.reshape(-1)]
+    beta = np.random.default_rng(6).standard_normal(prob.n)
+    r = prob.b - Mp @ beta
+    assert abs(prob.objective(beta) - (0.5 * r @ r + 0.3 * np.abs(beta).sum())) < 1e-12
+    P, D, gap = prob.certificate(beta)
+    assert abs(P - prob.objective(beta)) < 1e-12 and gap >= 0
+    # the scaled dual point is feasible: ||M_perp^T theta_s||_inf <= lambda
+    corr = np.abs(Mp.T @ r).max()
+    ts = r * min(1.0, 0.3 / corr)
+    assert np.abs(Mp.T @ ts).max() <= 0.3 * (1 + 1e-12)
+    assert abs(D - (prob.b @ ts - 0.5 * ts @ ts)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_preconditioner_closed_form(seed):
+    rng = np.random.default_rng(seed)
+    n = 7
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    L1, L2 = S1 + S2, S1 - S2
+    P = np.block([[np.diag(1 + L1), np.diag(L2)], [np.diag(L2), np.diag(L1)]])
+    Pinv = _dense(lambda e: np.concatenate(ipm.Pinv_apply(S1, S2, e[:n], e[n:])), 2 * n)
+    assert np.abs(Pinv - np.linalg.inv(P)).max() < 1e-12 * np.abs(np.linalg.inv(P)).max()
+    Pd = _dense(lambda e: np.concatenate(ipm.P_apply(S1, S2, e[:n], e[n:])), 2 * n)
+    assert np.abs(Pd - P).max() < 1e-14
+    # Prop. exprbd: D = Lambda1 (I + Lambda1) - Lambda2^2 = Sigma1 + Sigma2 + 4 Sigma1 Sigma2 > 0
+    D = L1 * (1 + L1) - L2 ** 2
+    assert np.abs(D - (S1 + S2 + 4 * S1 * S2)).max() < 1e-12 * D.max()
+    # Eq. (11block): Lambda1 D^{-1} lies in (0, 1)
+    assert np.all((L1 / D > 0) & (L1 / D < 1))
+
+
+@pytest.mark.parametrize("dims", [(8,), (4, 6), (2, 2, 4)])
+def test_K_structure_and_preconditioned_blocks(dims):
+    prob = _problem(dims)
+    n = prob.n
+    rng = np.random.default_rng(7)
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    L1, L2 = S1 + S2, S1 - S2
+    D = S1 + S2 + 4 * S1 * S2
+    G = _dense(prob.G, n)
+    K = _dense(lambda e: np.concatenate(ipm.K_apply(prob.G, S1, S2, e[:n], e[n:])), 2 * n)
+    P = _dense(lambda e: np.concatenate(ipm.P_apply(S1, S2, e[:n], e[n:])), 2 * n)
+    I = np.eye(n)
+    # K = P + [[G - I, 0], [0, 0]]  (Eq. (condensedkkt) against the definition of P)
+    E = np.zeros((2 * n, 2 * n))
+    E[:n, :n] = G - I
+    assert np.abs(K - (P + E)).max() < 1e-12 * np.abs(K).max()
+    # Eq. (precond1): blocks of P^{-1} K
+    PiK = _dense(lambda e: np.concatenate(ipm.Pinv_apply(S1, S2, *np.split(K @ e, 2))), 2 * n)
+    assert np.abs(PiK[:n, n:]).max() < 1e-12
+    assert np.abs(PiK[n:, n:] - I).max() < 1e-12
+    assert np.abs(PiK[:n, :n] - (I + np.diag(L1 / D) @ (G - I))).max() < 1e-12
+    assert np.abs(PiK[n:, :n] - (-np.diag(L2 / D) @ (G - I))).max() < 1e-12
+
+
+def _F(prob, w, sigma, mu_fixed):
+    """Barrier residual of Eq. (kktmu) with y = nu and target sigma*mu held fixed."""
+    beta, z, s1, s2, nu1, nu2 = np.split(w, 6)
+    Mp = prob._Mp
+    return np.concatenate([
+        Mp.T @ (Mp @ beta - prob.b) - nu1 + nu2,
+        prob.lam - nu1 - nu2,
+        z + beta - s1,
+        z - beta - s2,
+        s1 * nu1 - sigma * mu_fixed,
+        s2 * nu2 - sigma * mu_fixed,
+    ])
+
+
+@pytest.mark.parametrize("dims", [(8,), (4, 4), (2, 2, 4)])
+def test_condensed_newton_step_equals_full_newton_step(dims):
+    prob = _problem(dims, lam=0.2)
+    n = prob.n
+    prob._Mp = _dense(prob.A, n)[prob.mask.reshape(-1)]
+    rng = np.random.default_rng(8)
+    beta = rng.standard_normal(n) * 0.3
+    z = np.abs(beta) + rng.uniform(0.2, 1.0, n)
+    s1 = z + beta + rng.uniform(-0.05, 0.05, n)       # deliberately infeasible rows 5, 6
+    s2 = z - beta + rng.uniform(-0.05, 0.05, n)
+    nu1, nu2 = rng.uniform(0.05, 0.2, n), rng.uniform(0.05, 0.2, n)
+    w = [beta, z, s1, s2, nu1, nu2]
+    sigma = 0.1
+    mu = (nu1 @ s1 + nu2 @ s2) / (2 * n)
+    # Jacobian by central differences (exact for this linear + bilinear map)
+    W = np.concatenate(w)
+    h = 1e-3
+    J = np.stack([(_F(prob, W + h * e, sigma, mu) - _F(prob, W - h * e, sigma, mu)) / (2 * h)
+                  for e in np.eye(6 * n)], axis=1)
+    dW = np.linalg.solve(J, -_F(prob, W, sigma, mu))
+    # the oracle's condensed path
+    res, mu2 = ipm.residuals(prob, prob.G(beta), w, sigma)
+    assert abs(mu2 - mu) < 1e-15
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    rhs = ipm.condensed_rhs(res, w)
+    (db, dz), it, _ = ipm.pcg(lambda a, b: ipm.K_apply(prob.G, S1, S2, a, b),
+                              lambda a, b: ipm.Pinv_apply(S1, S2, a, b), rhs, 1e-14, 500)
+    ds1, ds2, dnu1, dnu2 = ipm.back_substitute(res, w, db, dz)
+    mine = np.concatenate([db, dz, ds1, ds2, dnu1, dnu2])
+    assert np.abs(mine - dW).max() < 1e-8 * max(1.0, np.abs(dW).max())
+
+
+def test_pcg_one_iteration_without_mask():
+    """No missing samples: G = I, so P^{-1} K = I (Sec. 3.5) and PCG stops after one step."""
+    dims = (4, 6)
+    prob = Problem(dims, np.ones(dims, bool), np.random.default_rng(9).standard_normal(dims), 0.1)
+    n = prob.n
+    rng = np.random.default_rng(10)
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    rhs = (rng.standard_normal(n), rng.standard_normal(n))
+    x, it, _ = ipm.pcg(lambda a, b: ipm.K_apply(prob.G, S1, S2, a, b),
+                       lambda a, b: ipm.Pinv_apply(S1, S2, a, b), rhs, 1e-12, 50)
+    assert it == 1
+    Kx = np.concatenate(ipm.K_apply(prob.G, S1, S2, *x))
+    assert np.abs(Kx - np.concatenate(rhs)).max() < 1e-12
+
+
+def test_pcg_solves_masked_system():
+    prob = _problem((6, 4), missing=0.4)
+    n = prob.n
+    rng = np.random.default_rng(11)
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    K = _dense(lambda e: np.concatenate(ipm.K_apply(prob.G, S1, S2, e[:n], e[n:])), 2 * n)
+    rhs = rng.standard_normal(2 * n)
+    x, it, _ = ipm.pcg(lambda a, b: ipm.K_apply(prob.G, S1, S2, a, b),
+                       lambda a, b: ipm.Pinv_apply(S1, S2, a, b), tuple(np.split(rhs, 2)), 1e-13, 500)
+    assert np.abs(np.concatenate(x) - np.linalg.solve(K, rhs)).max() < 1e-10
