@@ -1,0 +1,188 @@
+/*
+ * sdft_ipm.h -- C ABI of the GB300 (sm_103a) solver for sparse-DFT recovery
+ * from a masked, noisy real signal (arXiv 2502.04217).
+ *
+ * The library solves the LASSO problem of Sec. 3, Eq. (realopt),
+ *     beta* = argmin_beta 1/2 || b - M_perp beta ||^2 + lambda || beta ||_1,
+ * where A = C^H B^H is the real orthogonal operator of Eq. (map) (orthonormal
+ * inverse DFT composed with the real parametrisation beta = B v of a
+ * conjugate-symmetric spectrum, Eq. (beta)), M_perp = A restricted to the
+ * observed samples (Eq. (MMperp)), and b the observed samples.  It runs the
+ * primal-dual interior-point method of Sec. 3.3 on the slack QP
+ * Eq. (slackproblem); each Newton system is reduced to the condensed KKT
+ * system Eq. (condensedkkt) and solved matrix-free by conjugate gradients with
+ * the preconditioner P of Sec. 3.5 (closed-form inverse Eq. (invprecond1)).
+ * Every product with M_perp^T M_perp is a pair of hand-written FFTs with the
+ * mask in between (Sec. 3.1); no cuFFT, no CPU fallback.
+ *
+ * Conventions
+ *  - Every function returns an ipm_status; nothing is thrown across the ABI.
+ *    On error, ipm_last_error() describes the failure.
+ *  - Arguments are checked on the host before any GPU work: a bad argument
+ *    returns IPM_ERR_ARG and leaves the handle unchanged.
+ *  - The library never frees caller memory; caller buffers are copied where
+ *    stated, and never retained after the call returns.
+ *  - Grids are row-major with the LAST axis contiguous; every extent must be
+ *    even (Sec. 3 treats the even case) and of the form 2^a 3^b with b <= 1,
+ *    at most 1024 along the last axis and 512 along the others.
+ *  - "beta layout": vectors indexed like beta are held as 2H doubles, where
+ *    H = N_0 ... N_{d-2} (N_{d-1}/2 + 1) is the number of half-spectrum slots.
+ *    Slot s carries two doubles; coordinates that are not LASSO variables
+ *    (imaginary parts of self-conjugate frequencies, conjugate twins on the
+ *    planes k_{d-1} in {0, N_{d-1}/2}) are "ghosts" and are always 0.  The
+ *    order of slots is internal; use ipm_pack_beta / ipm_unpack_beta to move
+ *    between the beta layout and the canonical half spectrum.
+ *  - "canonical half spectrum": the orthonormal DFT v of Sec. 3 restricted to
+ *    k_{d-1} in [0, N_{d-1}/2], row-major with the halved axis last, as
+ *    interleaved (re, im) doubles: 2H doubles (the layout of numpy's rfftn).
+ *  - Two-block vectors of the condensed system (p, q, r, z in kkt_apply and
+ *    precond_apply) are [beta block | z block], 4H doubles.
+ *  - Pointers documented as "device" must be device (or managed) memory of
+ *    the handle's device; pointers documented as "host or device" are
+ *    detected with cudaPointerGetAttributes.
+ *  - All work is queued on the handle's CUDA stream.  Functions that return
+ *    results to the host synchronise that stream before returning.
+ */
+#ifndef SDFT_IPM_H
+#define SDFT_IPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdft_ipm sdft_ipm; /* opaque; owns every device buffer it allocates */
+
+typedef enum {
+  IPM_OK = 0,
+  IPM_ERR_ARG = 1,          /* invalid argument; no GPU work was done            */
+  IPM_ERR_CUDA = 2,         /* a CUDA call failed; see ipm_last_error()           */
+  IPM_ERR_OOM = 3,          /* device allocation failed                          */
+  IPM_MAXITER = 4,          /* the IPM stopped at max_ipm before reaching gap_tol */
+  IPM_KRYLOV_MAXITER = 5,   /* a PCG solve stopped at max_cg (solve continued)    */
+  IPM_NUMERICAL = 6         /* non-finite value or loss of positive definiteness */
+} ipm_status;
+
+typedef enum { IPM_FP64 = 0, IPM_MIXED = 1 } ipm_precision;
+
+typedef struct {
+  int precision;        /* ipm_precision; IPM_FP64 is the plain method                       */
+  double gap_tol;       /* stop when (P - D) / max(1, |P|) <= gap_tol (default 1e-6)          */
+  double cg_tol;        /* PCG tolerance on sqrt(r^T P^{-1} r) (default 1e-10)                 */
+  int cg_relative;      /* 1: relative to the initial residual (default); 0: absolute,
+                           as the paper's 1e-12 rule (Sec. 5)                                  */
+  int max_ipm;          /* IPM iteration cap (default 200)                                     */
+  int max_cg;           /* PCG iteration cap per IPM iteration (default 500)                   */
+  double sigma;         /* centring parameter (default 0.1)                                    */
+  double sigma_slow;    /* centring after a short step alpha < 0.1 (default 0.5)               */
+  double tau;           /* fraction to the boundary (default 0.995)                            */
+  int lambda_relative;  /* 1: lambda is a fraction of lambda_max = ||M_perp^T b||_inf          */
+  int cg_chunk;         /* PCG iterations queued between host checks (default 4)               */
+} ipm_options;
+
+typedef struct {
+  int status;           /* ipm_status of the solve                                   */
+  int ipm_iters;        /* Newton directions computed                                */
+  int cg_iters_total;   /* PCG iterations (= products with K) over the solve         */
+  int cg_iters_max;     /* largest PCG count of one IPM iteration                    */
+  double primal;        /* P = 1/2 ||b - M_perp beta||^2 + lambda ||beta||_1         */
+  double dual;          /* D of the scaled dual point (never above the optimum)      */
+  double rel_gap;       /* (P - D) / max(1, |P|)                                     */
+  double mu;            /* final duality measure                                     */
+  double lambda;        /* the lambda actually used                                  */
+  double lambda_max;    /* ||M_perp^T b||_inf                                        */
+  double seconds;       /* wall time of ipm_solve                                    */
+  int kkt_products;     /* products with M_perp^T M_perp (PCG plus one per IPM iter) */
+} ipm_result;
+
+/* Fill *opt with the defaults listed above. */
+void ipm_default_options(ipm_options* opt);
+
+/* Create a solver for one problem on the current CUDA device.
+ *  ndim      1, 2 or 3.
+ *  dims      ndim extents (row-major, last contiguous), see Conventions.
+ *  mask      n = prod(dims) bytes, 1 = observed, 0 = missing (the paper's set
+ *            M, Sec. 3); host or device; copied.  At least one sample observed.
+ *  y         n doubles, the noisy signal; values at missing samples are
+ *            ignored (b_hat of Sec. 3.1 is formed on the device); host or device; copied.
+ *  lambda    > 0: the penalty, or its fraction of lambda_max when
+ *            opt->lambda_relative is set.
+ *  opt       NULL for defaults.
+ *  stream    cudaStream_t to queue work on (NULL = legacy default stream).
+ * Computes M_perp^T b once (Eq. (xi)) and lambda_max. */
+ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y,
+                      double lambda, const ipm_options* opt, void* stream);
+
+/* Replace mask, y and lambda of an existing handle (same grid); host or
+ * device pointers, copied.  Recomputes M_perp^T b and lambda_max. */
+ipm_status ipm_set_problem(sdft_ipm* h, const uint8_t* mask, const double* y, double lambda);
+
+/* Replace the options (grid and data unchanged). */
+ipm_status ipm_set_options(sdft_ipm* h, const ipm_options* opt);
+
+/* Run the interior-point method from the cold start of Sec. 3.3 (or from the
+ * point set by ipm_set_point since the last solve).  Fills *res (may be NULL).
+ * Returns IPM_OK on convergence to gap_tol, IPM_MAXITER, or an error. */
+ipm_status ipm_solve(sdft_ipm* h, ipm_result* res);
+
+/* Sizes: *nslots = H (beta-layout vectors have 2H doubles), *n = prod(dims). */
+ipm_status ipm_sizes(const sdft_ipm* h, int64_t* nslots, int64_t* n);
+
+/* q = M_perp^T M_perp p for a beta-layout vector (Sec. 3.1); device pointers,
+ * 2H doubles each; p's ghost coordinates must be 0, q's are written as 0. */
+ipm_status gapply(sdft_ipm* h, const double* p, double* q);
+
+/* q = K p with K = [G + Lambda1, Lambda2; Lambda2, Lambda1] (Eq. (condensedkkt)),
+ * G = M_perp^T M_perp, Lambda1 = Sigma1 + Sigma2, Lambda2 = Sigma1 - Sigma2
+ * for the Sigma set by ipm_set_sigma (or the last IPM iterate).  Device
+ * pointers, 4H doubles each ([beta block | z block]). */
+ipm_status kkt_apply(sdft_ipm* h, const double* p, double* q);
+
+/* z = P^{-1} r by the closed form Eq. (invprecond1) with D = Sigma1 + Sigma2 +
+ * 4 Sigma1 Sigma2 (Prop. exprbd).  Device pointers, 4H doubles each. */
+ipm_status precond_apply(sdft_ipm* h, const double* r, double* z);
+
+/* Set Sigma_i = S_i^{-1} V_i (Eq. (defsigma)) from slacks s_i > 0 and bound
+ * multipliers nu_i > 0 in the beta layout (device pointers, 2H doubles each;
+ * ghost entries ignored). */
+ipm_status ipm_set_sigma(sdft_ipm* h, const double* s1, const double* nu1, const double* s2, const double* nu2);
+
+/* Start the next ipm_solve from w = (beta, z, s1, s2, nu1, nu2), each 2H
+ * doubles in the beta layout, host or device; s and nu must be > 0 on every
+ * non-ghost coordinate.  Used for warm starts and to resume a solve. */
+ipm_status ipm_set_point(sdft_ipm* h, const double* const w[6]);
+
+/* Copy the current iterate (beta, z, s1, s2, nu1, nu2) to six buffers of 2H
+ * doubles (host or device). */
+ipm_status ipm_get_point(sdft_ipm* h, double* const w[6]);
+
+/* The recovered spectrum v = B^H beta of the current iterate as the canonical
+ * half spectrum (2H doubles, host or device). */
+ipm_status ipm_get_spectrum(sdft_ipm* h, double* v_half);
+
+/* beta layout <-> canonical half spectrum (Eq. (beta) / Eq. (v)); device
+ * pointers, 2H doubles each.  pack ignores the entries of twins on the edge
+ * planes; unpack fills them with the conjugate of their representative. */
+ipm_status ipm_pack_beta(sdft_ipm* h, const double* v_half, double* beta);
+ipm_status ipm_unpack_beta(sdft_ipm* h, const double* beta, double* v_half);
+
+/* Per-kernel timing with CUDA events around every launch (0 = off, default).
+ * ipm_profile_get returns, for kernel class k (0: FFT row pass, 1: column
+ * pass, 2: middle pass, 3: PCG update, 4: IPM kernels), the number of
+ * launches and their summed duration in milliseconds since the last reset. */
+ipm_status ipm_profile_enable(sdft_ipm* h, int on);
+ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms);
+
+/* Message of the last failure on this handle (or of the last failed create
+ * when h is NULL).  Owned by the library. */
+const char* ipm_last_error(const sdft_ipm* h);
+
+/* Free every device buffer of the handle.  NULL is accepted. */
+void ipm_destroy(sdft_ipm* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDFT_IPM_H */

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libsdft_ipm.so (include/sdft_ipm.h), same names as the C ABI.
+
+Only argument marshalling lives here: every step of the solve runs in the
+CUDA library.  Loading fails loudly when the library has not been built;
+there is no fallback.
+
+Arrays may be torch tensors (CPU or CUDA), numpy arrays, or raw integer
+addresses.  The C functions documented as taking device pointers must be
+given CUDA tensors (or device addresses).
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsdft_ipm.so")
+
+IPM_OK, IPM_ERR_ARG, IPM_ERR_CUDA, IPM_ERR_OOM, IPM_MAXITER, IPM_KRYLOV_MAXITER, IPM_NUMERICAL = range(7)
+IPM_FP64, IPM_MIXED = 0, 1
+STATUS_NAMES = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_CUDA", 3: "IPM_ERR_OOM", 4: "IPM_MAXITER",
+                5: "IPM_KRYLOV_MAXITER", 6: "IPM_NUMERICAL"}
+PROFILE_CLASSES = {"fft_row": 0, "fft_col": 1, "fft_middle": 2, "pcg_update": 3, "ipm": 4}
+
+
+class ipm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("gap_tol", ctypes.c_double), ("cg_tol", ctypes.c_double),
+                ("cg_relative", ctypes.c_int), ("max_ipm", ctypes.c_int), ("max_cg", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("sigma_slow", ctypes.c_double), ("tau", ctypes.c_double),
+                ("lambda_relative", ctypes.c_int), ("cg_chunk", ctypes.c_int)]
+
+
+class ipm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("ipm_iters", ctypes.c_int), ("cg_iters_total", ctypes.c_int),
+                ("cg_iters_max", ctypes.c_int), ("primal", ctypes.c_double), ("dual", ctypes.c_double),
+                ("rel_gap", ctypes.c_double), ("mu", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("lambda_max", ctypes.c_double), ("seconds", ctypes.c_double), ("kkt_products", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class IpmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "ipm_default_options": (None, [ctypes.POINTER(ipm_options)]),
+    "ipm_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _P, _P,
+                                  ctypes.c_double, ctypes.POINTER(ipm_options), _P]),
+    "ipm_set_problem": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "ipm_set_options": (ctypes.c_int, [_P, ctypes.POINTER(ipm_options)]),
+    "ipm_solve": (ctypes.c_int, [_P, ctypes.POINTER(ipm_result)]),
+    "ipm_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "gapply": (ctypes.c_int, [_P, _P, _P]),
+    "kkt_apply": (ctypes.c_int, [_P, _P, _P]),
+    "precond_apply": (ctypes.c_int, [_P, _P, _P]),
+    "ipm_set_sigma": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "ipm_set_point": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "ipm_get_point": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "ipm_get_spectrum": (ctypes.c_int, [_P, _P]),
+    "ipm_pack_beta": (ctypes.c_int, [_P, _P, _P]),
+    "ipm_unpack_beta": (ctypes.c_int, [_P, _P, _P]),
+    "ipm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ipm_profile_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_double)]),
+    "ipm_last_error": (ctypes.c_char_p, [_P]),
+    "ipm_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load(path=None):
+    """Load libsdft_ipm.so (once) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def addr(x):
+    """Address of an array-like: torch tensor, numpy array or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def default_options(**kw):
+    o = ipm_options()
+    load().ipm_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _check(status, handle=None):
+    if status != IPM_OK:
+        msg = load().ipm_last_error(handle)
+        raise IpmError(status, msg.decode() if msg else "")
+    return status
+
+
+# ---- functions with the C names ---------------------------------------------------------
+
+def ipm_create(dims, mask, y, lam, options=None, stream=None):
+    """Returns a handle (int).  mask: uint8, y: float64, host or device, n elements each."""
+    lib = load()
+    h = _P()
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    st = lib.ipm_create(ctypes.byref(h), len(dims), d, addr(mask), addr(y), float(lam),
+                        ctypes.byref(options) if options is not None else None, stream)
+    _check(st, None)
+    return h.value
+
+
+def ipm_set_problem(h, mask, y, lam):
+    return _check(load().ipm_set_problem(h, addr(mask), addr(y), float(lam)), h)
+
+
+def ipm_set_options(h, options):
+    return _check(load().ipm_set_options(h, ctypes.byref(options)), h)
+
+
+def ipm_solve(h, check=True):
+    r = ipm_result()
+    st = load().ipm_solve(h, ctypes.byref(r))
+    if check and st not in (IPM_OK, IPM_KRYLOV_MAXITER):
+        _check(st, h)
+    out = r.as_dict()
+    out["lambda"] = out.pop("lambda_")
+    out["status_name"] = STATUS_NAMES.get(st, st)
+    return out
+
+
+def ipm_sizes(h):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().ipm_sizes(h, ctypes.byref(a), ctypes.byref(b)), h)
+    return a.value, b.value
+
+
+def gapply(h, p, q):
+    return _check(load().gapply(h, addr(p), addr(q)), h)
+
+
+def kkt_apply(h, p, q):
+    return _check(load().kkt_apply(h, addr(p), addr(q)), h)
+
+
+def precond_apply(h, r, z):
+    return _check(load().precond_apply(h, addr(r), addr(z)), h)
+
+
+def ipm_set_sigma(h, s1, nu1, s2, nu2):
+    return _check(load().ipm_set_sigma(h, addr(s1), addr(nu1), addr(s2), addr(nu2)), h)
+
+
+def ipm_set_point(h, w):
+    arr = (_P * 6)(*[addr(v) for v in w])
+    return _check(load().ipm_set_point(h, arr), h)
+
+
+def ipm_get_point(h, w):
+    arr = (_P * 6)(*[addr(v) for v in w])
+    return _check(load().ipm_get_point(h, arr), h)
+
+
+def ipm_get_spectrum(h, v_half):
+    return _check(load().ipm_get_spectrum(h, addr(v_half)), h)
+
+
+def ipm_pack_beta(h, v_half, beta):
+    return _check(load().ipm_pack_beta(h, addr(v_half), addr(beta)), h)
+
+
+def ipm_unpack_beta(h, beta, v_half):
+    return _check(load().ipm_unpack_beta(h, addr(beta), addr(v_half)), h)
+
+
+def ipm_profile_enable(h, on=True):
+    return _check(load().ipm_profile_enable(h, 1 if on else 0), h)
+
+
+def ipm_profile_get(h, k):
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(load().ipm_profile_get(h, int(k), ctypes.byref(n), ctypes.byref(ms)), h)
+    return n.value, ms.value
+
+
+def ipm_last_error(h=None):
+    m = load().ipm_last_error(h)
+    return m.decode() if m else ""
+
+
+def ipm_destroy(h):
+    load().ipm_destroy(h)

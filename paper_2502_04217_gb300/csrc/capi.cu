@@ -1,0 +1,758 @@
+// C ABI of the solver (declared in include/sdft_ipm.h): handle lifetime,
+// FFT pass planning, and the host side of the interior-point loop
+// (Sec. 3.3-3.5): every arithmetic step runs in the kernels of
+// fft_passes.cu and ipm_kernels.cu; the host only queues launches and reads
+// the device scalars where it has to decide (IPM stop, PCG chunk boundaries).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sdft_ipm.h"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace sdft;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// One planned launch of an FFT pass.
+struct PassCfg {
+  int kind = 0;             // 0 row, 1 column, 2 middle
+  int E = 8;
+  int lgP = 0, PP = 1, nwork = 0, threads = 32;
+  size_t smem = 0;
+  dim3 grid;
+  FftPlan plan{};
+  long long npencils = 0;
+  const void* tw = nullptr;
+  const void* twN = nullptr;
+};
+
+struct PassSet {
+  PassCfg row_inv, row_fwd, col_inv, col_fwd, mid;
+};
+
+struct ProfEntry {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+bool factor_ok(int L) {
+  int m = L;
+  while (m % 2 == 0) m /= 2;
+  if (m % 3 == 0) m /= 3;
+  return m == 1;
+}
+
+// Radices for length L: 8s, then a 4 and/or 2 (or, with a factor 3, 4s, 2s, then 3 last).
+FftPlan make_plan(int L, int E) {
+  FftPlan p{};
+  p.L = L;
+  int m = L;
+  bool three = (m % 3 == 0);
+  if (three) m /= 3;
+  while (E % 8 == 0 && m % 8 == 0) { p.radix[p.nst++] = 8; m /= 8; }
+  while (m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
+  while (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
+  if (three) p.radix[p.nst++] = 3;
+  return p;
+}
+
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+}  // namespace
+
+struct sdft_ipm {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  ipm_options opt{};
+  Layout lay{};
+  int dims[3] = {0, 0, 0};
+  std::string err;
+  double lambda_in = 0.0;
+  // device memory
+  std::vector<void*> allocs;
+  uint8_t* d_mask = nullptr;
+  double* d_y = nullptr;
+  uint32_t* d_maskw = nullptr;
+  IpmVectors w{};
+  void* d_U = nullptr;          // complex work buffer (H values, sized for double)
+  double* d_tmp = nullptr;      // 2H scratch for pack/unpack and spectrum readback
+  double* d_partials = nullptr;
+  unsigned* d_counter = nullptr;
+  DevScalars* d_sc = nullptr;
+  DevScalars* h_sc = nullptr;   // pinned mirror
+  size_t partial_cap = 0;
+  PassSet pass64, pass32;
+  std::vector<void*> tables;
+  bool point_set = false;
+  bool sigma_ready = false;
+  // profiling
+  bool prof = false;
+  std::vector<ProfEntry> prof_live;
+  std::vector<cudaEvent_t> ev_pool;
+  long long prof_count[5] = {0, 0, 0, 0, 0};
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      return e_ == cudaErrorMemoryAllocation ? IPM_ERR_OOM : IPM_ERR_CUDA;             \
+    }                                                                                  \
+  } while (0)
+
+ipm_status fail_arg(sdft_ipm* h, const char* msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return IPM_ERR_ARG;
+}
+
+template <typename Ptr>
+cudaError_t dalloc(sdft_ipm* h, Ptr** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+  if (e == cudaSuccess) { h->allocs.push_back(q); *p = (Ptr*)q; }
+  return e;
+}
+
+cudaEvent_t pool_event(sdft_ipm* h) {
+  if (!h->ev_pool.empty()) { cudaEvent_t e = h->ev_pool.back(); h->ev_pool.pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  sdft_ipm* h;
+  int cls;
+  cudaEvent_t a = nullptr;
+  ProfScope(sdft_ipm* h_, int c) : h(h_), cls(c) {
+    if (h->prof) { a = pool_event(h); cudaEventRecord(a, h->st); }
+  }
+  ~ProfScope() {
+    if (h->prof) {
+      cudaEvent_t b = pool_event(h);
+      cudaEventRecord(b, h->st);
+      h->prof_live.push_back({cls, a, b});
+    }
+  }
+};
+
+void prof_collect(sdft_ipm* h) {
+  if (h->prof_live.empty()) return;
+  cudaStreamSynchronize(h->st);
+  for (auto& e : h->prof_live) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e.a, e.b);
+    h->prof_count[e.cls] += 1;
+    h->prof_ms[e.cls] += ms;
+    h->ev_pool.push_back(e.a);
+    h->ev_pool.push_back(e.b);
+  }
+  h->prof_live.clear();
+}
+
+// Twiddle table exp(-2 pi i t / L), t = 0..L-1, in double and float.
+ipm_status make_tables(sdft_ipm* h, int L, const void** t64, const void** t32) {
+  std::vector<double> d(2 * (size_t)L);
+  std::vector<float> f(2 * (size_t)L);
+  for (int t = 0; t < L; ++t) {
+    const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)L;
+    d[2 * t] = (double)cosl(ang);
+    d[2 * t + 1] = (double)(-sinl(ang));
+    f[2 * t] = (float)d[2 * t];
+    f[2 * t + 1] = (float)d[2 * t + 1];
+  }
+  void *a = nullptr, *b = nullptr;
+  CK(dalloc(h, &a, d.size() * sizeof(double)));
+  CK(dalloc(h, &b, f.size() * sizeof(float)));
+  CK(cudaMemcpy(a, d.data(), d.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+  *t64 = a;
+  *t32 = b;
+  return IPM_OK;
+}
+
+// Choose pencils per tile P (power of two) for a pass of `npen` pencils of FFT
+// length L held in `rows` smem rows of element size esz.
+void plan_tile(PassCfg& c, int L, int rows, long long npen, bool fp32) {
+  const int esz = fp32 ? 8 : 16;
+  c.E = (L % 3 == 0) ? 12 : 8;
+  c.plan = make_plan(L, c.E);
+  int P = fp32 ? 16 : 8;
+  const int Pmin = fp32 ? 4 : 2;
+  // fewer pencils per tile when the pass would otherwise leave SMs idle
+  while (P > Pmin && (npen + P - 1) / P < 2 * 152) P /= 2;
+  // P * L must be a multiple of E; the thread count P * L / E at most 1024; smem bounded
+  while ((P * L) % c.E != 0) P *= 2;
+  while (P > 1 && ((P * L) / c.E > 512 || (size_t)rows * (P + 1) * esz > 200 * 1024)) P /= 2;
+  c.lgP = ilog2(P);
+  c.PP = (P >= (fp32 ? 16 : 8)) ? P + 1 : P;
+  c.nwork = (P * L) / c.E;
+  c.threads = ((c.nwork + 31) / 32) * 32;
+  if (c.threads < 64) c.threads = 64;
+  c.smem = (size_t)rows * c.PP * esz;
+  c.npencils = npen;
+}
+
+ipm_status plan_passes(sdft_ipm* h, PassSet& ps, bool fp32) {
+  const Layout& L = h->lay;
+  const void *t64, *t32;
+  // middle pass: h = Nl/2 complex FFT, Hl rows, M pencils
+  {
+    PassCfg& c = ps.mid;
+    c.kind = 2;
+    plan_tile(c, L.Nl / 2, L.Hl, L.M, fp32);
+    c.grid = dim3((unsigned)((L.M + (1 << c.lgP) - 1) >> c.lgP));
+    ipm_status s = make_tables(h, L.Nl / 2, &t64, &t32);
+    if (s != IPM_OK) return s;
+    c.tw = fp32 ? t32 : t64;
+    s = make_tables(h, L.Nl, &t64, &t32);
+    if (s != IPM_OK) return s;
+    c.twN = fp32 ? t32 : t64;
+  }
+  if (L.d >= 2) {
+    // row pass along the contiguous in-plane axis: rows of length Lr
+    const int Lr = (L.d == 3) ? L.N1 : L.N0;
+    const long long nrows = L.H / Lr;
+    PassCfg c;
+    c.kind = 0;
+    plan_tile(c, Lr, Lr, nrows, fp32);
+    c.grid = dim3((unsigned)((nrows + (1 << c.lgP) - 1) >> c.lgP));
+    ipm_status s = make_tables(h, Lr, &t64, &t32);
+    if (s != IPM_OK) return s;
+    c.tw = fp32 ? t32 : t64;
+    ps.row_inv = c;
+    ps.row_fwd = c;
+  }
+  if (L.d == 3) {
+    PassCfg c;
+    c.kind = 1;
+    plan_tile(c, L.N0, L.N0, (long long)L.N1 * L.Hl, fp32);
+    // column tiles cover P consecutive k1 of one plane
+    c.grid = dim3((unsigned)((L.N1 + (1 << c.lgP) - 1) >> c.lgP), (unsigned)L.Hl);
+    ipm_status s = make_tables(h, L.N0, &t64, &t32);
+    if (s != IPM_OK) return s;
+    c.tw = fp32 ? t32 : t64;
+    ps.col_inv = c;
+    ps.col_fwd = c;
+  }
+  return IPM_OK;
+}
+
+PassArgs base_args(sdft_ipm* h, const PassCfg& c) {
+  PassArgs a{};
+  a.lay = h->lay;
+  a.plan = c.plan;
+  a.lgP = c.lgP;
+  a.PP = c.PP;
+  a.nwork = c.nwork;
+  a.npencils = c.npencils;
+  a.tw = c.tw;
+  a.twN = c.twN;
+  a.buf = h->d_U;
+  a.maskw = h->d_maskw;
+  a.inv_n = 1.0 / (double)h->lay.n;
+  a.partials = h->d_partials;
+  a.counter = h->d_counter;
+  a.sc = h->d_sc;
+  a.out_scale = 1.0;
+  return a;
+}
+
+ipm_status launch(sdft_ipm* h, const PassCfg& c, bool inv, bool fp32, const PassArgs& a) {
+  ProfScope ps(h, c.kind);
+  CK(launch_pass(c.kind, inv, fp32, c.E, a, c.threads, c.smem, c.grid, h->st));
+  return IPM_OK;
+}
+
+// What one application of G starts from and ends in.
+struct GSpec {
+  int mapin = MAPIN_BETA;
+  const double* src = nullptr;   // MAPIN_BETA
+  int mapout = MAPOUT_BETA;
+  double* dst = nullptr;         // MAPOUT_BETA
+  double out_scale = 1.0;
+  bool pcg = false;              // MAPIN_PCG / MAPOUT_K inside PCG (p, zv, q of the handle)
+  const double* p_in = nullptr;  // kkt_apply: p and q given by the caller
+  double* q_out = nullptr;
+};
+
+// One application of G = A^T diag(m) A (with the chosen prologue/epilogue).
+ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
+  const Layout& L = h->lay;
+  const PassSet& ps = fp32 ? h->pass32 : h->pass64;
+  auto fill = [&](PassArgs& a, bool first, bool last) {
+    if (first) {
+      a.mapin = g.mapin;
+      a.src = g.src;
+      a.p = g.pcg ? h->w.p : const_cast<double*>(g.p_in);
+      a.zv = h->w.zv;
+    }
+    if (last) {
+      a.mapout = g.mapout;
+      a.dst = g.dst;
+      a.out_scale = g.out_scale;
+      a.p = g.pcg ? h->w.p : const_cast<double*>(g.p_in);
+      a.q = g.pcg ? h->w.q : g.q_out;
+      a.lam1 = h->w.lam1;
+      a.lam2 = h->w.lam2;
+      a.pcg_mode = g.pcg ? 1 : 0;
+    }
+    a.check_done = g.pcg ? 1 : 0;
+  };
+  ipm_status s;
+  if (L.d == 1) {
+    PassArgs a = base_args(h, ps.mid);
+    fill(a, true, true);
+    return launch(h, ps.mid, false, fp32, a);
+  }
+  {
+    PassArgs a = base_args(h, ps.row_inv);
+    fill(a, true, false);
+    if ((s = launch(h, ps.row_inv, true, fp32, a)) != IPM_OK) return s;
+  }
+  if (L.d == 3) {
+    PassArgs a = base_args(h, ps.col_inv);
+    fill(a, false, false);
+    if ((s = launch(h, ps.col_inv, true, fp32, a)) != IPM_OK) return s;
+  }
+  {
+    PassArgs a = base_args(h, ps.mid);
+    fill(a, false, false);
+    if ((s = launch(h, ps.mid, false, fp32, a)) != IPM_OK) return s;
+  }
+  if (L.d == 3) {
+    PassArgs a = base_args(h, ps.col_fwd);
+    fill(a, false, false);
+    if ((s = launch(h, ps.col_fwd, false, fp32, a)) != IPM_OK) return s;
+  }
+  PassArgs a = base_args(h, ps.row_fwd);
+  fill(a, false, true);
+  return launch(h, ps.row_fwd, false, fp32, a);
+}
+
+// c = M_perp^T b = B DFT(b_hat) / sqrt(n) scaling, in FP64 (Eq. (xi)).
+ipm_status compute_c(sdft_ipm* h) {
+  const Layout& L = h->lay;
+  const PassSet& ps = h->pass64;
+  const double scale = 1.0 / std::sqrt((double)L.n);
+  PassArgs a = base_args(h, ps.mid);
+  a.from_real = 1;
+  a.yreal = h->d_y;
+  ipm_status s;
+  if (L.d == 1) {
+    a.mapout = MAPOUT_BETA;
+    a.dst = h->w.c;
+    a.out_scale = scale;
+    return launch(h, ps.mid, false, false, a);
+  }
+  if ((s = launch(h, ps.mid, false, false, a)) != IPM_OK) return s;
+  if (L.d == 3) {
+    PassArgs b = base_args(h, ps.col_fwd);
+    if ((s = launch(h, ps.col_fwd, false, false, b)) != IPM_OK) return s;
+  }
+  PassArgs b = base_args(h, ps.row_fwd);
+  b.mapout = MAPOUT_BETA;
+  b.dst = h->w.c;
+  b.out_scale = scale;
+  return launch(h, ps.row_fwd, false, false, b);
+}
+
+ipm_status read_scalars(sdft_ipm* h) {
+  CK(cudaMemcpyAsync(h->h_sc, h->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IPM_OK;
+}
+
+ipm_status upload_problem(sdft_ipm* h, const uint8_t* mask, const double* y, double lambda) {
+  const Layout& L = h->lay;
+  if (!mask || !y) return fail_arg(h, "mask and y must not be NULL");
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail_arg(h, "lambda must be positive and finite");
+  CK(cudaMemcpyAsync(h->d_mask, mask, (size_t)L.n, cudaMemcpyDefault, h->st));
+  CK(cudaMemcpyAsync(h->d_y, y, (size_t)L.n * sizeof(double), cudaMemcpyDefault, h->st));
+  CK(k_pack_mask(h->d_mask, h->d_maskw, L.Nl, L.M, h->st));
+  Reduce red{h->d_partials, h->d_counter};
+  CK(k_observed_norm(h->d_y, h->d_mask, L.n, red, h->d_sc, h->st));
+  ipm_status s = compute_c(h);
+  if (s != IPM_OK) return s;
+  CK(k_cmax(h->w.c, 2 * L.H, lambda, h->opt.lambda_relative, red, h->d_sc, h->st));
+  h->lambda_in = lambda;
+  h->point_set = false;
+  return IPM_OK;
+}
+
+// After an upload: at least one observed sample and a positive lambda.
+ipm_status check_resolved(sdft_ipm* h) {
+  if (!(h->h_sc->nobs > 0)) return fail_arg(h, "the mask observes no sample");
+  if (!(h->h_sc->lambda > 0) || !std::isfinite(h->h_sc->lambda))
+    return fail_arg(h, "lambda resolved to a non-positive value (lambda_max = 0?)");
+  return IPM_OK;
+}
+
+ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
+  if (o.precision != IPM_FP64 && o.precision != IPM_MIXED) return fail_arg(h, "precision must be IPM_FP64 or IPM_MIXED");
+  if (!(o.gap_tol > 0) || !(o.cg_tol > 0)) return fail_arg(h, "gap_tol and cg_tol must be positive");
+  if (o.max_ipm < 0 || o.max_cg < 1 || o.cg_chunk < 1) return fail_arg(h, "iteration caps must be positive");
+  if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
+  if (!(o.tau > 0 && o.tau < 1)) return fail_arg(h, "tau must lie in (0,1)");
+  return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipm_default_options(ipm_options* o) {
+  if (!o) return;
+  o->precision = IPM_FP64;
+  o->gap_tol = 1e-6;
+  o->cg_tol = 1e-10;
+  o->cg_relative = 1;
+  o->max_ipm = 200;
+  o->max_cg = 500;
+  o->sigma = 0.1;
+  o->sigma_slow = 0.5;
+  o->tau = 0.995;
+  o->lambda_relative = 0;
+  o->cg_chunk = 4;
+}
+
+ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
+                      const ipm_options* opt, void* stream) {
+  g_create_error.clear();
+  if (!out) return fail_arg(nullptr, "out must not be NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > 3 || !dims) return fail_arg(nullptr, "ndim must be 1, 2 or 3");
+  for (int i = 0; i < ndim; ++i) {
+    if (dims[i] < 2 || dims[i] % 2 || dims[i] > 512 || !factor_ok((int)dims[i]))
+      return fail_arg(nullptr, "every extent must be even, of the form 2^a 3^b (b <= 1), and at most 512");
+  }
+  ipm_options o;
+  ipm_default_options(&o);
+  if (opt) o = *opt;
+  sdft_ipm* h = new sdft_ipm();
+  h->opt = o;
+  if (check_options(h, o) != IPM_OK) { g_create_error = h->err; delete h; return IPM_ERR_ARG; }
+  cudaGetDevice(&h->device);
+  h->st = (cudaStream_t)stream;
+  Layout& L = h->lay;
+  L.d = ndim;
+  for (int i = 0; i < ndim; ++i) h->dims[i] = (int)dims[i];
+  L.Nl = (int)dims[ndim - 1];
+  L.N0 = ndim >= 2 ? (int)dims[0] : 1;
+  L.N1 = ndim == 3 ? (int)dims[1] : 1;
+  L.M = L.N0 * L.N1;
+  L.Hl = L.Nl / 2 + 1;
+  L.H = (long long)L.Hl * L.M;
+  L.n = (long long)L.Nl * L.M;
+  auto cleanup_fail = [&](ipm_status s) {
+    g_create_error = h->err;
+    ipm_destroy(h);
+    return s;
+  };
+#define CKC(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+      return cleanup_fail(e_ == cudaErrorMemoryAllocation ? IPM_ERR_OOM : IPM_ERR_CUDA); \
+    }                                                                               \
+  } while (0)
+  const size_t v2 = 2 * (size_t)L.H * sizeof(double), v4 = 2 * v2;
+  CKC(dalloc(h, &h->d_mask, (size_t)L.n));
+  CKC(dalloc(h, &h->d_y, (size_t)L.n * sizeof(double)));
+  CKC(dalloc(h, &h->d_maskw, (size_t)((L.Nl + 31) / 32) * L.M * sizeof(uint32_t)));
+  double** vec2[] = {&h->w.beta, &h->w.z, &h->w.s1, &h->w.s2, &h->w.nu1, &h->w.nu2, &h->w.c, &h->w.Gb,
+                     &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->d_tmp};
+  for (double** p : vec2) CKC(dalloc(h, p, v2));
+  double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q};
+  for (double** p : vec4) CKC(dalloc(h, p, v4));
+  CKC(dalloc(h, &h->d_U, (size_t)L.H * 2 * sizeof(double)));
+  CKC(dalloc(h, &h->d_sc, sizeof(DevScalars)));
+  CKC(cudaMemsetAsync(h->d_sc, 0, sizeof(DevScalars), h->st));
+  {
+    void* p = nullptr;
+    CKC(cudaMallocHost(&p, sizeof(DevScalars)));
+    h->h_sc = (DevScalars*)p;
+  }
+  ipm_status s;
+  if ((s = plan_passes(h, h->pass64, false)) != IPM_OK) return cleanup_fail(s);
+  if ((s = plan_passes(h, h->pass32, true)) != IPM_OK) return cleanup_fail(s);
+  // partials: 4 values per elementwise block, 1 per FFT block
+  size_t cap = 4 * (size_t)kMaxElementwiseBlocks;
+  for (const PassSet* ps : {&h->pass64, &h->pass32}) {
+    for (const PassCfg* c : {&ps->row_fwd, &ps->mid}) {
+      const size_t nb = (size_t)c->grid.x * c->grid.y * c->grid.z;
+      if (nb > cap) cap = nb;
+    }
+  }
+  h->partial_cap = cap;
+  CKC(dalloc(h, &h->d_partials, cap * sizeof(double)));
+  CKC(dalloc(h, &h->d_counter, 64 * sizeof(unsigned)));
+  CKC(cudaMemsetAsync(h->d_counter, 0, 64 * sizeof(unsigned), h->st));
+  // vectors start at 0 (ghosts stay 0 from here on)
+  for (double** p : vec2) CKC(cudaMemsetAsync(*p, 0, v2, h->st));
+  for (double** p : vec4) CKC(cudaMemsetAsync(*p, 0, v4, h->st));
+  if ((s = upload_problem(h, mask, y, lambda)) != IPM_OK) return cleanup_fail(s);
+  if ((s = read_scalars(h)) != IPM_OK) return cleanup_fail(s);
+  if ((s = check_resolved(h)) != IPM_OK) return cleanup_fail(s);
+#undef CKC
+  *out = h;
+  return IPM_OK;
+}
+
+ipm_status ipm_set_problem(sdft_ipm* h, const uint8_t* mask, const double* y, double lambda) {
+  if (!h) return fail_arg(nullptr, "handle is NULL");
+  ipm_status s = upload_problem(h, mask, y, lambda);
+  if (s != IPM_OK) return s;
+  if ((s = read_scalars(h)) != IPM_OK) return s;
+  return check_resolved(h);
+}
+
+ipm_status ipm_set_options(sdft_ipm* h, const ipm_options* opt) {
+  if (!h || !opt) return fail_arg(h, "handle and options must not be NULL");
+  ipm_status s = check_options(h, *opt);
+  if (s != IPM_OK) return s;
+  const bool rel_changed = opt->lambda_relative != h->opt.lambda_relative;
+  h->opt = *opt;
+  if (rel_changed) {
+    Reduce red{h->d_partials, h->d_counter};
+    CK(k_cmax(h->w.c, 2 * h->lay.H, h->lambda_in, h->opt.lambda_relative, red, h->d_sc, h->st));
+    ipm_status r = read_scalars(h);
+    return r != IPM_OK ? r : check_resolved(h);
+  }
+  return IPM_OK;
+}
+
+ipm_status ipm_sizes(const sdft_ipm* h, int64_t* nslots, int64_t* n) {
+  if (!h) return IPM_ERR_ARG;
+  if (nslots) *nslots = h->lay.H;
+  if (n) *n = h->lay.n;
+  return IPM_OK;
+}
+
+ipm_status ipm_solve(sdft_ipm* h, ipm_result* res) {
+  if (!h) return fail_arg(nullptr, "handle is NULL");
+  const auto t0 = std::chrono::steady_clock::now();
+  const Layout& L = h->lay;
+  const ipm_options& o = h->opt;
+  const bool fp32 = o.precision == IPM_MIXED;
+  Reduce red{h->d_partials, h->d_counter};
+  ipm_status s;
+  {
+    ProfScope ps(h, 4);
+    if (h->point_set) CK(k_mu(L, h->w, red, h->d_sc, o.sigma, h->st));
+    else CK(k_init_point(L, h->w, red, h->d_sc, o.sigma, h->st));
+  }
+  h->point_set = false;
+  int ipm_iters = 0, cg_total = 0, cg_max = 0, products = 0;
+  ipm_status final_status = IPM_MAXITER;
+  bool krylov_cap = false;
+  for (int it = 0;; ++it) {
+    GSpec g;
+    g.src = h->w.beta;
+    g.dst = h->w.Gb;
+    if ((s = run_g(h, false, g)) != IPM_OK) return s;     // residual always in FP64
+    ++products;
+    {
+      ProfScope ps(h, 4);
+      CK(k_certificate(L, h->w.beta, h->w.Gb, h->w.c, red, h->d_sc, h->st));
+    }
+    if ((s = read_scalars(h)) != IPM_OK) return s;
+    if (!std::isfinite(h->h_sc->gap) || !std::isfinite(h->h_sc->mu)) { final_status = IPM_NUMERICAL; break; }
+    if (h->h_sc->gap <= o.gap_tol) { final_status = IPM_OK; break; }
+    if (it >= o.max_ipm) { final_status = IPM_MAXITER; break; }
+    {
+      ProfScope ps(h, 4);
+      CK(k_prepare(L, h->w, red, h->d_sc, o.cg_tol, o.cg_relative, h->st));
+    }
+    // PCG: chunks of cg_chunk iterations, each kernel returns at once after the stop
+    for (;;) {
+      for (int c = 0; c < o.cg_chunk; ++c) {
+        GSpec k;
+        k.mapin = MAPIN_PCG;
+        k.mapout = MAPOUT_K;
+        k.pcg = true;
+        if ((s = run_g(h, fp32, k)) != IPM_OK) return s;
+        ProfScope ps(h, 3);
+        CK(k_pcg_update(L, h->w, red, h->d_sc, o.max_cg, h->st));
+      }
+      if ((s = read_scalars(h)) != IPM_OK) return s;
+      if (h->h_sc->cg_done) break;
+    }
+    const int ncg = h->h_sc->cg_iter;
+    cg_total += ncg;
+    products += ncg;
+    if (ncg > cg_max) cg_max = ncg;
+    if (h->h_sc->cg_status == 2) { final_status = IPM_NUMERICAL; break; }
+    if (h->h_sc->cg_status == 1) krylov_cap = true;
+    {
+      ProfScope ps(h, 4);
+      CK(k_step_length(L, h->w, red, h->d_sc, o.tau, h->st));
+      CK(k_step_update(L, h->w, red, h->d_sc, o.sigma, o.sigma_slow, h->st));
+    }
+    ++ipm_iters;
+  }
+  if ((s = read_scalars(h)) != IPM_OK) return s;
+  prof_collect(h);
+  h->sigma_ready = true;
+  if (final_status == IPM_OK && krylov_cap) final_status = IPM_KRYLOV_MAXITER;
+  if (res) {
+    res->status = final_status;
+    res->ipm_iters = ipm_iters;
+    res->cg_iters_total = cg_total;
+    res->cg_iters_max = cg_max;
+    res->primal = h->h_sc->primal;
+    res->dual = h->h_sc->dual;
+    res->rel_gap = h->h_sc->gap;
+    res->mu = h->h_sc->mu;
+    res->lambda = h->h_sc->lambda;
+    res->lambda_max = h->h_sc->cmax;
+    res->kkt_products = products;
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (final_status == IPM_NUMERICAL) h->err = "non-finite value or breakdown of positive definiteness";
+  if (final_status == IPM_MAXITER) h->err = "IPM iteration cap reached before gap_tol";
+  return final_status;
+}
+
+ipm_status gapply(sdft_ipm* h, const double* p, double* q) {
+  if (!h || !p || !q) return fail_arg(h, "NULL argument");
+  GSpec g;
+  g.src = p;
+  g.dst = q;
+  ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, g);
+  if (s != IPM_OK) return s;
+  CK(cudaStreamSynchronize(h->st));
+  prof_collect(h);
+  return IPM_OK;
+}
+
+ipm_status kkt_apply(sdft_ipm* h, const double* p, double* q) {
+  if (!h || !p || !q) return fail_arg(h, "NULL argument");
+  if (!h->sigma_ready) return fail_arg(h, "Sigma is not set: call ipm_set_sigma or ipm_solve first");
+  GSpec g;
+  g.mapin = MAPIN_BETA;
+  g.src = p;
+  g.mapout = MAPOUT_K;
+  g.p_in = p;
+  g.q_out = q;
+  ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, g);
+  if (s != IPM_OK) return s;
+  CK(cudaStreamSynchronize(h->st));
+  prof_collect(h);
+  return IPM_OK;
+}
+
+ipm_status precond_apply(sdft_ipm* h, const double* r, double* z) {
+  if (!h || !r || !z) return fail_arg(h, "NULL argument");
+  if (!h->sigma_ready) return fail_arg(h, "Sigma is not set: call ipm_set_sigma or ipm_solve first");
+  {
+    ProfScope ps(h, 4);
+    CK(k_precond(h->lay, h->w, r, z, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  prof_collect(h);
+  return IPM_OK;
+}
+
+ipm_status ipm_set_sigma(sdft_ipm* h, const double* s1, const double* nu1, const double* s2, const double* nu2) {
+  if (!h || !s1 || !nu1 || !s2 || !nu2) return fail_arg(h, "NULL argument");
+  CK(k_sigma_coef(h->lay, s1, nu1, s2, nu2, h->w, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->sigma_ready = true;
+  return IPM_OK;
+}
+
+ipm_status ipm_set_point(sdft_ipm* h, const double* const wv[6]) {
+  if (!h || !wv) return fail_arg(h, "NULL argument");
+  for (int i = 0; i < 6; ++i)
+    if (!wv[i]) return fail_arg(h, "NULL vector in the point");
+  double* dst[6] = {h->w.beta, h->w.z, h->w.s1, h->w.s2, h->w.nu1, h->w.nu2};
+  const size_t bytes = 2 * (size_t)h->lay.H * sizeof(double);
+  for (int i = 0; i < 6; ++i) {
+    CK(cudaMemcpyAsync(dst[i], wv[i], bytes, cudaMemcpyDefault, h->st));
+    CK(k_clear_ghosts(h->lay, dst[i], 1, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  h->point_set = true;
+  return IPM_OK;
+}
+
+ipm_status ipm_get_point(sdft_ipm* h, double* const wv[6]) {
+  if (!h || !wv) return fail_arg(h, "NULL argument");
+  const double* src[6] = {h->w.beta, h->w.z, h->w.s1, h->w.s2, h->w.nu1, h->w.nu2};
+  const size_t bytes = 2 * (size_t)h->lay.H * sizeof(double);
+  for (int i = 0; i < 6; ++i) {
+    if (!wv[i]) return fail_arg(h, "NULL vector in the point");
+    CK(cudaMemcpyAsync(wv[i], src[i], bytes, cudaMemcpyDefault, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return IPM_OK;
+}
+
+ipm_status ipm_get_spectrum(sdft_ipm* h, double* v_half) {
+  if (!h || !v_half) return fail_arg(h, "NULL argument");
+  CK(k_unpack(h->lay, h->w.beta, h->d_tmp, h->st));
+  CK(cudaMemcpyAsync(v_half, h->d_tmp, 2 * (size_t)h->lay.H * sizeof(double), cudaMemcpyDefault, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IPM_OK;
+}
+
+ipm_status ipm_pack_beta(sdft_ipm* h, const double* v_half, double* beta) {
+  if (!h || !v_half || !beta) return fail_arg(h, "NULL argument");
+  CK(k_pack(h->lay, v_half, beta, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IPM_OK;
+}
+
+ipm_status ipm_unpack_beta(sdft_ipm* h, const double* beta, double* v_half) {
+  if (!h || !v_half || !beta) return fail_arg(h, "NULL argument");
+  CK(k_unpack(h->lay, beta, v_half, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return IPM_OK;
+}
+
+ipm_status ipm_profile_enable(sdft_ipm* h, int on) {
+  if (!h) return fail_arg(nullptr, "handle is NULL");
+  prof_collect(h);
+  h->prof = on != 0;
+  for (int k = 0; k < 5; ++k) { h->prof_count[k] = 0; h->prof_ms[k] = 0; }
+  return IPM_OK;
+}
+
+ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms) {
+  if (!h || k < 0 || k >= 5) return fail_arg(h, "bad kernel class");
+  prof_collect(h);
+  if (launches) *launches = h->prof_count[k];
+  if (ms) *ms = h->prof_ms[k];
+  return IPM_OK;
+}
+
+const char* ipm_last_error(const sdft_ipm* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void ipm_destroy(sdft_ipm* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  for (auto& e : h->prof_live) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_sc) cudaFreeHost(h->h_sc);
+  delete h;
+}
+
+}  // extern "C"

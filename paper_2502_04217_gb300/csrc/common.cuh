@@ -1,0 +1,157 @@
+// Shared device/host helpers of the sdft_ipm CUDA library: complex arithmetic,
+// the padded half-spectrum layout of the beta vector, and deterministic
+// block/grid reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdft {
+
+// ---------------------------------------------------------------------------
+// Complex helpers (double2 / float2 as interleaved re, im)
+// ---------------------------------------------------------------------------
+template <typename T> struct cvec;
+template <> struct cvec<double> { using type = double2; };
+template <> struct cvec<float> { using type = float2; };
+
+template <typename V> __device__ __forceinline__ V cmake(decltype(V::x) x, decltype(V::x) y) { V v; v.x = x; v.y = y; return v; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmake<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmake<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cmulconj(V a, V b) {   // a * conj(b)
+  return cmake<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cconj(V a) { return cmake<V>(a.x, -a.y); }
+template <typename V> __device__ __forceinline__ V cmul_i(V a) { return cmake<V>(-a.y, a.x); }      // i * a
+template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return cmake<V>(a.y, -a.x); }     // -i * a
+template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) { return cmake<V>(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// Layout of the half spectrum.  A grid N_0 x ... x N_{d-1} (row-major, last
+// axis contiguous) has H = Hl * M complex half-spectrum slots, Hl = N_l/2 + 1
+// along the halved last axis l and M = N_0 ... N_{d-2} in-plane frequencies.
+// Slot s = kl * M + k' (the halved axis is OUTERMOST), k' = k0 for d = 2 and
+// k' = k0 * N1 + k1 for d = 3.  The beta vector has 2H doubles: beta[2s] and
+// beta[2s+1] are the two real coordinates carried by slot s.
+//
+// Slot classes (the representative rule of the real parametrisation):
+//   INTERIOR  1 <= kl <= N_l/2 - 1: the slot is its pair's representative,
+//             beta = (sqrt2 Re v, sqrt2 Im v);
+//   EDGE_REP  kl in {0, N_l/2}, k' lexicographically before -k': as INTERIOR;
+//   EDGE_SC   kl in {0, N_l/2}, k' = -k' (self-conjugate): beta = (v, ghost);
+//   EDGE_TWIN kl in {0, N_l/2}, the other member of a pair: (ghost, ghost).
+// Ghost coordinates are kept at exactly 0 in every vector.
+// ---------------------------------------------------------------------------
+enum SlotClass { INTERIOR = 0, EDGE_REP = 1, EDGE_SC = 2, EDGE_TWIN = 3 };
+
+struct Layout {
+  int d;          // 1, 2 or 3
+  int N0, N1;     // in-plane lengths (d=3: N0 x N1; d=2: N0, N1 = 1; d=1: 1, 1)
+  int Nl;         // last (halved) axis length
+  int Hl;         // Nl / 2 + 1
+  int M;          // in-plane count
+  long long H;    // number of complex slots = Hl * M
+  long long n;    // number of grid points = Nl * M
+};
+
+__host__ __device__ __forceinline__ int slot_class(const Layout& L, long long s) {
+  // H < 2^31 for every supported grid, so 32-bit division suffices
+  const unsigned su = (unsigned)s, Mu = (unsigned)L.M;
+  const int kl = (int)(su / Mu);
+  if (kl >= 1 && kl <= L.Nl / 2 - 1) return INTERIOR;
+  const int kp = (int)(su - (unsigned)kl * Mu);
+  if (L.d == 1) return EDGE_SC;
+  int k0, k1;
+  if (L.d == 2) { k0 = kp; k1 = 0; }
+  else { k0 = kp / L.N1; k1 = kp - k0 * L.N1; }
+  if (k0 == 0 || 2 * k0 == L.N0) {
+    if (L.d == 2) return EDGE_SC;
+    if (k1 == 0 || 2 * k1 == L.N1) return EDGE_SC;
+    return (2 * k1 < L.N1) ? EDGE_REP : EDGE_TWIN;
+  }
+  return (2 * k0 < L.N0) ? EDGE_REP : EDGE_TWIN;
+}
+
+// true when beta element i (0 <= i < 2H) is a ghost coordinate
+__host__ __device__ __forceinline__ bool is_ghost(const Layout& L, long long i) {
+  int c = slot_class(L, i >> 1);
+  return c == EDGE_TWIN || (c == EDGE_SC && (i & 1));
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: a fixed tree inside each block, then the last
+// block to finish (ticket counter) combines the per-block partials in block
+// order.  The result is bit-identical from run to run for a fixed grid.
+// ---------------------------------------------------------------------------
+enum RedOp { RED_SUM = 0, RED_MAX = 1, RED_MIN = 2 };
+
+__device__ __forceinline__ double red_combine(double a, double b, int op) {
+  return op == RED_SUM ? a + b : (op == RED_MAX ? fmax(a, b) : fmin(a, b));
+}
+__device__ __forceinline__ double red_identity(int op) {
+  return op == RED_SUM ? 0.0 : (op == RED_MAX ? -1.0 / 0.0 : 1.0 / 0.0);
+}
+
+// Reduce NV values over the block; result valid in thread 0.  scratch must hold
+// NV * 32 doubles.  blockDim.x must be a multiple of 32.
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], const int (&ops)[NV], double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = red_combine(v[k], __shfl_down_sync(0xffffffffu, v[k], o), ops[k]);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) scratch[k * 32 + warp] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = lane < nw ? scratch[k * 32 + lane] : red_identity(ops[k]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] = red_combine(v[k], __shfl_down_sync(0xffffffffu, v[k], o), ops[k]);
+    }
+  }
+}
+
+// Store this block's partials; returns true in exactly one block (the last to
+// arrive), in which thread 0 holds the grid-wide result in v on return.
+// partials must hold NV * gridDim.x doubles; counter is reset for the next use.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(double (&v)[NV], const int (&ops)[NV], double* partials,
+                                            unsigned* counter, double* scratch) {
+  __shared__ bool am_last;
+  block_reduce<NV>(v, ops, scratch);
+  const unsigned nb = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[(size_t)k * nb + bid] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == nb - 1);
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  // combine partials in block order, each thread a strided slice, then a block tree
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double acc = red_identity(ops[k]);
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x)
+      acc = red_combine(acc, ((volatile double*)partials)[(size_t)k * nb + b], ops[k]);
+    v[k] = acc;
+  }
+  block_reduce<NV>(v, ops, scratch);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+}  // namespace sdft

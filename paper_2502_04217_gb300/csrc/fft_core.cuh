@@ -1,0 +1,155 @@
+// Shared-memory Stockham FFT on a tile of P pencils (Sec. 3.1: the masked
+// operators are applied with forward / inverse DFTs; this is our own
+// mixed-radix, self-sorting formulation).
+//
+// Tile layout in shared memory: element e of pencil p lives at buf[e * PP + p]
+// (pencil index fastest, PP = P or P + 1 to spread banks), so the threads of a
+// warp, which walk p fastest, touch consecutive words.
+//
+// Each thread owns E complex values per stage (E/R butterflies of radix R).
+// A stage reads all its inputs into registers, synchronises, then writes its
+// outputs into the same buffer (Stockham autosort, decimation in time):
+//     for butterfly j of a stage of radix R after Ns = R_1 ... R_{s-1}:
+//       a_r = x[j + r L/R] * w_L^{(j mod Ns) r L/(Ns R)},   r = 0..R-1
+//       a   = DFT_R(a)
+//       y[(j div Ns) Ns R + (j mod Ns) + r Ns] = a_r
+// Forward transforms use w_L = exp(-2 pi i / L), inverse ones its conjugate;
+// neither is normalised.  Radix 3 (if present) is always the last stage, so Ns
+// is a power of two in every stage.
+#pragma once
+
+#include "common.cuh"
+
+namespace sdft {
+
+constexpr double kSqrtHalf = 0.70710678118654752440;
+constexpr double kSin60 = 0.86602540378443864676;
+
+struct FftPlan {
+  int L;           // transform length
+  int nst;         // number of stages
+  int radix[12];   // stage radices in application order
+};
+
+template <bool INV, typename V> __device__ __forceinline__ void dft2(V* a) {
+  V t = a[0];
+  a[0] = cadd(t, a[1]);
+  a[1] = csub(t, a[1]);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft4(V* a) {
+  V t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+  V t2 = cadd(a[1], a[3]), t3 = csub(a[1], a[3]);
+  V r3 = INV ? cmul_i(t3) : cmul_mi(t3);
+  a[0] = cadd(t0, t2);
+  a[2] = csub(t0, t2);
+  a[1] = cadd(t1, r3);
+  a[3] = csub(t1, r3);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft8(V* a) {
+  using T = decltype(V::x);
+  V e[4] = {a[0], a[2], a[4], a[6]};
+  V o[4] = {a[1], a[3], a[5], a[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  const T h = (T)kSqrtHalf;
+  // o[q] *= w8^q with w8 = exp(-+ 2 pi i / 8)
+  V o1 = INV ? cmake<V>((o[1].x - o[1].y) * h, (o[1].x + o[1].y) * h)
+             : cmake<V>((o[1].x + o[1].y) * h, (o[1].y - o[1].x) * h);
+  V o2 = INV ? cmul_i(o[2]) : cmul_mi(o[2]);
+  V o3 = INV ? cmake<V>((-o[3].x - o[3].y) * h, (o[3].x - o[3].y) * h)
+             : cmake<V>((o[3].y - o[3].x) * h, (-o[3].x - o[3].y) * h);
+  a[0] = cadd(e[0], o[0]);
+  a[4] = csub(e[0], o[0]);
+  a[1] = cadd(e[1], o1);
+  a[5] = csub(e[1], o1);
+  a[2] = cadd(e[2], o2);
+  a[6] = csub(e[2], o2);
+  a[3] = cadd(e[3], o3);
+  a[7] = csub(e[3], o3);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft3(V* a) {
+  using T = decltype(V::x);
+  const T s = INV ? (T)kSin60 : -(T)kSin60;
+  V t1 = cadd(a[1], a[2]);
+  V d = csub(a[1], a[2]);
+  V m = cmake<V>(a[0].x - (T)0.5 * t1.x, a[0].y - (T)0.5 * t1.y);
+  V isd = cmake<V>(-s * d.y, s * d.x);      // i * s * d
+  a[0] = cadd(a[0], t1);
+  a[1] = cadd(m, isd);
+  a[2] = csub(m, isd);
+}
+
+template <int R, bool INV, typename V> __device__ __forceinline__ void dft_r(V* a) {
+  if constexpr (R == 2) dft2<INV>(a);
+  else if constexpr (R == 3) dft3<INV>(a);
+  else if constexpr (R == 4) dft4<INV>(a);
+  else dft8<INV>(a);
+}
+
+// One Stockham stage of radix R over the tile.  nwork = P * L / E threads
+// carry the work (threads beyond that only join the barriers).
+template <int E, int R, bool INV, typename V>
+__device__ __forceinline__ void fft_stage(V* buf, int L, int lgNs, int lgP, int PP, const V* __restrict__ tw,
+                                          int tid, int nwork) {
+  constexpr int B = E / R;
+  const int Ns = 1 << lgNs;
+  const int LR = L / R;
+  const int twstride = L / (Ns * R);
+  V a[B][R];
+  const bool active = tid < nwork;
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int w = tid + b * nwork;
+      const int p = w & ((1 << lgP) - 1), j = w >> lgP, k = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        V v = buf[(j + r * LR) * PP + p];
+        if (r > 0 && Ns > 1) {
+          V t = __ldg(&tw[k * r * twstride]);
+          v = INV ? cmulconj(v, t) : cmul(v, t);
+        }
+        a[b][r] = v;
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int w = tid + b * nwork;
+      const int p = w & ((1 << lgP) - 1), j = w >> lgP, k = j & (Ns - 1);
+      dft_r<R, INV>(a[b]);
+      const int base = ((j >> lgNs) << lgNs) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[(base + r * Ns) * PP + p] = a[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full transform of the P pencils held in buf (length plan.L each), in place.
+template <int E, bool INV, typename V>
+__device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, int PP, const V* __restrict__ tw,
+                                         int tid, int nwork) {
+  int lgNs = 0;
+  for (int s = 0; s < plan.nst; ++s) {
+    const int R = plan.radix[s];
+    if constexpr (E % 8 == 0) {
+      if (R == 8) fft_stage<E, 8, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
+    }
+    if constexpr (E % 4 == 0) {
+      if (R == 4) fft_stage<E, 4, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
+    }
+    if (R == 2) fft_stage<E, 2, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
+    if constexpr (E % 3 == 0) {
+      if (R == 3) fft_stage<E, 3, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
+    }
+    lgNs += (R == 8) ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));   // radix 3 is last
+  }
+}
+
+}  // namespace sdft

@@ -1,0 +1,78 @@
+// Internal declarations shared by the kernels and the C-ABI layer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "fft_core.cuh"
+
+namespace sdft {
+
+// Device-resident scalars of one solve.  Written by the last block of the
+// reduction kernels, read by later kernels, copied to the host only at the
+// points where the host decides (IPM convergence, PCG chunk boundaries).
+struct DevScalars {
+  // PCG
+  double rho;        // r^T z of the current iterate
+  double cg_stop;    // stop when sqrt(rho) <= cg_stop
+  double pq;         // p^T K p of the last product
+  double alpha_cg;   // rho / p^T K p
+  double beta_cg;    // rho_new / rho (0 before the first product)
+  int cg_done;       // 1 once PCG has stopped (kernels then return at once)
+  int cg_iter;       // PCG iterations of the current solve
+  int cg_status;     // 0 ok, 1 hit max_cg, 2 non-finite value
+  int pad0;
+  // IPM
+  double lambda;     // penalty
+  double mu;         // duality measure (nu1^T s1 + nu2^T s2) / 2n
+  double sigma;      // centring parameter for the next direction
+  double alpha;      // last IPM step
+  double primal, dual, gap;
+  double yy;         // ||b||^2 over observed samples
+  double cmax;       // ||M_perp^T b||_inf
+  double theta2;     // ||b - M_perp beta||^2
+  double corr;       // ||M_perp^T (b - M_perp beta)||_inf
+  double l1;         // ||beta||_1
+  double nobs;       // number of observed samples
+};
+
+enum MapIn { MAPIN_NONE = 0, MAPIN_BETA = 1, MAPIN_PCG = 2 };
+enum MapOut { MAPOUT_NONE = 0, MAPOUT_BETA = 1, MAPOUT_K = 2 };
+
+// Arguments of one FFT pass kernel.  Vectors in the beta layout are doubles
+// (2H per block); the work buffer holds H complex values of the pass type.
+struct PassArgs {
+  Layout lay;
+  FftPlan plan;          // length L (row/column passes) or h = Nl/2 (middle pass)
+  int lgP, PP;           // pencils per tile = 1 << lgP, smem pencil stride
+  int nwork;             // threads carrying FFT work = P * L / E
+  long long npencils;    // pencils of the pass (row: number of rows; middle: M)
+  const void* tw;        // roots of unity for plan.L (pass type)
+  const void* twN;       // middle pass: roots of unity for Nl
+  void* buf;             // in-place complex work buffer (H values)
+  int mapin, mapout;
+  const double* src;     // MAPIN_BETA: beta-layout vector (2H)
+  double* p;             // MAPIN_PCG / MAPOUT_K: p (4H: beta block, z block)
+  const double* zv;      // MAPIN_PCG: preconditioned residual (4H)
+  double* dst;           // MAPOUT_BETA: output beta-layout vector (2H)
+  double out_scale;      // MAPOUT_BETA scale
+  const double* lam1;    // MAPOUT_K: Lambda1, Lambda2 (2H each)
+  const double* lam2;
+  double* q;             // MAPOUT_K: K p (4H)
+  int pcg_mode;          // MAPOUT_K inside PCG: form alpha = rho / p^T q
+  int check_done;        // return at once when sc->cg_done
+  const uint32_t* maskw; // middle pass: bit-packed mask, word (xl/32)*M + x'
+  double inv_n;          // 1/n, applied with the mask
+  const double* yreal;   // middle pass "from real": the signal on the grid (row-major)
+  int from_real;         // middle pass: R2C only, of yreal * mask
+  double* partials;
+  unsigned* counter;
+  DevScalars* sc;
+};
+
+// Launchers (fft_passes.cu).  `pass_kind`: 0 row, 1 column, 2 middle.
+cudaError_t launch_pass(int pass_kind, bool inv, bool fp32, int E, const PassArgs& a, int threads,
+                        size_t smem, dim3 grid, cudaStream_t st);
+
+}  // namespace sdft

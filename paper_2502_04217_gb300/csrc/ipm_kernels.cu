@@ -1,0 +1,439 @@
+// Elementwise and reduction kernels of the interior-point method (FP64).
+//
+// Vectors use the beta layout of common.cuh (2H doubles, ghost coordinates
+// held at 0 and skipped by every reduction).  Two-block vectors (x, r, z, p, q
+// of the condensed system) are [beta block | z block], 4H doubles.
+#include "internal.h"
+#include "kernels.h"
+
+namespace sdft {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) pack_mask_kernel(const uint8_t* __restrict__ mask, uint32_t* __restrict__ words,
+                                                             int Nl, int M) {
+  // one thread per output word: 32 consecutive samples of one row x'
+  const long long nw = (long long)((Nl + 31) / 32) * M;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw; i += (long long)gridDim.x * blockDim.x) {
+    const int blk = (int)(i / M), xp = (int)(i - (long long)blk * M);
+    uint32_t w = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int xl = blk * 32 + b;
+      if (xl < Nl && mask[(size_t)xp * Nl + xl]) w |= (1u << b);
+    }
+    words[i] = w;
+  }
+}
+
+// ||b||^2 over observed samples, and the count of observed samples
+__global__ void __launch_bounds__(kThreads) observed_norm_kernel(const double* __restrict__ y, const uint8_t* __restrict__ mask,
+                                                                 long long n, double* partials, unsigned* counter,
+                                                                 DevScalars* sc) {
+  __shared__ double scratch[64];
+  double v[2] = {0.0, 0.0};
+  const int ops[2] = {RED_SUM, RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (mask[i]) { v[0] += y[i] * y[i]; v[1] += 1.0; }
+  }
+  if (grid_reduce<2>(v, ops, partials, counter, scratch) && threadIdx.x == 0) { sc->yy = v[0]; sc->nobs = v[1]; }
+}
+
+// ||c||_inf for lambda_max; sets lambda (relative or absolute) and the start point scale
+__global__ void __launch_bounds__(kThreads) cmax_kernel(const double* __restrict__ c, long long n2, double lam_in, int relative,
+                                                        double* partials, unsigned* counter, DevScalars* sc) {
+  __shared__ double scratch[32];
+  double v[1] = {0.0};
+  const int ops[1] = {RED_MAX};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
+    v[0] = fmax(v[0], fabs(c[i]));
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    sc->cmax = v[0];
+    sc->lambda = relative ? lam_in * v[0] : lam_in;
+  }
+}
+
+// Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu
+__global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double* beta, double* z, double* s1, double* s2,
+                                                              double* nu1, double* nu2, double* partials, unsigned* counter,
+                                                              DevScalars* sc, double sigma0) {
+  __shared__ double scratch[32];
+  const double zeta = fmax(1.0, sc->cmax), hl = 0.5 * sc->lambda;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  const long long n2 = 2 * lay.H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const bool gh = is_ghost(lay, i);
+    beta[i] = 0.0;
+    z[i] = gh ? 0.0 : zeta;
+    s1[i] = gh ? 0.0 : zeta;
+    s2[i] = gh ? 0.0 : zeta;
+    nu1[i] = gh ? 0.0 : hl;
+    nu2[i] = gh ? 0.0 : hl;
+    if (!gh) v[0] += hl * zeta + hl * zeta;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    sc->mu = v[0] / (2.0 * (double)lay.n);
+    sc->sigma = sigma0;
+    sc->alpha = 0.0;
+  }
+}
+
+// mu = (nu1^T s1 + nu2^T s2) / 2n at a given point (after ipm_set_point)
+__global__ void __launch_bounds__(kThreads) mu_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
+                                                      DevScalars* sc, double sigma0) {
+  __shared__ double scratch[32];
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  const long long n2 = 2 * lay.H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
+    if (!is_ghost(lay, i)) v[0] += w.nu1[i] * w.s1[i] + w.nu2[i] * w.s2[i];
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    sc->mu = v[0] / (2.0 * (double)lay.n);
+    sc->sigma = sigma0;
+    sc->alpha = 0.0;
+  }
+}
+
+// Duality-gap certificate at beta from G beta and c = M_perp^T b:
+//   ||theta||^2 = ||b||^2 - 2 c^T beta + beta^T G beta,  b^T theta = ||b||^2 - c^T beta,
+//   ||M_perp^T theta||_inf = ||c - G beta||_inf,  P = ||theta||^2/2 + lambda ||beta||_1,
+//   D = s b^T theta - s^2 ||theta||^2 / 2 with s = min(1, lambda / ||M_perp^T theta||_inf).
+__global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, const double* __restrict__ beta,
+                                                               const double* __restrict__ Gb, const double* __restrict__ c,
+                                                               double* partials, unsigned* counter, DevScalars* sc) {
+  __shared__ double scratch[4 * 32];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int ops[4] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double b = beta[i], g = Gb[i], ci = c[i];
+    v[0] += ci * b;
+    v[1] += b * g;
+    v[2] += fabs(b);
+    v[3] = fmax(v[3], fabs(ci - g));
+  }
+  if (grid_reduce<4>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double lam = sc->lambda;
+    const double th2 = fmax(sc->yy - 2.0 * v[0] + v[1], 0.0);
+    const double bth = sc->yy - v[0];
+    const double P = 0.5 * th2 + lam * v[2];
+    const double s = (v[3] <= lam) ? 1.0 : lam / v[3];
+    const double D = s * bth - 0.5 * s * s * th2;
+    sc->theta2 = th2;
+    sc->corr = v[3];
+    sc->l1 = v[2];
+    sc->primal = P;
+    sc->dual = D;
+    sc->gap = (P - D) / fmax(1.0, fabs(P));
+  }
+}
+
+// Barrier diagonals, preconditioner coefficients, condensed right-hand side and
+// PCG start (x = 0, r = rhs, z = P^{-1} r, p = z, rho = r^T z).
+__global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
+                                                           DevScalars* sc, double cg_tol, int cg_relative) {
+  __shared__ double scratch[32];
+  const long long n2 = 2 * lay.H;
+  const double lam = sc->lambda, smu = sc->sigma * sc->mu;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, rb = 0, rc = 0, zb = 0, zz = 0;
+    if (!is_ghost(lay, i)) {
+      const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
+      const double is1 = 1.0 / s1, is2 = 1.0 / s2;
+      const double S1 = n1 * is1, S2 = n2_ * is2;              // Sigma_i = S_i^{-1} V_i
+      const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
+      const double r_z = lam - n1 - n2_;
+      const double r_p1 = z + b - s1, r_p2 = z - b - s2;
+      const double rc1s = n1 - smu * is1;                       // r_c1 / s1 = (s1 nu1 - sigma mu) / s1
+      const double rc2s = n2_ - smu * is2;
+      rb = -r_d - rc1s - S1 * r_p1 + rc2s + S2 * r_p2;
+      rc = -r_z - rc1s - S1 * r_p1 - rc2s - S2 * r_p2;
+      l1 = S1 + S2;
+      l2 = S1 - S2;
+      const double iD = 1.0 / (S1 + S2 + 4.0 * S1 * S2);       // D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2
+      pa = l1 * iD;
+      pb = l2 * iD;
+      pc = (1.0 + l1) * iD;
+      zb = pa * rb - pb * rc;
+      zz = -pb * rb + pc * rc;
+    }
+    w.lam1[i] = l1; w.lam2[i] = l2;
+    w.pa[i] = pa; w.pb[i] = pb; w.pc[i] = pc;
+    w.x[i] = 0.0; w.x[n2 + i] = 0.0;
+    w.r[i] = rb; w.r[n2 + i] = rc;
+    w.zv[i] = zb; w.zv[n2 + i] = zz;
+    w.p[i] = zb; w.p[n2 + i] = zz;
+    v[0] += rb * zb + rc * zz;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double rho = v[0];
+    sc->rho = rho;
+    sc->beta_cg = 0.0;
+    sc->cg_iter = 0;
+    sc->cg_status = 0;
+    sc->cg_stop = cg_relative ? cg_tol * sqrt(fmax(rho, 0.0)) : cg_tol;
+    sc->cg_done = (sqrt(fmax(rho, 0.0)) <= sc->cg_stop) ? 1 : 0;
+    if (!isfinite(rho)) { sc->cg_status = 2; sc->cg_done = 1; }
+  }
+}
+
+// Preconditioner coefficients only (for precond_apply / kkt_apply on a given Sigma)
+__global__ void __launch_bounds__(kThreads) sigma_coef_kernel(Layout lay, const double* s1, const double* nu1, const double* s2,
+                                                              const double* nu2, double* lam1, double* lam2, double* pa,
+                                                              double* pb, double* pc) {
+  const long long n2 = 2 * lay.H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    double l1 = 0, l2 = 0, a = 0, b = 0, c = 0;
+    if (!is_ghost(lay, i)) {
+      const double S1 = nu1[i] / s1[i], S2 = nu2[i] / s2[i];
+      l1 = S1 + S2;
+      l2 = S1 - S2;
+      const double iD = 1.0 / (S1 + S2 + 4.0 * S1 * S2);
+      a = l1 * iD;
+      b = l2 * iD;
+      c = (1.0 + l1) * iD;
+    }
+    lam1[i] = l1; lam2[i] = l2; pa[i] = a; pb[i] = b; pc[i] = c;
+  }
+}
+
+// z = P^{-1} r  (Eq. (invprecond1): [L1/D, -L2/D; -L2/D, (1+L1)/D])
+__global__ void __launch_bounds__(kThreads) precond_kernel(long long n2, const double* __restrict__ pa, const double* __restrict__ pb,
+                                                           const double* __restrict__ pc, const double* __restrict__ r,
+                                                           double* __restrict__ z) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double rb = r[i], rz = r[n2 + i], a = pa[i], b = pb[i], c = pc[i];
+    z[i] = a * rb - b * rz;
+    z[n2 + i] = -b * rb + c * rz;
+  }
+}
+
+// One PCG update after q = K p: x += alpha p, r -= alpha q, z = P^{-1} r, rho' = r^T z,
+// beta_cg = rho'/rho, stop test.
+__global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
+                                                              DevScalars* sc, int max_cg) {
+  __shared__ double scratch[32];
+  if (sc->cg_done) return;
+  const double alpha = sc->alpha_cg;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double pbv = w.p[i], pzv = w.p[n2 + i];
+    w.x[i] += alpha * pbv;
+    w.x[n2 + i] += alpha * pzv;
+    const double rb = w.r[i] - alpha * w.q[i];
+    const double rz = w.r[n2 + i] - alpha * w.q[n2 + i];
+    w.r[i] = rb;
+    w.r[n2 + i] = rz;
+    const double a = w.pa[i], b = w.pb[i], c = w.pc[i];
+    const double zb = a * rb - b * rz, zz = -b * rb + c * rz;
+    w.zv[i] = zb;
+    w.zv[n2 + i] = zz;
+    v[0] += rb * zb + rz * zz;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double rho_new = v[0];
+    sc->beta_cg = rho_new / sc->rho;
+    sc->rho = rho_new;
+    sc->cg_iter += 1;
+    if (!isfinite(rho_new)) { sc->cg_status = 2; sc->cg_done = 1; }
+    else if (sqrt(fmax(rho_new, 0.0)) <= sc->cg_stop) sc->cg_done = 1;
+    else if (sc->cg_iter >= max_cg) { sc->cg_status = 1; sc->cg_done = 1; }
+  }
+}
+
+// Newton direction of the eliminated variables (same arithmetic in both step kernels)
+struct Dir { double ds1, ds2, dn1, dn2; };
+__device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long long n2, double smu) {
+  const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
+  const double db = w.x[i], dz = w.x[n2 + i];
+  const double is1 = 1.0 / s1, is2 = 1.0 / s2;
+  Dir d;
+  d.ds1 = dz + db + (z + b - s1);
+  d.ds2 = dz - db + (z - b - s2);
+  d.dn1 = -(n1 - smu * is1) - (n1 * is1) * d.ds1;
+  d.dn2 = -(n2_ - smu * is2) - (n2_ * is2) * d.ds2;
+  return d;
+}
+
+// Largest step keeping (s, nu) >= 0; alpha = min(1, tau * alpha_max)
+__global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
+                                                               DevScalars* sc, double tau) {
+  __shared__ double scratch[32];
+  const long long n2 = 2 * lay.H;
+  const double smu = sc->sigma * sc->mu;
+  double v[1] = {1.0 / 0.0};
+  const int ops[1] = {RED_MIN};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    if (is_ghost(lay, i)) continue;
+    const Dir d = direction(w, i, n2, smu);
+    if (d.ds1 < 0) v[0] = fmin(v[0], -w.s1[i] / d.ds1);
+    if (d.ds2 < 0) v[0] = fmin(v[0], -w.s2[i] / d.ds2);
+    if (d.dn1 < 0) v[0] = fmin(v[0], -w.nu1[i] / d.dn1);
+    if (d.dn2 < 0) v[0] = fmin(v[0], -w.nu2[i] / d.dn2);
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) sc->alpha = fmin(1.0, tau * v[0]);
+}
+
+// Take the step and form the new duality measure mu
+__global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
+                                                               DevScalars* sc, double sigma0, double sigma_slow) {
+  __shared__ double scratch[32];
+  const long long n2 = 2 * lay.H;
+  const double smu = sc->sigma * sc->mu, alpha = sc->alpha;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    if (is_ghost(lay, i)) continue;
+    const Dir d = direction(w, i, n2, smu);
+    w.beta[i] += alpha * w.x[i];
+    w.z[i] += alpha * w.x[n2 + i];
+    const double s1 = w.s1[i] + alpha * d.ds1, s2 = w.s2[i] + alpha * d.ds2;
+    const double n1 = w.nu1[i] + alpha * d.dn1, n2_ = w.nu2[i] + alpha * d.dn2;
+    w.s1[i] = s1; w.s2[i] = s2; w.nu1[i] = n1; w.nu2[i] = n2_;
+    v[0] += n1 * s1 + n2_ * s2;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    sc->mu = v[0] / (2.0 * (double)lay.n);
+    sc->sigma = (alpha < 0.1) ? sigma_slow : sigma0;
+  }
+}
+
+// Canonical half spectrum (row-major, last axis halved, interleaved re/im) <-> beta layout.
+// unpack: v = B^H beta restricted to the half spectrum, twins filled with conj(rep).
+__global__ void __launch_bounds__(kThreads) unpack_kernel(Layout lay, const double* __restrict__ beta, double* __restrict__ vh) {
+  const long long H = lay.H;
+  const double rh = 0.70710678118654752440;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < H; t += (long long)gridDim.x * blockDim.x) {
+    // t = canonical index: k' * Hl + kl
+    const long long kp = t / lay.Hl;
+    const int kl = (int)(t - kp * lay.Hl);
+    const long long s = (long long)kl * lay.M + kp;
+    const int cls = slot_class(lay, s);
+    double re = 0, im = 0;
+    if (cls == INTERIOR || cls == EDGE_REP) { re = beta[2 * s] * rh; im = beta[2 * s + 1] * rh; }
+    else if (cls == EDGE_SC) { re = beta[2 * s]; }
+    else {
+      // twin: conj of the representative at -k' on the same edge plane
+      int k0 = 0, k1 = 0;
+      if (lay.d == 2) k0 = (int)kp;
+      else { k0 = (int)(kp / lay.N1); k1 = (int)(kp - (long long)k0 * lay.N1); }
+      const int m0 = (lay.N0 - k0) % lay.N0;
+      const int m1 = (lay.d == 3) ? (lay.N1 - k1) % lay.N1 : 0;
+      const long long kpr = (lay.d == 3) ? (long long)m0 * lay.N1 + m1 : m0;
+      const long long sr = (long long)kl * lay.M + kpr;
+      re = beta[2 * sr] * rh;
+      im = -beta[2 * sr + 1] * rh;
+    }
+    vh[2 * t] = re;
+    vh[2 * t + 1] = im;
+  }
+}
+
+// pack: beta = B v from the canonical half spectrum (twin slots of vh ignored)
+__global__ void __launch_bounds__(kThreads) pack_kernel(Layout lay, const double* __restrict__ vh, double* __restrict__ beta) {
+  const long long H = lay.H;
+  const double r2 = 1.41421356237309504880;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < H; s += (long long)gridDim.x * blockDim.x) {
+    const int kl = (int)(s / lay.M);
+    const long long kp = s - (long long)kl * lay.M;
+    const long long t = kp * lay.Hl + kl;
+    const int cls = slot_class(lay, s);
+    double b0 = 0, b1 = 0;
+    if (cls == INTERIOR || cls == EDGE_REP) { b0 = r2 * vh[2 * t]; b1 = r2 * vh[2 * t + 1]; }
+    else if (cls == EDGE_SC) { b0 = vh[2 * t]; }
+    beta[2 * s] = b0;
+    beta[2 * s + 1] = b1;
+  }
+}
+
+// ghost-aware copy of a beta-layout vector with ghosts forced to 0
+__global__ void __launch_bounds__(kThreads) clear_ghosts_kernel(Layout lay, double* v, int blocks) {
+  const long long n2 = 2 * lay.H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    if (is_ghost(lay, i))
+      for (int b = 0; b < blocks; ++b) v[b * n2 + i] = 0.0;
+  }
+}
+
+int grid_for(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  const long long cap = 152 * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, cudaStream_t st) {
+  const long long nw = (long long)((Nl + 31) / 32) * M;
+  pack_mask_kernel<<<grid_for(nw), kThreads, 0, st>>>(mask, words, Nl, M);
+  return cudaGetLastError();
+}
+cudaError_t k_observed_norm(const double* y, const uint8_t* mask, long long n, Reduce red, DevScalars* sc, cudaStream_t st) {
+  observed_norm_kernel<<<grid_for(n), kThreads, 0, st>>>(y, mask, n, red.partials, red.counter, sc);
+  return cudaGetLastError();
+}
+cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Reduce red, DevScalars* sc, cudaStream_t st) {
+  cmax_kernel<<<grid_for(n2), kThreads, 0, st>>>(c, n2, lam, relative, red.partials, red.counter, sc);
+  return cudaGetLastError();
+}
+cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st) {
+  init_point_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, red.partials,
+                                                              red.counter, sc, sigma0);
+  return cudaGetLastError();
+}
+cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st) {
+  mu_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0);
+  return cudaGetLastError();
+}
+cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
+                          DevScalars* sc, cudaStream_t st) {
+  certificate_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, beta, Gb, c, red.partials, red.counter, sc);
+  return cudaGetLastError();
+}
+cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
+                      cudaStream_t st) {
+  prepare_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, cg_tol, cg_relative);
+  return cudaGetLastError();
+}
+cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
+                         IpmVectors w, cudaStream_t st) {
+  sigma_coef_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc);
+  return cudaGetLastError();
+}
+cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, cudaStream_t st) {
+  precond_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w.pa, w.pb, w.pc, r, z);
+  return cudaGetLastError();
+}
+cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, cudaStream_t st) {
+  pcg_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, max_cg);
+  return cudaGetLastError();
+}
+cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st) {
+  step_length_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, tau);
+  return cudaGetLastError();
+}
+cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
+                          cudaStream_t st) {
+  step_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0, sigma_slow);
+  return cudaGetLastError();
+}
+cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, cudaStream_t st) {
+  unpack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, beta, vh);
+  return cudaGetLastError();
+}
+cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, cudaStream_t st) {
+  pack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, vh, beta);
+  return cudaGetLastError();
+}
+cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, cudaStream_t st) {
+  clear_ghosts_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, v, blocks);
+  return cudaGetLastError();
+}
+
+}  // namespace sdft

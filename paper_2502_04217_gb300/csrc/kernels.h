@@ -1,0 +1,46 @@
+// Launchers of the IPM kernels (ipm_kernels.cu), used by the C-ABI layer.
+#pragma once
+
+#include "internal.h"
+
+namespace sdft {
+
+// Device vectors of one problem, all in the beta layout (2H doubles per block).
+struct IpmVectors {
+  double *beta, *z, *s1, *s2, *nu1, *nu2;     // IPM iterate
+  double *c;                                  // M_perp^T b
+  double *Gb;                                 // G beta at the current iterate
+  double *lam1, *lam2;                        // Lambda1, Lambda2 of K
+  double *pa, *pb, *pc;                       // P^{-1} = [pa, -pb; -pb, pc] per element
+  double *x, *r, *zv, *p, *q;                 // PCG vectors, 2 blocks each (4H)
+};
+
+// grid size used by every elementwise kernel (also sizes the partials buffer)
+constexpr int kMaxElementwiseBlocks = 152 * 8;
+
+struct Reduce {
+  double* partials;
+  unsigned* counter;
+};
+
+cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, cudaStream_t st);
+cudaError_t k_observed_norm(const double* y, const uint8_t* mask, long long n, Reduce red, DevScalars* sc, cudaStream_t st);
+cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Reduce red, DevScalars* sc, cudaStream_t st);
+cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st);
+cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st);
+cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
+                          DevScalars* sc, cudaStream_t st);
+cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
+                      cudaStream_t st);
+cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
+                         IpmVectors w, cudaStream_t st);
+cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, cudaStream_t st);
+cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, cudaStream_t st);
+cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st);
+cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
+                          cudaStream_t st);
+cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, cudaStream_t st);
+cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, cudaStream_t st);
+cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, cudaStream_t st);
+
+}  // namespace sdft

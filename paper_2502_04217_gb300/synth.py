@@ -58,7 +58,7 @@ def _sparse_signal(rng, dims, k, amp="normal"):
     else:
         amps = rng.standard_normal(k) + 1j * rng.standard_normal(k)
     spec.reshape(-1)[freqs] = amps
-    x = np.fft.irfftn(spec, s=dims, norm="ortho")
+    x = np.fft.irfftn(spec, s=dims, axes=tuple(range(len(dims))), norm="ortho")
     return x, freqs, amps
 
 

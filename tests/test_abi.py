@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every entry point declared in include/ (no GPU).
+
+Only argument checking is exercised here: no call in this file launches a kernel.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2502_04217_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sdft_ipm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        from paper_2502_04217_gb300 import build
+        build.build()
+    return binding.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while")))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ipm_create", "ipm_solve", "kkt_apply", "precond_apply", "ipm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in binding._SIGNATURES, name
+
+
+def test_default_options(lib):
+    o = binding.default_options()
+    assert o.precision == binding.IPM_FP64
+    assert o.gap_tol == 1e-6 and o.cg_relative == 1 and o.tau == 0.995 and o.sigma == 0.1
+
+
+@pytest.mark.parametrize("dims,why", [((7,), "odd"), ((10,), "factor 5"), ((4, 4, 4, 4), "ndim"),
+                                      ((1024,), "too long"), ((0,), "empty")])
+def test_create_rejects_bad_grids_without_gpu_work(lib, dims, why):
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    dummy = (ctypes.c_double * 4)()
+    st = lib.ipm_create(ctypes.byref(h), len(dims), d, ctypes.cast(dummy, ctypes.c_void_p),
+                        ctypes.cast(dummy, ctypes.c_void_p), 1.0, None, None)
+    assert st == binding.IPM_ERR_ARG, why
+    assert h.value is None
+    assert binding.ipm_last_error(None)
+
+
+def test_create_rejects_bad_options(lib):
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * 1)(8)
+    dummy = (ctypes.c_double * 8)()
+    o = binding.default_options(tau=1.5)
+    st = lib.ipm_create(ctypes.byref(h), 1, d, ctypes.cast(dummy, ctypes.c_void_p),
+                        ctypes.cast(dummy, ctypes.c_void_p), 1.0, ctypes.byref(o), None)
+    assert st == binding.IPM_ERR_ARG and "tau" in binding.ipm_last_error(None)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.ipm_solve(None, None) == binding.IPM_ERR_ARG
+    assert lib.kkt_apply(None, None, None) == binding.IPM_ERR_ARG
+    assert lib.precond_apply(None, None, None) == binding.IPM_ERR_ARG
+    lib.ipm_destroy(None)

@@ -1,0 +1,217 @@
+"""CUDA path against the CPU oracle, element by element (needs a GB300).
+
+Tolerances (derived from the arithmetic): an FFT of length n in precision eps
+has a relative 2-norm error of a few eps log2 n.  G = M_perp^T M_perp is an
+orthogonal projector, so ||G p|| <= ||p|| and we bound the max-norm error of
+G p by tol * ||p||_2 with tol = 1e-12 in FP64 (eps = 1.1e-16, log2 n <= 27) and
+tol = 5e-5 in FP32 (eps = 6e-8).  The diagonal terms of K and P^{-1} are FP64
+products, compared relative to the magnitude of their terms.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import ipm as oipm
+from oracle.lasso import Problem
+from paper_2502_04217_gb300 import binding
+from paper_2502_04217_gb300.synth import make_problem
+
+from layout import ghost_mask, lib_to_half, oracle_to_half, oracle_to_lib, to_device
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(8,), (12,), (96,), (256,), (512,),
+         (8, 6), (16, 12), (48, 64), (64, 48), (96, 32),
+         (4, 6, 8), (8, 8, 8), (16, 12, 8), (12, 16, 24), (32, 24, 16)]
+
+
+def _workload(dims, seed=0, missing=0.15):
+    w = make_problem("custom", dims=dims, missing=missing, seed=seed)
+    return w
+
+
+def _handle(w, precision=binding.IPM_FP64, lam_rel=0.1, **opt):
+    o = binding.default_options(precision=precision, lambda_relative=1, **opt)
+    return binding.ipm_create(w.dims, np.ascontiguousarray(w.mask), np.ascontiguousarray(w.y), lam_rel, o)
+
+
+def _oracle(w, lam):
+    return Problem(w.dims, w.mask.astype(bool), w.y, lam)
+
+
+def _interior(n, rng):
+    return (rng.uniform(0.05, 3.0, n), rng.uniform(0.05, 3.0, n), rng.uniform(0.05, 3.0, n),
+            rng.uniform(0.05, 3.0, n))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    binding.load()
+
+
+@pytest.mark.parametrize("dims", SIZES)
+def test_pack_unpack_roundtrip(dims):
+    w = _workload(dims)
+    h = _handle(w)
+    try:
+        n = int(np.prod(dims))
+        beta = np.random.default_rng(1).standard_normal(n)
+        lib = oracle_to_lib(h, beta, dims)
+        assert np.abs(lib_to_half(h, lib) - oracle_to_half(beta, dims)).max() < 1e-15 * 8
+        assert np.count_nonzero(~ghost_mask(h, dims)) == n       # exactly n LASSO coordinates
+    finally:
+        binding.ipm_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+@pytest.mark.parametrize("dims", SIZES)
+def test_gapply_matches_oracle(dims, precision):
+    w = _workload(dims, seed=2)
+    h = _handle(w, precision)
+    try:
+        n = int(np.prod(dims))
+        prob = _oracle(w, 1.0)
+        beta = np.random.default_rng(3).standard_normal(n)
+        p = oracle_to_lib(h, beta, dims)
+        q = torch.empty_like(p)
+        binding.gapply(h, p, q)
+        ref = oracle_to_half(prob.G(beta), dims)
+        got = lib_to_half(h, q)
+        tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * np.linalg.norm(beta)
+        assert np.abs(got - ref).max() < tol
+        assert np.all(q.cpu().numpy()[ghost_mask(h, dims)] == 0.0)
+    finally:
+        binding.ipm_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+@pytest.mark.parametrize("dims", [(256,), (48, 64), (16, 12, 8), (32, 24, 16)])
+def test_kkt_and_precond_match_oracle(dims, precision):
+    w = _workload(dims, seed=4)
+    h = _handle(w, precision)
+    try:
+        n = int(np.prod(dims))
+        prob = _oracle(w, 1.0)
+        rng = np.random.default_rng(5)
+        s1, nu1, s2, nu2 = _interior(n, rng)
+        binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+        S1, S2 = oipm.sigmas(s1, nu1, s2, nu2)
+        pb, pz = rng.standard_normal(n), rng.standard_normal(n)
+        p = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
+        q = torch.empty_like(p)
+        binding.kkt_apply(h, p, q)
+        qb, qz = oipm.K_apply(prob.G, S1, S2, pb, pz)
+        H2 = p.numel() // 2
+        scale = np.linalg.norm(np.concatenate([pb, pz])) * (1 + (S1 + S2).max())
+        tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * scale
+        assert np.abs(lib_to_half(h, q[:H2]) - oracle_to_half(qb, dims)).max() < tol
+        assert np.abs(lib_to_half(h, q[H2:]) - oracle_to_half(qz, dims)).max() < 1e-13 * scale
+        # preconditioner: always FP64
+        z = torch.empty_like(p)
+        binding.precond_apply(h, p, z)
+        zb, zz = oipm.Pinv_apply(S1, S2, pb, pz)
+        zs = np.abs(np.concatenate([zb, zz])).max()
+        assert np.abs(lib_to_half(h, z[:H2]) - oracle_to_half(zb, dims)).max() < 1e-14 * max(1, zs)
+        assert np.abs(lib_to_half(h, z[H2:]) - oracle_to_half(zz, dims)).max() < 1e-14 * max(1, zs)
+        # Eq. (precond1): P^{-1} K [0; u] = [0; u]
+        u = torch.cat([torch.zeros_like(p[:H2]), oracle_to_lib(h, rng.standard_normal(n), dims)])
+        Ku = torch.empty_like(u)
+        binding.kkt_apply(h, u, Ku)
+        PKu = torch.empty_like(u)
+        binding.precond_apply(h, Ku, PKu)
+        assert torch.abs(PKu - u).max().item() < 1e-10 * (1 + (S1 + S2).max())
+    finally:
+        binding.ipm_destroy(h)
+
+
+def _solve_both(w, lam_rel, gap_tol, precision=binding.IPM_FP64):
+    h = _handle(w, precision, lam_rel=lam_rel, gap_tol=gap_tol)
+    try:
+        res = binding.ipm_solve(h)
+        H, n = binding.ipm_sizes(h)
+        v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+        binding.ipm_get_spectrum(h, v)
+        v = v.cpu().numpy()
+        beta_lib = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+        binding.ipm_get_point(h, [beta_lib] + [torch.empty_like(beta_lib) for _ in range(5)])
+    finally:
+        binding.ipm_destroy(h)
+    prob = _oracle(w, res["lambda"])
+    return res, v, prob
+
+
+@pytest.mark.parametrize("name,dims", [("1d", None), ("custom", (48, 64)), ("custom", (16, 12, 8))])
+def test_solve_matches_oracle_fp64(name, dims):
+    w = make_problem(name) if name != "custom" else _workload(dims, seed=6)
+    lam_rel = w.lam_rel if name != "custom" else 0.1
+    res, v, prob = _solve_both(w, lam_rel, 1e-10)
+    assert res["status"] in (binding.IPM_OK,)
+    assert res["rel_gap"] <= 1e-10
+    assert abs(res["lambda"] - lam_rel * prob.lambda_max()) <= 1e-12 * prob.lambda_max()
+    ora = oipm.solve(prob, gap_tol=1e-10)
+    assert abs(res["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
+    vref = oracle_to_half(ora["beta"], w.dims)
+    assert np.abs(v - vref).max() <= 1e-6 * np.abs(vref).max()
+    # the oracle's own certificate at the GPU point
+    assert ora["ipm_iters"] > 0
+
+
+def test_config_2d_full_size_fp64():
+    """512 x 512, the benchmark workload: GPU solve to 1e-6, oracle certifies it."""
+    w = make_problem("2d")
+    res, v, prob = _solve_both(w, w.lam_rel, 1e-6)
+    assert res["status"] == binding.IPM_OK and res["rel_gap"] <= 1e-6
+    ora = oipm.solve(prob, gap_tol=1e-6)
+    assert abs(res["primal"] - ora["primal"]) <= 2e-6 * abs(ora["primal"])
+    # recompute the certificate from the GPU spectrum with the oracle
+    from oracle import mapping
+    vf = np.zeros(w.dims, dtype=np.complex128)
+    vh = (v[0::2] + 1j * v[1::2]).reshape(w.dims[0], w.dims[1] // 2 + 1)
+    vf[:, : w.dims[1] // 2 + 1] = vh
+    k0 = (-np.arange(w.dims[0])) % w.dims[0]
+    for k1 in range(w.dims[1] // 2 + 1, w.dims[1]):
+        vf[:, k1] = np.conj(vh[k0, w.dims[1] - k1])
+    beta = mapping.v_to_beta(vf, w.dims)
+    P, D, gap = prob.certificate(beta)
+    assert gap <= 1.5e-6 and abs(P - res["primal"]) <= 1e-9 * abs(P)
+
+
+def test_unmasked_equals_soft_threshold():
+    dims = (32, 24)
+    w = _workload(dims, seed=7, missing=0.0)
+    w.mask[:] = 1
+    res, v, prob = _solve_both(w, 0.2, 1e-12)
+    from oracle.brute import soft_threshold
+    ref = oracle_to_half(soft_threshold(prob.c, prob.lam), dims)
+    assert np.abs(v - ref).max() < 1e-8
+
+
+def test_lambda_above_max_gives_zero():
+    w = _workload((16, 12, 8), seed=8)
+    res, v, prob = _solve_both(w, 1.05, 1e-10)
+    assert np.abs(v).max() < 1e-8
+
+
+def test_solve_is_deterministic():
+    w = _workload((48, 64), seed=9)
+    r1, v1, _ = _solve_both(w, 0.1, 1e-8)
+    r2, v2, _ = _solve_both(w, 0.1, 1e-8)
+    assert np.array_equal(v1, v2) and r1["primal"] == r2["primal"] and r1["cg_iters_total"] == r2["cg_iters_total"]
+
+
+def test_mixed_precision_solve_reaches_gap():
+    w = _workload((64, 48), seed=10)
+    r64, v64, prob = _solve_both(w, 0.1, 1e-8)
+    r32, v32, _ = _solve_both(w, 0.1, 1e-8, precision=binding.IPM_MIXED)
+    assert r32["rel_gap"] <= 1e-8
+    assert abs(r32["primal"] - r64["primal"]) <= 1e-7 * abs(r64["primal"])
+    assert np.abs(v32 - v64).max() <= 1e-4 * np.abs(v64).max()
+
+
+def test_empty_mask_rejected():
+    w = _workload((8, 8), seed=11)
+    w.mask[:] = 0
+    with pytest.raises(binding.IpmError) as e:
+        _handle(w)
+    assert e.value.status == binding.IPM_ERR_ARG
