@@ -23,8 +23,8 @@
  *  - The library never frees caller memory; caller buffers are copied where
  *    stated, and never retained after the call returns.
  *  - Grids are row-major with the LAST axis contiguous; every extent must be
- *    even (Sec. 3 treats the even case) and of the form 2^a 3^b with b <= 1,
- *    at most 1024 along the last axis and 512 along the others.
+ *    even (Sec. 3 treats the even case), of the form 2^a 3^b with b <= 1, and
+ *    at most 512.
  *  - "beta layout": vectors indexed like beta are held as 2H doubles, where
  *    H = N_0 ... N_{d-2} (N_{d-1}/2 + 1) is the number of half-spectrum slots.
  *    Slot s carries two doubles; coordinates that are not LASSO variables
@@ -38,8 +38,8 @@
  *  - Two-block vectors of the condensed system (p, q, r, z in kkt_apply and
  *    precond_apply) are [beta block | z block], 4H doubles.
  *  - Pointers documented as "device" must be device (or managed) memory of
- *    the handle's device; pointers documented as "host or device" are
- *    detected with cudaPointerGetAttributes.
+ *    the handle's device; pointers documented as "host or device" may be
+ *    either (copies use unified addressing, cudaMemcpyDefault).
  *  - All work is queued on the handle's CUDA stream.  Functions that return
  *    results to the host synchronise that stream before returning.
  */
@@ -78,7 +78,10 @@ typedef struct {
   double sigma_slow;    /* centring after a short step alpha < 0.1 (default 0.5)               */
   double tau;           /* fraction to the boundary (default 0.995)                            */
   int lambda_relative;  /* 1: lambda is a fraction of lambda_max = ||M_perp^T b||_inf          */
-  int cg_chunk;         /* PCG iterations queued between host checks (default 4)               */
+  int cg_chunk;         /* host-driven mode: PCG iterations queued between host checks (4)     */
+  int use_graph;        /* 1 (default): the whole solve is one CUDA graph whose IPM and PCG
+                           loops are conditional WHILE nodes decided on the device; 0: the
+                           host drives the loops (also used while profiling is on)             */
 } ipm_options;
 
 typedef struct {
@@ -167,10 +170,13 @@ ipm_status ipm_get_spectrum(sdft_ipm* h, double* v_half);
 ipm_status ipm_pack_beta(sdft_ipm* h, const double* v_half, double* beta);
 ipm_status ipm_unpack_beta(sdft_ipm* h, const double* beta, double* v_half);
 
-/* Per-kernel timing with CUDA events around every launch (0 = off, default).
- * ipm_profile_get returns, for kernel class k (0: FFT row pass, 1: column
- * pass, 2: middle pass, 3: PCG update, 4: IPM kernels), the number of
- * launches and their summed duration in milliseconds since the last reset. */
+/* Per-kernel timing with CUDA events around every launch (0 = off, default;
+ * each call resets the counters).  ipm_profile_get returns, for kernel class
+ * k (0: FFT row pass, 1: column pass, 2: middle pass, 3: PCG update, 4: other
+ * IPM kernels), the number of launches and their summed duration in
+ * milliseconds since the last reset (timed only while profiling is on); for
+ * k = 5 it returns the number of kernels the library launched since the last
+ * reset, timed or not, and *ms = 0. */
 ipm_status ipm_profile_enable(sdft_ipm* h, int on);
 ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms);
 

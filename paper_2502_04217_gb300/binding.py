@@ -26,7 +26,7 @@ class ipm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gap_tol", ctypes.c_double), ("cg_tol", ctypes.c_double),
                 ("cg_relative", ctypes.c_int), ("max_ipm", ctypes.c_int), ("max_cg", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("sigma_slow", ctypes.c_double), ("tau", ctypes.c_double),
-                ("lambda_relative", ctypes.c_int), ("cg_chunk", ctypes.c_int)]
+                ("lambda_relative", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 class ipm_result(ctypes.Structure):

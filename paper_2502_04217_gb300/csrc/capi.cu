@@ -98,6 +98,13 @@ struct sdft_ipm {
   std::vector<cudaEvent_t> ev_pool;
   long long prof_count[5] = {0, 0, 0, 0, 0};
   double prof_ms[5] = {0, 0, 0, 0, 0};
+  unsigned long long launch_base = 0;   // device launch counter at the last profile reset
+  // whole-solve CUDA graph (two nested conditional WHILE loops)
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_valid = false;
+  cudaGraphConditionalHandle c_ipm = 0, c_cg = 0;
 };
 
 namespace {
@@ -380,12 +387,21 @@ ipm_status upload_problem(sdft_ipm* h, const uint8_t* mask, const double* y, dou
   if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail_arg(h, "lambda must be positive and finite");
   CK(cudaMemcpyAsync(h->d_mask, mask, (size_t)L.n, cudaMemcpyDefault, h->st));
   CK(cudaMemcpyAsync(h->d_y, y, (size_t)L.n * sizeof(double), cudaMemcpyDefault, h->st));
-  CK(k_pack_mask(h->d_mask, h->d_maskw, L.Nl, L.M, h->st));
   Reduce red{h->d_partials, h->d_counter};
-  CK(k_observed_norm(h->d_y, h->d_mask, L.n, red, h->d_sc, h->st));
+  {
+    ProfScope ps(h, 4);
+    CK(k_pack_mask(h->d_mask, h->d_maskw, L.Nl, L.M, h->d_sc, h->st));
+  }
+  {
+    ProfScope ps(h, 4);
+    CK(k_observed_norm(h->d_y, h->d_mask, L.n, red, h->d_sc, h->st));
+  }
   ipm_status s = compute_c(h);
   if (s != IPM_OK) return s;
-  CK(k_cmax(h->w.c, 2 * L.H, lambda, h->opt.lambda_relative, red, h->d_sc, h->st));
+  {
+    ProfScope ps(h, 4);
+    CK(k_cmax(h->w.c, 2 * L.H, lambda, h->opt.lambda_relative, red, h->d_sc, h->st));
+  }
   h->lambda_in = lambda;
   h->point_set = false;
   return IPM_OK;
@@ -425,6 +441,7 @@ void ipm_default_options(ipm_options* o) {
   o->tau = 0.995;
   o->lambda_relative = 0;
   o->cg_chunk = 4;
+  o->use_graph = 1;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -485,6 +502,7 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
     CKC(cudaMallocHost(&p, sizeof(DevScalars)));
     h->h_sc = (DevScalars*)p;
   }
+  for (cudaStream_t& c : h->cap) CKC(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
   ipm_status s;
   if ((s = plan_passes(h, h->pass64, false)) != IPM_OK) return cleanup_fail(s);
   if ((s = plan_passes(h, h->pass32, true)) != IPM_OK) return cleanup_fail(s);
@@ -525,9 +543,13 @@ ipm_status ipm_set_options(sdft_ipm* h, const ipm_options* opt) {
   if (s != IPM_OK) return s;
   const bool rel_changed = opt->lambda_relative != h->opt.lambda_relative;
   h->opt = *opt;
+  h->graph_valid = false;            // kernel arguments of the graph depend on the options
   if (rel_changed) {
     Reduce red{h->d_partials, h->d_counter};
-    CK(k_cmax(h->w.c, 2 * h->lay.H, h->lambda_in, h->opt.lambda_relative, red, h->d_sc, h->st));
+    {
+      ProfScope ps(h, 4);
+      CK(k_cmax(h->w.c, 2 * h->lay.H, h->lambda_in, h->opt.lambda_relative, red, h->d_sc, h->st));
+    }
     ipm_status r = read_scalars(h);
     return r != IPM_OK ? r : check_resolved(h);
   }
@@ -541,12 +563,155 @@ ipm_status ipm_sizes(const sdft_ipm* h, int64_t* nslots, int64_t* n) {
   return IPM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Swap the handle onto a capturing stream with per-launch profiling off.
+struct StreamSwap {
+  sdft_ipm* h;
+  cudaStream_t saved;
+  bool prof;
+  StreamSwap(sdft_ipm* h_, cudaStream_t s) : h(h_), saved(h_->st), prof(h_->prof) { h->st = s; h->prof = false; }
+  ~StreamSwap() { h->st = saved; h->prof = prof; }
+};
+
+// Conditional handle for a WHILE node to be added to the graph being captured on h->st.
+ipm_status make_cond(sdft_ipm* h, cudaGraphConditionalHandle* hc, unsigned dflt) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(h->st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive) { h->err = "stream is not capturing"; return IPM_ERR_CUDA; }
+  CK(cudaGraphConditionalHandleCreate(hc, g, dflt, cudaGraphCondAssignDefault));
+  return IPM_OK;
+}
+
+// Append a WHILE node (condition hc) to the graph captured on h->st; its body is
+// captured from `body` on stream bs.
+template <typename F>
+ipm_status add_while(sdft_ipm* h, cudaGraphConditionalHandle hc, cudaStream_t bs, F&& body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(h->st, &cs, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hc;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+  CK(cudaStreamUpdateCaptureDependencies(h->st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  ipm_status s;
+  {
+    StreamSwap sw(h, bs);
+    s = body();
+  }
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(bs, &out);
+  if (s != IPM_OK) return s;
+  CK(e);
+  return IPM_OK;
+}
+
+// One IPM iteration as launched work: residual product, certificate + stop test,
+// Newton system, PCG loop, step.  In graph mode `pcg_loop` wraps the PCG body
+// in a WHILE node; in host mode the caller drives PCG.
+ipm_status queue_residual_and_test(sdft_ipm* h, LoopCtl ipm_loop) {
+  const Layout& L = h->lay;
+  const ipm_options& o = h->opt;
+  Reduce red{h->d_partials, h->d_counter};
+  GSpec g;
+  g.src = h->w.beta;
+  g.dst = h->w.Gb;
+  ipm_status s = run_g(h, false, g);                   // residual always in FP64
+  if (s != IPM_OK) return s;
+  ProfScope ps(h, 4);
+  CK(k_certificate(L, h->w.beta, h->w.Gb, h->w.c, red, h->d_sc, o.gap_tol, o.max_ipm, ipm_loop, h->st));
+  return IPM_OK;
+}
+
+ipm_status queue_prepare(sdft_ipm* h, LoopCtl cg_loop) {
+  Reduce red{h->d_partials, h->d_counter};
+  ProfScope ps(h, 4);
+  CK(k_prepare(h->lay, h->w, red, h->d_sc, h->opt.cg_tol, h->opt.cg_relative, cg_loop, h->st));
+  return IPM_OK;
+}
+
+ipm_status queue_pcg_iteration(sdft_ipm* h, LoopCtl cg_loop) {
+  GSpec k;
+  k.mapin = MAPIN_PCG;
+  k.mapout = MAPOUT_K;
+  k.pcg = true;
+  ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, k);
+  if (s != IPM_OK) return s;
+  Reduce red{h->d_partials, h->d_counter};
+  ProfScope ps(h, 3);
+  CK(k_pcg_update(h->lay, h->w, red, h->d_sc, h->opt.max_cg, cg_loop, h->st));
+  return IPM_OK;
+}
+
+ipm_status queue_step(sdft_ipm* h) {
+  Reduce red{h->d_partials, h->d_counter};
+  {
+    ProfScope ps(h, 4);
+    CK(k_step_length(h->lay, h->w, red, h->d_sc, h->opt.tau, h->st));
+  }
+  ProfScope ps(h, 4);
+  CK(k_step_update(h->lay, h->w, red, h->d_sc, h->opt.sigma, h->opt.sigma_slow, h->st));
+  return IPM_OK;
+}
+
+// Capture the whole IPM loop into a graph:
+//   WHILE (c_ipm):  G beta -> certificate (writes c_ipm) -> prepare (writes c_cg)
+//                   WHILE (c_cg): K p passes -> pcg_update (writes c_cg)
+//                   step length -> step update
+ipm_status build_graph(sdft_ipm* h) {
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+  h->graph_valid = false;
+  CK(cudaStreamBeginCapture(h->cap[0], cudaStreamCaptureModeRelaxed));
+  ipm_status s;
+  {
+    StreamSwap sw(h, h->cap[0]);
+    s = make_cond(h, &h->c_ipm, 1u);
+    if (s == IPM_OK) {
+      s = add_while(h, h->c_ipm, h->cap[1], [h]() -> ipm_status {
+        ipm_status r = make_cond(h, &h->c_cg, 0u);
+        if (r != IPM_OK) return r;
+        if ((r = queue_residual_and_test(h, LoopCtl{h->c_ipm, 1})) != IPM_OK) return r;
+        if ((r = queue_prepare(h, LoopCtl{h->c_cg, 1})) != IPM_OK) return r;
+        r = add_while(h, h->c_cg, h->cap[2], [h]() -> ipm_status {
+          return queue_pcg_iteration(h, LoopCtl{h->c_cg, 1});
+        });
+        if (r != IPM_OK) return r;
+        return queue_step(h);
+      });
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap[0], &g);
+  if (s != IPM_OK) { if (g) cudaGraphDestroy(g); return s; }
+  CK(e);
+  h->graph = g;
+  CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+  h->graph_valid = true;
+  return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 ipm_status ipm_solve(sdft_ipm* h, ipm_result* res) {
   if (!h) return fail_arg(nullptr, "handle is NULL");
   const auto t0 = std::chrono::steady_clock::now();
   const Layout& L = h->lay;
   const ipm_options& o = h->opt;
-  const bool fp32 = o.precision == IPM_MIXED;
   Reduce red{h->d_partials, h->d_counter};
   ipm_status s;
   {
@@ -555,70 +720,44 @@ ipm_status ipm_solve(sdft_ipm* h, ipm_result* res) {
     else CK(k_init_point(L, h->w, red, h->d_sc, o.sigma, h->st));
   }
   h->point_set = false;
-  int ipm_iters = 0, cg_total = 0, cg_max = 0, products = 0;
-  ipm_status final_status = IPM_MAXITER;
-  bool krylov_cap = false;
-  for (int it = 0;; ++it) {
-    GSpec g;
-    g.src = h->w.beta;
-    g.dst = h->w.Gb;
-    if ((s = run_g(h, false, g)) != IPM_OK) return s;     // residual always in FP64
-    ++products;
-    {
-      ProfScope ps(h, 4);
-      CK(k_certificate(L, h->w.beta, h->w.Gb, h->w.c, red, h->d_sc, h->st));
-    }
-    if ((s = read_scalars(h)) != IPM_OK) return s;
-    if (!std::isfinite(h->h_sc->gap) || !std::isfinite(h->h_sc->mu)) { final_status = IPM_NUMERICAL; break; }
-    if (h->h_sc->gap <= o.gap_tol) { final_status = IPM_OK; break; }
-    if (it >= o.max_ipm) { final_status = IPM_MAXITER; break; }
-    {
-      ProfScope ps(h, 4);
-      CK(k_prepare(L, h->w, red, h->d_sc, o.cg_tol, o.cg_relative, h->st));
-    }
-    // PCG: chunks of cg_chunk iterations, each kernel returns at once after the stop
+  const LoopCtl none{0, 0};
+  if (o.use_graph && !h->prof) {
+    if (!h->graph_valid && (s = build_graph(h)) != IPM_OK) return s;
+    CK(cudaGraphLaunch(h->gexec, h->st));
+  } else {
+    // host-driven loop: the same kernels, the host reads the device decisions
     for (;;) {
-      for (int c = 0; c < o.cg_chunk; ++c) {
-        GSpec k;
-        k.mapin = MAPIN_PCG;
-        k.mapout = MAPOUT_K;
-        k.pcg = true;
-        if ((s = run_g(h, fp32, k)) != IPM_OK) return s;
-        ProfScope ps(h, 3);
-        CK(k_pcg_update(L, h->w, red, h->d_sc, o.max_cg, h->st));
-      }
+      if ((s = queue_residual_and_test(h, none)) != IPM_OK) return s;
       if ((s = read_scalars(h)) != IPM_OK) return s;
-      if (h->h_sc->cg_done) break;
+      if (h->h_sc->ipm_done) break;
+      if ((s = queue_prepare(h, none)) != IPM_OK) return s;
+      for (;;) {
+        for (int c = 0; c < o.cg_chunk; ++c)
+          if ((s = queue_pcg_iteration(h, none)) != IPM_OK) return s;
+        if ((s = read_scalars(h)) != IPM_OK) return s;
+        if (h->h_sc->cg_done) break;
+      }
+      if ((s = queue_step(h)) != IPM_OK) return s;
     }
-    const int ncg = h->h_sc->cg_iter;
-    cg_total += ncg;
-    products += ncg;
-    if (ncg > cg_max) cg_max = ncg;
-    if (h->h_sc->cg_status == 2) { final_status = IPM_NUMERICAL; break; }
-    if (h->h_sc->cg_status == 1) krylov_cap = true;
-    {
-      ProfScope ps(h, 4);
-      CK(k_step_length(L, h->w, red, h->d_sc, o.tau, h->st));
-      CK(k_step_update(L, h->w, red, h->d_sc, o.sigma, o.sigma_slow, h->st));
-    }
-    ++ipm_iters;
   }
   if ((s = read_scalars(h)) != IPM_OK) return s;
   prof_collect(h);
   h->sigma_ready = true;
-  if (final_status == IPM_OK && krylov_cap) final_status = IPM_KRYLOV_MAXITER;
+  const DevScalars& sc = *h->h_sc;
+  ipm_status final_status = sc.ipm_status == 0 ? IPM_OK : (sc.ipm_status == 4 ? IPM_MAXITER : IPM_NUMERICAL);
+  if (final_status == IPM_OK && sc.cg_cap_hit) final_status = IPM_KRYLOV_MAXITER;
   if (res) {
     res->status = final_status;
-    res->ipm_iters = ipm_iters;
-    res->cg_iters_total = cg_total;
-    res->cg_iters_max = cg_max;
-    res->primal = h->h_sc->primal;
-    res->dual = h->h_sc->dual;
-    res->rel_gap = h->h_sc->gap;
-    res->mu = h->h_sc->mu;
-    res->lambda = h->h_sc->lambda;
-    res->lambda_max = h->h_sc->cmax;
-    res->kkt_products = products;
+    res->ipm_iters = sc.ipm_it;
+    res->cg_iters_total = sc.cg_total;
+    res->cg_iters_max = sc.cg_max;
+    res->primal = sc.primal;
+    res->dual = sc.dual;
+    res->rel_gap = sc.gap;
+    res->mu = sc.mu;
+    res->lambda = sc.lambda;
+    res->lambda_max = sc.cmax;
+    res->kkt_products = sc.cg_total + sc.ipm_it + 1;
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (final_status == IPM_NUMERICAL) h->err = "non-finite value or breakdown of positive definiteness";
@@ -659,7 +798,7 @@ ipm_status precond_apply(sdft_ipm* h, const double* r, double* z) {
   if (!h->sigma_ready) return fail_arg(h, "Sigma is not set: call ipm_set_sigma or ipm_solve first");
   {
     ProfScope ps(h, 4);
-    CK(k_precond(h->lay, h->w, r, z, h->st));
+    CK(k_precond(h->lay, h->w, r, z, h->d_sc, h->st));
   }
   CK(cudaStreamSynchronize(h->st));
   prof_collect(h);
@@ -668,7 +807,10 @@ ipm_status precond_apply(sdft_ipm* h, const double* r, double* z) {
 
 ipm_status ipm_set_sigma(sdft_ipm* h, const double* s1, const double* nu1, const double* s2, const double* nu2) {
   if (!h || !s1 || !nu1 || !s2 || !nu2) return fail_arg(h, "NULL argument");
-  CK(k_sigma_coef(h->lay, s1, nu1, s2, nu2, h->w, h->st));
+  {
+    ProfScope ps(h, 4);
+    CK(k_sigma_coef(h->lay, s1, nu1, s2, nu2, h->w, h->d_sc, h->st));
+  }
   CK(cudaStreamSynchronize(h->st));
   h->sigma_ready = true;
   return IPM_OK;
@@ -682,7 +824,8 @@ ipm_status ipm_set_point(sdft_ipm* h, const double* const wv[6]) {
   const size_t bytes = 2 * (size_t)h->lay.H * sizeof(double);
   for (int i = 0; i < 6; ++i) {
     CK(cudaMemcpyAsync(dst[i], wv[i], bytes, cudaMemcpyDefault, h->st));
-    CK(k_clear_ghosts(h->lay, dst[i], 1, h->st));
+    ProfScope ps(h, 4);
+    CK(k_clear_ghosts(h->lay, dst[i], 1, h->d_sc, h->st));
   }
   CK(cudaStreamSynchronize(h->st));
   h->point_set = true;
@@ -703,7 +846,10 @@ ipm_status ipm_get_point(sdft_ipm* h, double* const wv[6]) {
 
 ipm_status ipm_get_spectrum(sdft_ipm* h, double* v_half) {
   if (!h || !v_half) return fail_arg(h, "NULL argument");
-  CK(k_unpack(h->lay, h->w.beta, h->d_tmp, h->st));
+  {
+    ProfScope ps(h, 4);
+    CK(k_unpack(h->lay, h->w.beta, h->d_tmp, h->d_sc, h->st));
+  }
   CK(cudaMemcpyAsync(v_half, h->d_tmp, 2 * (size_t)h->lay.H * sizeof(double), cudaMemcpyDefault, h->st));
   CK(cudaStreamSynchronize(h->st));
   return IPM_OK;
@@ -711,14 +857,20 @@ ipm_status ipm_get_spectrum(sdft_ipm* h, double* v_half) {
 
 ipm_status ipm_pack_beta(sdft_ipm* h, const double* v_half, double* beta) {
   if (!h || !v_half || !beta) return fail_arg(h, "NULL argument");
-  CK(k_pack(h->lay, v_half, beta, h->st));
+  {
+    ProfScope ps(h, 4);
+    CK(k_pack(h->lay, v_half, beta, h->d_sc, h->st));
+  }
   CK(cudaStreamSynchronize(h->st));
   return IPM_OK;
 }
 
 ipm_status ipm_unpack_beta(sdft_ipm* h, const double* beta, double* v_half) {
   if (!h || !v_half || !beta) return fail_arg(h, "NULL argument");
-  CK(k_unpack(h->lay, beta, v_half, h->st));
+  {
+    ProfScope ps(h, 4);
+    CK(k_unpack(h->lay, beta, v_half, h->d_sc, h->st));
+  }
   CK(cudaStreamSynchronize(h->st));
   return IPM_OK;
 }
@@ -728,12 +880,22 @@ ipm_status ipm_profile_enable(sdft_ipm* h, int on) {
   prof_collect(h);
   h->prof = on != 0;
   for (int k = 0; k < 5; ++k) { h->prof_count[k] = 0; h->prof_ms[k] = 0; }
+  ipm_status s = read_scalars(h);
+  if (s != IPM_OK) return s;
+  h->launch_base = h->h_sc->launches;
   return IPM_OK;
 }
 
 ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms) {
-  if (!h || k < 0 || k >= 5) return fail_arg(h, "bad kernel class");
+  if (!h || k < 0 || k > 5) return fail_arg(h, "bad kernel class");
   prof_collect(h);
+  if (k == 5) {
+    ipm_status s = read_scalars(h);
+    if (s != IPM_OK) return s;
+    if (launches) *launches = (int64_t)(h->h_sc->launches - h->launch_base);
+    if (ms) *ms = 0.0;
+    return IPM_OK;
+  }
   if (launches) *launches = h->prof_count[k];
   if (ms) *ms = h->prof_ms[k];
   return IPM_OK;
@@ -748,6 +910,10 @@ void ipm_destroy(sdft_ipm* h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (cudaStream_t c : h->cap)
+    if (c) cudaStreamDestroy(c);
   for (auto& e : h->prof_live) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(512, 1) row_pass_kernel(PassArgs a) {
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
+  count_launch(a.sc);
   if (a.check_done && a.sc->cg_done) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP, L = a.plan.L;
@@ -154,6 +155,7 @@ template <typename T, int E, bool INV>
 __global__ void __launch_bounds__(512, 1) col_pass_kernel(PassArgs a) {
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  count_launch(a.sc);
   if (a.check_done && a.sc->cg_done) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP, L = a.plan.L;
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(512, 1) middle_pass_kernel(PassArgs a) {
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
+  count_launch(a.sc);
   if (a.check_done && a.sc->cg_done) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP;

@@ -35,7 +35,20 @@ struct DevScalars {
   double corr;       // ||M_perp^T (b - M_perp beta)||_inf
   double l1;         // ||beta||_1
   double nobs;       // number of observed samples
+  // IPM control, kept on the device so a whole solve can run inside one graph
+  int ipm_done;      // 1 once the stop test has fired
+  int ipm_it;        // Newton directions taken
+  int ipm_status;    // 0 converged, 4 iteration cap, 6 non-finite
+  int cg_total;      // PCG iterations over the solve
+  int cg_max;        // largest PCG count of one IPM iteration
+  int cg_cap_hit;    // some PCG solve stopped at max_cg
+  unsigned long long launches;   // kernels launched by the library (every kernel adds 1)
 };
+
+// Count one launch (thread 0 of block 0 of every kernel).
+__device__ __forceinline__ void count_launch(DevScalars* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicAdd(&sc->launches, 1ull);
+}
 
 enum MapIn { MAPIN_NONE = 0, MAPIN_BETA = 1, MAPIN_PCG = 2 };
 enum MapOut { MAPOUT_NONE = 0, MAPOUT_BETA = 1, MAPOUT_K = 2 };

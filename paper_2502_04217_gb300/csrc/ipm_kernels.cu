@@ -3,6 +3,13 @@
 // Vectors use the beta layout of common.cuh (2H doubles, ghost coordinates
 // held at 0 and skipped by every reduction).  Two-block vectors (x, r, z, p, q
 // of the condensed system) are [beta block | z block], 4H doubles.
+//
+// The stop decisions live on the device (DevScalars), so that a whole solve
+// can run as one CUDA graph with two nested conditional WHILE nodes: the IPM
+// loop (condition written by certificate_kernel) and, inside it, the PCG loop
+// (condition written by prepare_kernel and pcg_update_kernel).  Every kernel
+// that writes a condition writes it from exactly one thread, on every path,
+// and both loops are bounded by their iteration caps.
 #include "internal.h"
 #include "kernels.h"
 
@@ -12,8 +19,15 @@ namespace {
 
 constexpr int kThreads = 256;
 
+__device__ __forceinline__ bool first_thread() { return threadIdx.x == 0 && blockIdx.x == 0; }
+
+__device__ __forceinline__ void set_cond(const LoopCtl& c, unsigned v) {
+  if (c.use) cudaGraphSetConditional(c.handle, v);
+}
+
 __global__ void __launch_bounds__(kThreads) pack_mask_kernel(const uint8_t* __restrict__ mask, uint32_t* __restrict__ words,
-                                                             int Nl, int M) {
+                                                             int Nl, int M, DevScalars* sc) {
+  count_launch(sc);
   // one thread per output word: 32 consecutive samples of one row x'
   const long long nw = (long long)((Nl + 31) / 32) * M;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw; i += (long long)gridDim.x * blockDim.x) {
@@ -32,6 +46,7 @@ __global__ void __launch_bounds__(kThreads) observed_norm_kernel(const double* _
                                                                  long long n, double* partials, unsigned* counter,
                                                                  DevScalars* sc) {
   __shared__ double scratch[64];
+  count_launch(sc);
   double v[2] = {0.0, 0.0};
   const int ops[2] = {RED_SUM, RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -40,10 +55,11 @@ __global__ void __launch_bounds__(kThreads) observed_norm_kernel(const double* _
   if (grid_reduce<2>(v, ops, partials, counter, scratch) && threadIdx.x == 0) { sc->yy = v[0]; sc->nobs = v[1]; }
 }
 
-// ||c||_inf for lambda_max; sets lambda (relative or absolute) and the start point scale
+// ||c||_inf for lambda_max; sets lambda (relative or absolute)
 __global__ void __launch_bounds__(kThreads) cmax_kernel(const double* __restrict__ c, long long n2, double lam_in, int relative,
                                                         double* partials, unsigned* counter, DevScalars* sc) {
   __shared__ double scratch[32];
+  count_launch(sc);
   double v[1] = {0.0};
   const int ops[1] = {RED_MAX};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
@@ -54,11 +70,25 @@ __global__ void __launch_bounds__(kThreads) cmax_kernel(const double* __restrict
   }
 }
 
-// Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu
+__device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double sigma0) {
+  sc->mu = mu;
+  sc->sigma = sigma0;
+  sc->alpha = 0.0;
+  sc->ipm_done = 0;
+  sc->ipm_it = 0;
+  sc->ipm_status = 0;
+  sc->cg_total = 0;
+  sc->cg_max = 0;
+  sc->cg_cap_hit = 0;
+  sc->cg_done = 1;
+}
+
+// Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu; control reset
 __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double* beta, double* z, double* s1, double* s2,
                                                               double* nu1, double* nu2, double* partials, unsigned* counter,
                                                               DevScalars* sc, double sigma0) {
   __shared__ double scratch[32];
+  count_launch(sc);
   const double zeta = fmax(1.0, sc->cmax), hl = 0.5 * sc->lambda;
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
@@ -73,37 +103,36 @@ __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double
     nu2[i] = gh ? 0.0 : hl;
     if (!gh) v[0] += hl * zeta + hl * zeta;
   }
-  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
-    sc->mu = v[0] / (2.0 * (double)lay.n);
-    sc->sigma = sigma0;
-    sc->alpha = 0.0;
-  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0)
+    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0);
 }
 
-// mu = (nu1^T s1 + nu2^T s2) / 2n at a given point (after ipm_set_point)
+// mu = (nu1^T s1 + nu2^T s2) / 2n at a given point (after ipm_set_point); control reset
 __global__ void __launch_bounds__(kThreads) mu_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                       DevScalars* sc, double sigma0) {
   __shared__ double scratch[32];
+  count_launch(sc);
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
   const long long n2 = 2 * lay.H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
     if (!is_ghost(lay, i)) v[0] += w.nu1[i] * w.s1[i] + w.nu2[i] * w.s2[i];
-  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
-    sc->mu = v[0] / (2.0 * (double)lay.n);
-    sc->sigma = sigma0;
-    sc->alpha = 0.0;
-  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0)
+    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0);
 }
 
-// Duality-gap certificate at beta from G beta and c = M_perp^T b:
+// Duality-gap certificate at beta from G beta and c = M_perp^T b, and the IPM stop test:
 //   ||theta||^2 = ||b||^2 - 2 c^T beta + beta^T G beta,  b^T theta = ||b||^2 - c^T beta,
 //   ||M_perp^T theta||_inf = ||c - G beta||_inf,  P = ||theta||^2/2 + lambda ||beta||_1,
 //   D = s b^T theta - s^2 ||theta||^2 / 2 with s = min(1, lambda / ||M_perp^T theta||_inf).
+// Stop when the relative gap (P - D) / max(1, |P|) <= gap_tol, at the iteration cap,
+// or on a non-finite value; the IPM loop condition is !ipm_done.
 __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, const double* __restrict__ beta,
                                                                const double* __restrict__ Gb, const double* __restrict__ c,
-                                                               double* partials, unsigned* counter, DevScalars* sc) {
+                                                               double* partials, unsigned* counter, DevScalars* sc,
+                                                               double gap_tol, int max_ipm, LoopCtl ipm_loop) {
   __shared__ double scratch[4 * 32];
+  count_launch(sc);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   const int ops[4] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
@@ -120,20 +149,30 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
     const double P = 0.5 * th2 + lam * v[2];
     const double s = (v[3] <= lam) ? 1.0 : lam / v[3];
     const double D = s * bth - 0.5 * s * s * th2;
+    const double gap = (P - D) / fmax(1.0, fabs(P));
     sc->theta2 = th2;
     sc->corr = v[3];
     sc->l1 = v[2];
     sc->primal = P;
     sc->dual = D;
-    sc->gap = (P - D) / fmax(1.0, fabs(P));
+    sc->gap = gap;
+    if (!isfinite(gap) || !isfinite(sc->mu)) { sc->ipm_done = 1; sc->ipm_status = 6; }
+    else if (gap <= gap_tol) { sc->ipm_done = 1; sc->ipm_status = 0; }
+    else if (sc->ipm_it >= max_ipm) { sc->ipm_done = 1; sc->ipm_status = 4; }
+    set_cond(ipm_loop, sc->ipm_done ? 0u : 1u);
   }
 }
 
 // Barrier diagonals, preconditioner coefficients, condensed right-hand side and
 // PCG start (x = 0, r = rhs, z = P^{-1} r, p = z, rho = r^T z).
 __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
-                                                           DevScalars* sc, double cg_tol, int cg_relative) {
+                                                           DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop) {
   __shared__ double scratch[32];
+  count_launch(sc);
+  if (sc->ipm_done) {                       // after the stop test: no PCG
+    if (first_thread()) { sc->cg_done = 1; set_cond(cg_loop, 0u); }
+    return;
+  }
   const long long n2 = 2 * lay.H;
   const double lam = sc->lambda, smu = sc->sigma * sc->mu;
   double v[1] = {0.0};
@@ -177,13 +216,15 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     sc->cg_stop = cg_relative ? cg_tol * sqrt(fmax(rho, 0.0)) : cg_tol;
     sc->cg_done = (sqrt(fmax(rho, 0.0)) <= sc->cg_stop) ? 1 : 0;
     if (!isfinite(rho)) { sc->cg_status = 2; sc->cg_done = 1; }
+    set_cond(cg_loop, sc->cg_done ? 0u : 1u);
   }
 }
 
 // Preconditioner coefficients only (for precond_apply / kkt_apply on a given Sigma)
 __global__ void __launch_bounds__(kThreads) sigma_coef_kernel(Layout lay, const double* s1, const double* nu1, const double* s2,
                                                               const double* nu2, double* lam1, double* lam2, double* pa,
-                                                              double* pb, double* pc) {
+                                                              double* pb, double* pc, DevScalars* sc) {
+  count_launch(sc);
   const long long n2 = 2 * lay.H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     double l1 = 0, l2 = 0, a = 0, b = 0, c = 0;
@@ -203,7 +244,8 @@ __global__ void __launch_bounds__(kThreads) sigma_coef_kernel(Layout lay, const 
 // z = P^{-1} r  (Eq. (invprecond1): [L1/D, -L2/D; -L2/D, (1+L1)/D])
 __global__ void __launch_bounds__(kThreads) precond_kernel(long long n2, const double* __restrict__ pa, const double* __restrict__ pb,
                                                            const double* __restrict__ pc, const double* __restrict__ r,
-                                                           double* __restrict__ z) {
+                                                           double* __restrict__ z, DevScalars* sc) {
+  count_launch(sc);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     const double rb = r[i], rz = r[n2 + i], a = pa[i], b = pb[i], c = pc[i];
     z[i] = a * rb - b * rz;
@@ -212,11 +254,15 @@ __global__ void __launch_bounds__(kThreads) precond_kernel(long long n2, const d
 }
 
 // One PCG update after q = K p: x += alpha p, r -= alpha q, z = P^{-1} r, rho' = r^T z,
-// beta_cg = rho'/rho, stop test.
+// beta_cg = rho'/rho, stop test; the PCG loop condition is !cg_done.
 __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
-                                                              DevScalars* sc, int max_cg) {
+                                                              DevScalars* sc, int max_cg, LoopCtl cg_loop) {
   __shared__ double scratch[32];
-  if (sc->cg_done) return;
+  count_launch(sc);
+  if (sc->cg_done) {
+    if (first_thread()) set_cond(cg_loop, 0u);
+    return;
+  }
   const double alpha = sc->alpha_cg;
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
@@ -242,6 +288,7 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmV
     if (!isfinite(rho_new)) { sc->cg_status = 2; sc->cg_done = 1; }
     else if (sqrt(fmax(rho_new, 0.0)) <= sc->cg_stop) sc->cg_done = 1;
     else if (sc->cg_iter >= max_cg) { sc->cg_status = 1; sc->cg_done = 1; }
+    set_cond(cg_loop, sc->cg_done ? 0u : 1u);
   }
 }
 
@@ -263,6 +310,8 @@ __device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long 
 __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                                DevScalars* sc, double tau) {
   __shared__ double scratch[32];
+  count_launch(sc);
+  if (sc->ipm_done) return;
   const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu;
   double v[1] = {1.0 / 0.0};
@@ -278,10 +327,12 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) sc->alpha = fmin(1.0, tau * v[0]);
 }
 
-// Take the step and form the new duality measure mu
+// Take the step, form the new duality measure mu, count the iteration
 __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                                DevScalars* sc, double sigma0, double sigma_slow) {
   __shared__ double scratch[32];
+  count_launch(sc);
+  if (sc->ipm_done) return;
   const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu, alpha = sc->alpha;
   double v[1] = {0.0};
@@ -299,12 +350,19 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
     sc->mu = v[0] / (2.0 * (double)lay.n);
     sc->sigma = (alpha < 0.1) ? sigma_slow : sigma0;
+    sc->ipm_it += 1;
+    sc->cg_total += sc->cg_iter;
+    if (sc->cg_iter > sc->cg_max) sc->cg_max = sc->cg_iter;
+    if (sc->cg_status == 1) sc->cg_cap_hit = 1;
+    if (sc->cg_status == 2) { sc->ipm_done = 1; sc->ipm_status = 6; }
   }
 }
 
 // Canonical half spectrum (row-major, last axis halved, interleaved re/im) <-> beta layout.
 // unpack: v = B^H beta restricted to the half spectrum, twins filled with conj(rep).
-__global__ void __launch_bounds__(kThreads) unpack_kernel(Layout lay, const double* __restrict__ beta, double* __restrict__ vh) {
+__global__ void __launch_bounds__(kThreads) unpack_kernel(Layout lay, const double* __restrict__ beta, double* __restrict__ vh,
+                                                          DevScalars* sc) {
+  count_launch(sc);
   const long long H = lay.H;
   const double rh = 0.70710678118654752440;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < H; t += (long long)gridDim.x * blockDim.x) {
@@ -334,7 +392,9 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(Layout lay, const doub
 }
 
 // pack: beta = B v from the canonical half spectrum (twin slots of vh ignored)
-__global__ void __launch_bounds__(kThreads) pack_kernel(Layout lay, const double* __restrict__ vh, double* __restrict__ beta) {
+__global__ void __launch_bounds__(kThreads) pack_kernel(Layout lay, const double* __restrict__ vh, double* __restrict__ beta,
+                                                        DevScalars* sc) {
+  count_launch(sc);
   const long long H = lay.H;
   const double r2 = 1.41421356237309504880;
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < H; s += (long long)gridDim.x * blockDim.x) {
@@ -350,8 +410,9 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(Layout lay, const double
   }
 }
 
-// ghost-aware copy of a beta-layout vector with ghosts forced to 0
-__global__ void __launch_bounds__(kThreads) clear_ghosts_kernel(Layout lay, double* v, int blocks) {
+// ghost coordinates of a beta-layout vector forced to 0
+__global__ void __launch_bounds__(kThreads) clear_ghosts_kernel(Layout lay, double* v, int blocks, DevScalars* sc) {
+  count_launch(sc);
   const long long n2 = 2 * lay.H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i))
@@ -361,17 +422,16 @@ __global__ void __launch_bounds__(kThreads) clear_ghosts_kernel(Layout lay, doub
 
 int grid_for(long long n) {
   long long g = (n + kThreads - 1) / kThreads;
-  const long long cap = 152 * 8;
-  if (g > cap) g = cap;
+  if (g > kMaxElementwiseBlocks) g = kMaxElementwiseBlocks;
   if (g < 1) g = 1;
   return (int)g;
 }
 
 }  // namespace
 
-cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, cudaStream_t st) {
+cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, DevScalars* sc, cudaStream_t st) {
   const long long nw = (long long)((Nl + 31) / 32) * M;
-  pack_mask_kernel<<<grid_for(nw), kThreads, 0, st>>>(mask, words, Nl, M);
+  pack_mask_kernel<<<grid_for(nw), kThreads, 0, st>>>(mask, words, Nl, M, sc);
   return cudaGetLastError();
 }
 cudaError_t k_observed_norm(const double* y, const uint8_t* mask, long long n, Reduce red, DevScalars* sc, cudaStream_t st) {
@@ -392,26 +452,29 @@ cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, do
   return cudaGetLastError();
 }
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
-                          DevScalars* sc, cudaStream_t st) {
-  certificate_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, beta, Gb, c, red.partials, red.counter, sc);
+                          DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st) {
+  certificate_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, beta, Gb, c, red.partials, red.counter, sc,
+                                                               gap_tol, max_ipm, loop);
   return cudaGetLastError();
 }
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      cudaStream_t st) {
-  prepare_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, cg_tol, cg_relative);
+                      LoopCtl loop, cudaStream_t st) {
+  prepare_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, cg_tol, cg_relative,
+                                                           loop);
   return cudaGetLastError();
 }
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
-                         IpmVectors w, cudaStream_t st) {
-  sigma_coef_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc);
+                         IpmVectors w, DevScalars* sc, cudaStream_t st) {
+  sigma_coef_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc, sc);
   return cudaGetLastError();
 }
-cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, cudaStream_t st) {
-  precond_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w.pa, w.pb, w.pc, r, z);
+cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st) {
+  precond_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w.pa, w.pb, w.pc, r, z, sc);
   return cudaGetLastError();
 }
-cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, cudaStream_t st) {
-  pcg_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, max_cg);
+cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
+                         cudaStream_t st) {
+  pcg_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, max_cg, loop);
   return cudaGetLastError();
 }
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st) {
@@ -423,16 +486,16 @@ cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalar
   step_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0, sigma_slow);
   return cudaGetLastError();
 }
-cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, cudaStream_t st) {
-  unpack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, beta, vh);
+cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, DevScalars* sc, cudaStream_t st) {
+  unpack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, beta, vh, sc);
   return cudaGetLastError();
 }
-cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, cudaStream_t st) {
-  pack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, vh, beta);
+cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, DevScalars* sc, cudaStream_t st) {
+  pack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, vh, beta, sc);
   return cudaGetLastError();
 }
-cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, cudaStream_t st) {
-  clear_ghosts_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, v, blocks);
+cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, DevScalars* sc, cudaStream_t st) {
+  clear_ghosts_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, v, blocks, sc);
   return cudaGetLastError();
 }
 

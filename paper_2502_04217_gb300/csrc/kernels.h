@@ -23,24 +23,32 @@ struct Reduce {
   unsigned* counter;
 };
 
-cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, cudaStream_t st);
+// Loop condition of a conditional WHILE graph node, written by the kernel that
+// decides the loop (use = 0 outside graphs).
+struct LoopCtl {
+  cudaGraphConditionalHandle handle;
+  int use;
+};
+
+cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, DevScalars* sc, cudaStream_t st);
 cudaError_t k_observed_norm(const double* y, const uint8_t* mask, long long n, Reduce red, DevScalars* sc, cudaStream_t st);
 cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Reduce red, DevScalars* sc, cudaStream_t st);
 cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st);
 cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st);
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
-                          DevScalars* sc, cudaStream_t st);
+                          DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st);
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      cudaStream_t st);
+                      LoopCtl loop, cudaStream_t st);
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
-                         IpmVectors w, cudaStream_t st);
-cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, cudaStream_t st);
-cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, cudaStream_t st);
+                         IpmVectors w, DevScalars* sc, cudaStream_t st);
+cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st);
+cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
+                         cudaStream_t st);
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st);
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           cudaStream_t st);
-cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, cudaStream_t st);
-cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, cudaStream_t st);
-cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, cudaStream_t st);
+cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, DevScalars* sc, cudaStream_t st);
+cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, DevScalars* sc, cudaStream_t st);
+cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, DevScalars* sc, cudaStream_t st);
 
 }  // namespace sdft
