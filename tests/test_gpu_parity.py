@@ -215,3 +215,53 @@ def test_empty_mask_rejected():
     with pytest.raises(binding.IpmError) as e:
         _handle(w)
     assert e.value.status == binding.IPM_ERR_ARG
+
+
+@pytest.mark.parametrize("dims,precision", [((256,), binding.IPM_FP64), ((48, 64), binding.IPM_FP64),
+                                            ((16, 12, 8), binding.IPM_MIXED)])
+def test_graph_and_host_driven_solves_agree(dims, precision):
+    """The whole-solve CUDA graph (conditional WHILE loops decided on the device)
+    runs the same kernels in the same order as the host-driven loop: bit-identical."""
+    w = _workload(dims, seed=12)
+    out = []
+    for use_graph in (1, 0):
+        h = _handle(w, precision, gap_tol=1e-9, use_graph=use_graph)
+        try:
+            binding.ipm_profile_enable(h, False)          # resets the launch counter
+            res = binding.ipm_solve(h)
+            launches, _ = binding.ipm_profile_get(h, 5)
+            H, n = binding.ipm_sizes(h)
+            v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+            binding.ipm_get_spectrum(h, v)
+            out.append((res, v.cpu().numpy(), launches))
+            # a second solve on the same handle reuses the graph and gives the same answer
+            res2 = binding.ipm_solve(h)
+            assert res2["primal"] == res["primal"] and res2["cg_iters_total"] == res["cg_iters_total"]
+        finally:
+            binding.ipm_destroy(h)
+    (rg, vg, lg), (rh, vh, lh) = out
+    assert np.array_equal(vg, vh)
+    assert rg["primal"] == rh["primal"] and rg["ipm_iters"] == rh["ipm_iters"]
+    assert rg["cg_iters_total"] == rh["cg_iters_total"] and rg["rel_gap"] <= 1e-9
+    assert lg > 0 and lh > 0
+
+
+def test_iteration_cap_reported():
+    w = _workload((32, 24), seed=13)
+    h = _handle(w, gap_tol=1e-12, max_ipm=3)
+    try:
+        res = binding.ipm_solve(h, check=False)
+        assert res["status"] == binding.IPM_MAXITER and res["ipm_iters"] == 3
+    finally:
+        binding.ipm_destroy(h)
+
+
+def test_pcg_cap_reported():
+    w = _workload((32, 24), seed=14)
+    h = _handle(w, gap_tol=1e-8, max_cg=1, cg_tol=1e-14)
+    try:
+        res = binding.ipm_solve(h, check=False)
+        assert res["cg_iters_max"] <= 1
+        assert res["status"] in (binding.IPM_KRYLOV_MAXITER, binding.IPM_MAXITER)
+    finally:
+        binding.ipm_destroy(h)
