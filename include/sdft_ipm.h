@@ -180,6 +180,31 @@ ipm_status ipm_unpack_beta(sdft_ipm* h, const double* beta, double* v_half);
 ipm_status ipm_profile_enable(sdft_ipm* h, int on);
 ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms);
 
+/* q = M_perp^T M_perp p, like gapply, but without a handle and without
+ * allocating any device memory (the paper has no counterpart: this entry point
+ * serves callers that cannot call cudaMalloc -- hosts that hand out all device
+ * memory through their own allocator or a fixed budget, code that must not take
+ * the implicit device synchronisation of cudaMalloc/cudaFree, plugins running in
+ * another program's CUDA context).
+ *  ndim, dims  as for ipm_create; the half spectrum may have at most 262144
+ *              slots (H = N_0..N_{d-2} (N_{d-1}/2 + 1)); 512 x 512 and
+ *              64 x 64 x 64 fit, larger grids return IPM_ERR_ARG.
+ *  mask        device pointer, n = prod(dims) bytes, 1 = observed.
+ *  p, q        device pointers, 2H doubles each in the beta layout of the
+ *              handle-based API (the layout depends only on dims); p's ghost
+ *              coordinates must be 0, q's are written as 0.
+ *  stream      cudaStream_t the work is queued on (NULL = legacy default
+ *              stream); the call returns without waiting for it.
+ * The caller still owns every input and output.  Scratch is one fixed
+ * file-scope device array of about 4.7 MB that each GPU loading the library
+ * keeps until the process exits.  The first call on a device (with that device
+ * current) looks up the array's device address once; make that first call
+ * before any stream capture.  All calls share the array and each rewrites what
+ * it needs, so calls that overlap on the GPU (other streams, other host threads
+ * on the same device) race: order them on one stream.  FP64 arithmetic. */
+ipm_status gapply_noalloc(int ndim, const int64_t* dims, const uint8_t* mask, const double* p, double* q,
+                          void* stream);
+
 /* Message of the last failure on this handle (or of the last failed create
  * when h is NULL).  Owned by the library. */
 const char* ipm_last_error(const sdft_ipm* h);

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "ipm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ipm_profile_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "gapply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
     "ipm_last_error": (ctypes.c_char_p, [_P]),
     "ipm_destroy": (None, [_P]),
 }
@@ -208,6 +209,12 @@ def ipm_profile_get(h, k):
     n, ms = ctypes.c_int64(), ctypes.c_double()
     _check(load().ipm_profile_get(h, int(k), ctypes.byref(n), ctypes.byref(ms)), h)
     return n.value, ms.value
+
+
+def gapply_noalloc(dims, mask, p, q, stream=None):
+    """Handle-free, allocation-free q = M_perp^T M_perp p (device mask, p, q)."""
+    d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
+    return _check(load().gapply_noalloc(len(dims), d, addr(mask), addr(p), addr(q), stream), None)
 
 
 def ipm_last_error(h=None):

@@ -922,3 +922,8 @@ void ipm_destroy(sdft_ipm* h) {
 }
 
 }  // extern "C"
+
+namespace sdft {
+// Message returned by ipm_last_error(NULL) (used by entry points without a handle).
+void record_error(const char* msg) { g_create_error = msg; }
+}  // namespace sdft
