@@ -25,21 +25,25 @@ namespace {
 
 constexpr double kSqrt2 = 1.41421356237309504880;
 
+// The scalings run in the pass type T: FP64 passes scale in FP64, FP32 passes
+// round to FP32 first and scale there (their products are FP32 anyway).
 template <typename V>
 __device__ __forceinline__ V map_in(int cls, double b0, double b1) {
   using T = decltype(V::x);
   if (cls == EDGE_TWIN) return cmake<V>((T)0, (T)0);
   if (cls == EDGE_SC) return cmake<V>((T)b0, (T)0);
-  const double s = (cls == INTERIOR) ? kSqrtHalf : kSqrt2;
-  return cmake<V>((T)(b0 * s), (T)(b1 * s));
+  const T s = (cls == INTERIOR) ? (T)kSqrtHalf : (T)kSqrt2;
+  return cmake<V>((T)b0 * s, (T)b1 * s);
 }
 
 template <typename V>
 __device__ __forceinline__ void map_out(int cls, V w, double scale, double& o0, double& o1) {
+  using T = decltype(V::x);
   if (cls == EDGE_TWIN) { o0 = 0.0; o1 = 0.0; return; }
-  if (cls == EDGE_SC) { o0 = (double)w.x * scale; o1 = 0.0; return; }
-  o0 = (double)w.x * (kSqrt2 * scale);
-  o1 = (double)w.y * (kSqrt2 * scale);
+  if (cls == EDGE_SC) { o0 = (double)(w.x * (T)scale); o1 = 0.0; return; }
+  const T s = (T)(kSqrt2 * scale);
+  o0 = (double)(w.x * s);
+  o1 = (double)(w.y * s);
 }
 
 // Load the complex value of slot g for the first pass.
@@ -311,12 +315,21 @@ cudaError_t launch_typed(int kind, bool inv, const PassArgs& a, int threads, siz
 
 }  // namespace
 
+template <typename T>
+cudaError_t launch_e(int kind, bool inv, int E, const PassArgs& a, int threads, size_t smem, dim3 grid, cudaStream_t st) {
+  switch (E) {
+    case 4: return launch_typed<T, 4>(kind, inv, a, threads, smem, grid, st);
+    case 6: return launch_typed<T, 6>(kind, inv, a, threads, smem, grid, st);
+    case 8: return launch_typed<T, 8>(kind, inv, a, threads, smem, grid, st);
+    case 12: return launch_typed<T, 12>(kind, inv, a, threads, smem, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_pass(int kind, bool inv, bool fp32, int E, const PassArgs& a, int threads, size_t smem,
                         dim3 grid, cudaStream_t st) {
-  if (fp32) return E == 12 ? launch_typed<float, 12>(kind, inv, a, threads, smem, grid, st)
-                           : launch_typed<float, 8>(kind, inv, a, threads, smem, grid, st);
-  return E == 12 ? launch_typed<double, 12>(kind, inv, a, threads, smem, grid, st)
-                 : launch_typed<double, 8>(kind, inv, a, threads, smem, grid, st);
+  return fp32 ? launch_e<float>(kind, inv, E, a, threads, smem, grid, st)
+              : launch_e<double>(kind, inv, E, a, threads, smem, grid, st);
 }
 
 }  // namespace sdft

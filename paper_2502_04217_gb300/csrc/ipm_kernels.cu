@@ -21,6 +21,20 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ bool first_thread() { return threadIdx.x == 0 && blockIdx.x == 0; }
 
+// 1/x by two Newton-Raphson steps y <- y + y (1 - x y) from a single-precision
+// seed (~23 correct bits -> ~46 -> full double precision, within about one ulp).
+// GB300 executes FP64 divides at ~58 G/s, several times the cost of these four
+// FMAs.  Outside the single-precision normal range it falls back to a divide.
+__device__ __forceinline__ double rcp(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
+  double y = (double)__frcp_rn((float)x);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 __device__ __forceinline__ void set_cond(const LoopCtl& c, unsigned v) {
   if (c.use) cudaGraphSetConditional(c.handle, v);
 }
@@ -178,10 +192,11 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
-    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, rb = 0, rc = 0, zb = 0, zz = 0;
+    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, rb = 0, rc = 0, zb = 0, zz = 0, is1 = 0, is2 = 0;
     if (!is_ghost(lay, i)) {
       const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
-      const double is1 = 1.0 / s1, is2 = 1.0 / s2;
+      is1 = rcp(s1);
+      is2 = rcp(s2);
       const double S1 = n1 * is1, S2 = n2_ * is2;              // Sigma_i = S_i^{-1} V_i
       const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
       const double r_z = lam - n1 - n2_;
@@ -192,13 +207,14 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
       rc = -r_z - rc1s - S1 * r_p1 - rc2s - S2 * r_p2;
       l1 = S1 + S2;
       l2 = S1 - S2;
-      const double iD = 1.0 / (S1 + S2 + 4.0 * S1 * S2);       // D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2
+      const double iD = rcp(S1 + S2 + 4.0 * S1 * S2);          // D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2
       pa = l1 * iD;
       pb = l2 * iD;
       pc = (1.0 + l1) * iD;
       zb = pa * rb - pb * rc;
       zz = -pb * rb + pc * rc;
     }
+    w.is1[i] = is1; w.is2[i] = is2;
     w.lam1[i] = l1; w.lam2[i] = l2;
     w.pa[i] = pa; w.pb[i] = pb; w.pc[i] = pc;
     w.x[i] = 0.0; w.x[n2 + i] = 0.0;
@@ -297,7 +313,7 @@ struct Dir { double ds1, ds2, dn1, dn2; };
 __device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long long n2, double smu) {
   const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
   const double db = w.x[i], dz = w.x[n2 + i];
-  const double is1 = 1.0 / s1, is2 = 1.0 / s2;
+  const double is1 = w.is1[i], is2 = w.is2[i];       // 1/s of this iterate, from prepare_kernel
   Dir d;
   d.ds1 = dz + db + (z + b - s1);
   d.ds2 = dz - db + (z - b - s2);
@@ -314,16 +330,25 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
   if (sc->ipm_done) return;
   const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu;
-  double v[1] = {1.0 / 0.0};
-  const int ops[1] = {RED_MIN};
+  // ratio test min over {w / (-dw) : dw < 0}: candidates are compared as fractions
+  // (num * best_den < best_num * den, all positive), so each thread divides once
+  double bn = 1.0, bd = 0.0;          // best fraction so far; bd = 0 means +inf
+  auto consider = [&](double wv, double dw) {
+    if (dw < 0.0) {
+      const double den = -dw;
+      if (bd == 0.0 || wv * bd < bn * den) { bn = wv; bd = den; }
+    }
+  };
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i)) continue;
     const Dir d = direction(w, i, n2, smu);
-    if (d.ds1 < 0) v[0] = fmin(v[0], -w.s1[i] / d.ds1);
-    if (d.ds2 < 0) v[0] = fmin(v[0], -w.s2[i] / d.ds2);
-    if (d.dn1 < 0) v[0] = fmin(v[0], -w.nu1[i] / d.dn1);
-    if (d.dn2 < 0) v[0] = fmin(v[0], -w.nu2[i] / d.dn2);
+    consider(w.s1[i], d.ds1);
+    consider(w.s2[i], d.ds2);
+    consider(w.nu1[i], d.dn1);
+    consider(w.nu2[i], d.dn2);
   }
+  double v[1] = {bd == 0.0 ? 1.0 / 0.0 : bn / bd};
+  const int ops[1] = {RED_MIN};
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) sc->alpha = fmin(1.0, tau * v[0]);
 }
 

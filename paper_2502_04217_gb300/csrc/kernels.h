@@ -12,6 +12,7 @@ struct IpmVectors {
   double *Gb;                                 // G beta at the current iterate
   double *lam1, *lam2;                        // Lambda1, Lambda2 of K
   double *pa, *pb, *pc;                       // P^{-1} = [pa, -pb; -pb, pc] per element
+  double *is1, *is2;                          // 1/s1, 1/s2 at the current iterate (step kernels)
   double *x, *r, *zv, *p, *q;                 // PCG vectors, 2 blocks each (4H)
 };
 

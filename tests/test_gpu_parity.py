@@ -265,3 +265,51 @@ def test_pcg_cap_reported():
         assert res["status"] in (binding.IPM_KRYLOV_MAXITER, binding.IPM_MAXITER)
     finally:
         binding.ipm_destroy(h)
+
+
+@pytest.mark.parametrize("tile_e,tile_p", [(4, 1), (4, 4), (8, 1), (8, 16), (4, 32)])
+@pytest.mark.parametrize("dims", [(512,), (96, 32), (64, 48), (12, 16, 24), (32, 24, 16)])
+def test_every_tile_shape_matches_oracle(dims, tile_e, tile_p):
+    """The autotuner may pick any launchable tile shape: each one must compute the
+    same product.  Lengths with a factor 3 map E=4 -> 6 and E=8 -> 12."""
+    for precision in (binding.IPM_FP64, binding.IPM_MIXED):
+        w = _workload(dims, seed=15)
+        three = {4: 6, 8: 12}
+        h = None
+        try:
+            # one option set per call; lengths with a factor 3 ignore the power-of-two budgets and
+            # vice versa, so run both spellings
+            for e in (tile_e, three[tile_e]):
+                h = _handle(w, precision, tile_e=e, tile_p=tile_p, autotune=0)
+                n = int(np.prod(dims))
+                prob = _oracle(w, 1.0)
+                beta = np.random.default_rng(16).standard_normal(n)
+                p = oracle_to_lib(h, beta, dims)
+                q = torch.empty_like(p)
+                binding.gapply(h, p, q)
+                tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * np.linalg.norm(beta)
+                assert np.abs(lib_to_half(h, q) - oracle_to_half(prob.G(beta), dims)).max() < tol
+                binding.ipm_destroy(h)
+                h = None
+        finally:
+            if h is not None:
+                binding.ipm_destroy(h)
+
+
+def test_autotuned_solve_matches_default_tiles():
+    w = _workload((64, 48), seed=17)
+    r_def, v_def, _ = None, None, None
+    out = []
+    for autotune in (0, 1):
+        h = _handle(w, gap_tol=1e-10, autotune=autotune)
+        try:
+            res = binding.ipm_solve(h)
+            H, n = binding.ipm_sizes(h)
+            v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+            binding.ipm_get_spectrum(h, v)
+            out.append((res, v.cpu().numpy()))
+        finally:
+            binding.ipm_destroy(h)
+    (r0, v0), (r1, v1) = out
+    assert abs(r0["primal"] - r1["primal"]) <= 1e-10 * abs(r0["primal"])
+    assert np.abs(v0 - v1).max() <= 1e-7 * np.abs(v0).max()

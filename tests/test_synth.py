@@ -1,0 +1,37 @@
+"""The seeded workload generator (no GPU): shapes, mask geometry, seeds."""
+
+import numpy as np
+
+from paper_2502_04217_gb300.synth import batch_workloads, lattice_mask, make_problem
+
+
+def test_config_masks_have_the_stated_missing_fractions():
+    # 2d: discs of radius 3 (29 pixels) on a period-16 lattice -> 29/256
+    w2 = make_problem("2d")
+    assert w2.dims == (512, 512) and abs((1 - w2.mask.mean()) - 29 / 256) < 1e-12
+    # 3d: balls |d|^2 <= 4 (33 voxels) on a period-8 lattice -> 33/512
+    m3 = lattice_mask((64, 64, 64), 8, 4)
+    assert abs((1 - m3.mean()) - 33 / 512) < 1e-12
+    w1 = make_problem("1d")
+    assert w1.dims == (256,) and int((1 - w1.mask).sum()) == 26
+
+
+def test_generator_is_seeded_and_deterministic():
+    a, b = make_problem("1d"), make_problem("1d")
+    assert np.array_equal(a.y, b.y) and np.array_equal(a.mask, b.mask)
+    c = make_problem("2d", index=1)
+    assert not np.array_equal(c.y, make_problem("2d").y)
+
+
+def test_batch_workload_shapes():
+    ws = batch_workloads(8)
+    assert all(w.dims[0] in (32, 48, 64, 96, 128) and len(set(w.dims)) == 1 for w in ws)
+    assert all(0.0 < 1 - w.mask.mean() < 0.5 for w in ws)
+    assert len({w.dims[0] for w in ws}) >= 2
+
+
+def test_sparse_spectrum_is_what_was_planted():
+    w = make_problem("custom", dims=(16, 12), k=5, noise=0.0, missing=0.0, seed=3)
+    spec = np.fft.rfftn(w.y, norm="ortho").reshape(-1)
+    big = np.flatnonzero(np.abs(spec) > 1e-9)
+    assert sorted(big.tolist()) == sorted(int(f) for f in w.freqs)
