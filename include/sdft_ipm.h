@@ -82,6 +82,15 @@ typedef struct {
   int use_graph;        /* 1 (default): the whole solve is one CUDA graph whose IPM and PCG
                            loops are conditional WHILE nodes decided on the device; 0: the
                            host drives the loops (also used while profiling is on)             */
+  int autotune;         /* 1 (default): at ipm_create, time every launchable tile shape
+                           (pencils per block, per-thread radix budget) of each FFT pass on
+                           the device and keep the fastest (cached per shape for the
+                           process); 0: a fixed heuristic                                     */
+  int tile_e;           /* 0 (default): chosen as above; else force this per-thread element
+                           budget (4 or 8, or 6 or 12 for lengths with a factor 3) wherever
+                           launchable                                                         */
+  int tile_p;           /* 0 (default): chosen as above; else force this many pencils per
+                           tile (a power of two) wherever launchable                          */
 } ipm_options;
 
 typedef struct {
@@ -204,6 +213,40 @@ ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms);
  * on the same device) race: order them on one stream.  FP64 arithmetic. */
 ipm_status gapply_noalloc(int ndim, const int64_t* dims, const uint8_t* mask, const double* p, double* q,
                           void* stream);
+
+/* ---- batches of independent problems ------------------------------------
+ * A batch holds `count` problems of possibly different grids and solves them
+ * together: ipm_solve_batch is ONE CUDA graph launch whose branches are the
+ * problems' whole solves (each with its IPM and PCG loops as conditional WHILE
+ * nodes), so the problems' kernels run concurrently and the host waits once.
+ * Each problem keeps its own device buffers; FFT tile shapes are tuned per grid
+ * shape once per process and shared by equal shapes. */
+typedef struct sdft_ipm_batch sdft_ipm_batch;
+
+/* Create a batch.  ndims[i], dims[3i .. 3i + ndims[i] - 1], masks[i], ys[i] and
+ * lambdas[i] describe problem i exactly as for ipm_create (host or device
+ * pointers, copied).  One options struct (NULL = defaults) and one stream for
+ * all.  On failure nothing is kept and ipm_last_error(NULL) names the problem. */
+ipm_status ipm_create_batch(sdft_ipm_batch** out, int count, const int* ndims, const int64_t* dims,
+                            const uint8_t* const* masks, const double* const* ys, const double* lambdas,
+                            const ipm_options* opt, void* stream);
+
+/* Solve every problem of the batch from the cold start of Sec. 3.3 in one graph
+ * launch; results (may be NULL) receives `count` entries (seconds = the wall
+ * time of the whole batch).  Returns IPM_OK when every problem reached gap_tol,
+ * else the status of the first problem that did not. */
+ipm_status ipm_solve_batch(sdft_ipm_batch* b, ipm_result* results);
+
+/* Number of problems; the handle of problem i (owned by the batch: use it for
+ * ipm_get_spectrum, ipm_get_point, ... but never destroy it); NULL if out of range. */
+int ipm_batch_size(const sdft_ipm_batch* b);
+sdft_ipm* ipm_batch_member(sdft_ipm_batch* b, int i);
+
+/* Message of the last failure of the batch (NULL: of the last failed create). */
+const char* ipm_batch_last_error(const sdft_ipm_batch* b);
+
+/* Destroy the batch and every member handle.  NULL is accepted. */
+void ipm_destroy_batch(sdft_ipm_batch* b);
 
 /* Message of the last failure on this handle (or of the last failed create
  * when h is NULL).  Owned by the library. */

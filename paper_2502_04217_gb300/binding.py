@@ -26,7 +26,8 @@ class ipm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gap_tol", ctypes.c_double), ("cg_tol", ctypes.c_double),
                 ("cg_relative", ctypes.c_int), ("max_ipm", ctypes.c_int), ("max_cg", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("sigma_slow", ctypes.c_double), ("tau", ctypes.c_double),
-                ("lambda_relative", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("lambda_relative", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("tile_e", ctypes.c_int), ("tile_p", ctypes.c_int)]
 
 
 class ipm_result(ctypes.Structure):
@@ -66,6 +67,14 @@ _SIGNATURES = {
     "ipm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ipm_profile_get": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_double)]),
+    "ipm_create_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ipm_options), _P]),
+    "ipm_solve_batch": (ctypes.c_int, [_P, ctypes.POINTER(ipm_result)]),
+    "ipm_batch_size": (ctypes.c_int, [_P]),
+    "ipm_batch_member": (_P, [_P, ctypes.c_int]),
+    "ipm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "ipm_destroy_batch": (None, [_P]),
     "gapply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
     "ipm_last_error": (ctypes.c_char_p, [_P]),
     "ipm_destroy": (None, [_P]),
@@ -209,6 +218,49 @@ def ipm_profile_get(h, k):
     n, ms = ctypes.c_int64(), ctypes.c_double()
     _check(load().ipm_profile_get(h, int(k), ctypes.byref(n), ctypes.byref(ms)), h)
     return n.value, ms.value
+
+
+def ipm_create_batch(problems, options=None, stream=None):
+    """problems: list of (dims, mask, y, lam).  Returns a batch handle (int)."""
+    lib = load()
+    count = len(problems)
+    nd = (ctypes.c_int * count)(*[len(p[0]) for p in problems])
+    flat = []
+    for p in problems:
+        flat += [int(v) for v in p[0]] + [0] * (3 - len(p[0]))
+    dims = (ctypes.c_int64 * (3 * count))(*flat)
+    masks = (_P * count)(*[addr(p[1]) for p in problems])
+    ys = (_P * count)(*[addr(p[2]) for p in problems])
+    lams = (ctypes.c_double * count)(*[float(p[3]) for p in problems])
+    b = _P()
+    st = lib.ipm_create_batch(ctypes.byref(b), count, nd, dims, masks, ys, lams,
+                              ctypes.byref(options) if options is not None else None, stream)
+    _check(st, None)
+    return b.value
+
+
+def ipm_solve_batch(b, check=True):
+    lib = load()
+    count = lib.ipm_batch_size(b)
+    res = (ipm_result * count)()
+    st = lib.ipm_solve_batch(b, res)
+    if check and st not in (IPM_OK, IPM_KRYLOV_MAXITER):
+        m = lib.ipm_batch_last_error(b)
+        raise IpmError(st, m.decode() if m else "")
+    out = []
+    for r in res:
+        d = r.as_dict()
+        d["lambda"] = d.pop("lambda_")
+        out.append(d)
+    return out
+
+
+def ipm_batch_member(b, i):
+    return load().ipm_batch_member(b, int(i))
+
+
+def ipm_destroy_batch(b):
+    load().ipm_destroy_batch(b)
 
 
 def gapply_noalloc(dims, mask, p, q, stream=None):

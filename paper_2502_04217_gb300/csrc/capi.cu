@@ -4,6 +4,8 @@
 // fft_passes.cu and ipm_kernels.cu; the host only queues launches and reads
 // the device scalars where it has to decide (IPM stop, PCG chunk boundaries).
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -49,7 +51,8 @@ bool factor_ok(int L) {
   return m == 1;
 }
 
-// Radices for length L: 8s, then a 4 and/or 2 (or, with a factor 3, 4s, 2s, then 3 last).
+// Radices for length L: with element budget E per thread, 8s (E = 8), then 4s
+// (E divisible by 4), then 2s, and a single 3 last when L has a factor 3.
 FftPlan make_plan(int L, int E) {
   FftPlan p{};
   p.L = L;
@@ -57,7 +60,7 @@ FftPlan make_plan(int L, int E) {
   bool three = (m % 3 == 0);
   if (three) m /= 3;
   while (E % 8 == 0 && m % 8 == 0) { p.radix[p.nst++] = 8; m /= 8; }
-  while (m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
+  while (E % 4 == 0 && m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
   if (three) p.radix[p.nst++] = 3;
   return p;
@@ -189,67 +192,162 @@ ipm_status make_tables(sdft_ipm* h, int L, const void** t64, const void** t32) {
   return IPM_OK;
 }
 
-// Choose pencils per tile P (power of two) for a pass of `npen` pencils of FFT
-// length L held in `rows` smem rows of element size esz.
-void plan_tile(PassCfg& c, int L, int rows, long long npen, bool fp32) {
+// Tile configuration of a pass: FFT length L, `rows` shared-memory rows, npen
+// pencils, element budget E per thread, P pencils per tile.  Returns false when
+// the combination is not launchable (P * L must be a multiple of E, at most 512
+// threads, at most 200 KB of shared memory).
+bool make_cfg(PassCfg& c, int L, int rows, long long npen, bool fp32, int E, int P) {
   const int esz = fp32 ? 8 : 16;
-  c.E = (L % 3 == 0) ? 12 : 8;
-  c.plan = make_plan(L, c.E);
-  int P = fp32 ? 16 : 8;
-  const int Pmin = fp32 ? 4 : 2;
-  // fewer pencils per tile when the pass would otherwise leave SMs idle
-  while (P > Pmin && (npen + P - 1) / P < 2 * 152) P /= 2;
-  // P * L must be a multiple of E; the thread count P * L / E at most 1024; smem bounded
-  while ((P * L) % c.E != 0) P *= 2;
-  while (P > 1 && ((P * L) / c.E > 512 || (size_t)rows * (P + 1) * esz > 200 * 1024)) P /= 2;
+  if ((P * L) % E != 0 || (P * L) / E > 512 || (P * L) / E < 1) return false;
+  const int PP = (P >= (fp32 ? 16 : 8)) ? P + 1 : P;
+  if ((size_t)rows * PP * esz > 200 * 1024) return false;
+  c.E = E;
+  c.plan = make_plan(L, E);
   c.lgP = ilog2(P);
-  c.PP = (P >= (fp32 ? 16 : 8)) ? P + 1 : P;
-  c.nwork = (P * L) / c.E;
+  c.PP = PP;
+  c.nwork = (P * L) / E;
   c.threads = ((c.nwork + 31) / 32) * 32;
   if (c.threads < 64) c.threads = 64;
-  c.smem = (size_t)rows * c.PP * esz;
+  c.smem = (size_t)rows * PP * esz;
   c.npencils = npen;
+  return true;
+}
+
+// Default choice without timing: E = 8 (12 with a factor 3), P as large as keeps
+// two tiles per SM, at least 2 (FP64) or 4 (FP32).
+void plan_tile(PassCfg& c, int L, int rows, long long npen, bool fp32) {
+  const int E = (L % 3 == 0) ? 12 : 8;
+  int P = fp32 ? 16 : 8;
+  const int Pmin = fp32 ? 4 : 2;
+  while (P > Pmin && (npen + P - 1) / P < 2 * 152) P /= 2;
+  while ((P * L) % E != 0) P *= 2;
+  while (P > 1 && !make_cfg(c, L, rows, npen, fp32, E, P)) P /= 2;
+  make_cfg(c, L, rows, npen, fp32, E, P);
+}
+
+dim3 pass_grid(const Layout& L, int kind, long long npen, int lgP) {
+  if (kind == 1) return dim3((unsigned)((L.N1 + (1 << lgP) - 1) >> lgP), (unsigned)L.Hl);
+  return dim3((unsigned)((npen + (1 << lgP) - 1) >> lgP));
+}
+
+// Autotuner: time every launchable (E, P) of a pass on the handle's own work
+// buffer (the FFT core only, no prologue or epilogue) and keep the fastest.
+// Results are cached per (pass, length, rows, pencils, precision) for the process.
+struct TuneKey {
+  int kind, L, rows, fp32;
+  long long npen;
+  bool operator<(const TuneKey& o) const {
+    if (kind != o.kind) return kind < o.kind;
+    if (L != o.L) return L < o.L;
+    if (rows != o.rows) return rows < o.rows;
+    if (fp32 != o.fp32) return fp32 < o.fp32;
+    return npen < o.npen;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tuned;       // -> (E, P)
+
+ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long long npen, bool fp32) {
+  c.kind = kind;
+  plan_tile(c, L, rows, npen, fp32);
+  c.grid = pass_grid(h->lay, kind, npen, c.lgP);
+  if (h->opt.tile_e > 0 || h->opt.tile_p > 0) {
+    // forced shape (tests and experiments): keep the default for what is not forced
+    const int E = h->opt.tile_e > 0 ? h->opt.tile_e : c.E;
+    const int P = h->opt.tile_p > 0 ? h->opt.tile_p : (1 << c.lgP);
+    const bool e_ok = (L % 3 == 0) ? (E == 6 || E == 12) : (E == 4 || E == 8);
+    PassCfg t = c;
+    if (e_ok && make_cfg(t, L, rows, npen, fp32, E, P)) {
+      c = t;
+      c.grid = pass_grid(h->lay, kind, npen, c.lgP);
+    }
+    return IPM_OK;
+  }
+  if (!h->opt.autotune) return IPM_OK;
+  const TuneKey key{kind, L, rows, fp32 ? 1 : 0, npen};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      make_cfg(c, L, rows, npen, fp32, it->second.first, it->second.second);
+      c.grid = pass_grid(h->lay, kind, npen, c.lgP);
+      return IPM_OK;
+    }
+  }
+  const int Es[2] = {(L % 3 == 0) ? 12 : 8, (L % 3 == 0) ? 6 : 4};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  PassCfg best_c = c;
+  for (int E : Es) {
+    for (int P = 1; P <= 32; P *= 2) {
+      PassCfg t = c;
+      if (!make_cfg(t, L, rows, npen, fp32, E, P)) continue;
+      t.grid = pass_grid(h->lay, kind, npen, t.lgP);
+      PassArgs a{};
+      a.lay = h->lay;
+      a.plan = t.plan;
+      a.lgP = t.lgP;
+      a.PP = t.PP;
+      a.nwork = t.nwork;
+      a.npencils = npen;
+      a.tw = t.tw;
+      a.twN = t.twN;
+      a.buf = h->d_U;
+      a.maskw = h->d_maskw;
+      a.inv_n = 1.0 / (double)h->lay.n;
+      a.out_scale = 1.0;
+      a.sc = h->d_sc;
+      const bool inv = (kind != 2);
+      CK(launch_pass(kind, inv, fp32, E, a, t.threads, t.smem, t.grid, h->st));     // warm-up
+      CK(cudaEventRecord(e0, h->st));
+      for (int r = 0; r < 5; ++r) CK(launch_pass(kind, inv, fp32, E, a, t.threads, t.smem, t.grid, h->st));
+      CK(cudaEventRecord(e1, h->st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; best_c = t; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c = best_c;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[key] = {c.E, 1 << c.lgP};
+  return IPM_OK;
 }
 
 ipm_status plan_passes(sdft_ipm* h, PassSet& ps, bool fp32) {
   const Layout& L = h->lay;
   const void *t64, *t32;
+  ipm_status s;
   // middle pass: h = Nl/2 complex FFT, Hl rows, M pencils
   {
     PassCfg& c = ps.mid;
-    c.kind = 2;
-    plan_tile(c, L.Nl / 2, L.Hl, L.M, fp32);
-    c.grid = dim3((unsigned)((L.M + (1 << c.lgP) - 1) >> c.lgP));
-    ipm_status s = make_tables(h, L.Nl / 2, &t64, &t32);
-    if (s != IPM_OK) return s;
+    if ((s = make_tables(h, L.Nl / 2, &t64, &t32)) != IPM_OK) return s;
     c.tw = fp32 ? t32 : t64;
-    s = make_tables(h, L.Nl, &t64, &t32);
-    if (s != IPM_OK) return s;
+    if ((s = make_tables(h, L.Nl, &t64, &t32)) != IPM_OK) return s;
     c.twN = fp32 ? t32 : t64;
+    if ((s = tune_tile(h, c, 2, L.Nl / 2, L.Hl, L.M, fp32)) != IPM_OK) return s;
   }
   if (L.d >= 2) {
     // row pass along the contiguous in-plane axis: rows of length Lr
     const int Lr = (L.d == 3) ? L.N1 : L.N0;
     const long long nrows = L.H / Lr;
     PassCfg c;
-    c.kind = 0;
-    plan_tile(c, Lr, Lr, nrows, fp32);
-    c.grid = dim3((unsigned)((nrows + (1 << c.lgP) - 1) >> c.lgP));
-    ipm_status s = make_tables(h, Lr, &t64, &t32);
-    if (s != IPM_OK) return s;
+    if ((s = make_tables(h, Lr, &t64, &t32)) != IPM_OK) return s;
     c.tw = fp32 ? t32 : t64;
+    if ((s = tune_tile(h, c, 0, Lr, Lr, nrows, fp32)) != IPM_OK) return s;
     ps.row_inv = c;
     ps.row_fwd = c;
   }
   if (L.d == 3) {
-    PassCfg c;
-    c.kind = 1;
-    plan_tile(c, L.N0, L.N0, (long long)L.N1 * L.Hl, fp32);
     // column tiles cover P consecutive k1 of one plane
-    c.grid = dim3((unsigned)((L.N1 + (1 << c.lgP) - 1) >> c.lgP), (unsigned)L.Hl);
-    ipm_status s = make_tables(h, L.N0, &t64, &t32);
-    if (s != IPM_OK) return s;
+    PassCfg c;
+    if ((s = make_tables(h, L.N0, &t64, &t32)) != IPM_OK) return s;
     c.tw = fp32 ? t32 : t64;
+    if ((s = tune_tile(h, c, 1, L.N0, L.N0, (long long)L.N1 * L.Hl, fp32)) != IPM_OK) return s;
     ps.col_inv = c;
     ps.col_fwd = c;
   }
@@ -442,6 +540,9 @@ void ipm_default_options(ipm_options* o) {
   o->lambda_relative = 0;
   o->cg_chunk = 4;
   o->use_graph = 1;
+  o->autotune = 1;
+  o->tile_e = 0;
+  o->tile_p = 0;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -490,11 +591,12 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   CKC(dalloc(h, &h->d_y, (size_t)L.n * sizeof(double)));
   CKC(dalloc(h, &h->d_maskw, (size_t)((L.Nl + 31) / 32) * L.M * sizeof(uint32_t)));
   double** vec2[] = {&h->w.beta, &h->w.z, &h->w.s1, &h->w.s2, &h->w.nu1, &h->w.nu2, &h->w.c, &h->w.Gb,
-                     &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->d_tmp};
+                     &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->w.is1, &h->w.is2, &h->d_tmp};
   for (double** p : vec2) CKC(dalloc(h, p, v2));
   double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q};
   for (double** p : vec4) CKC(dalloc(h, p, v4));
   CKC(dalloc(h, &h->d_U, (size_t)L.H * 2 * sizeof(double)));
+  CKC(cudaMemsetAsync(h->d_U, 0, (size_t)L.H * 2 * sizeof(double), h->st));
   CKC(dalloc(h, &h->d_sc, sizeof(DevScalars)));
   CKC(cudaMemsetAsync(h->d_sc, 0, sizeof(DevScalars), h->st));
   {
@@ -666,10 +768,28 @@ ipm_status queue_step(sdft_ipm* h) {
   return IPM_OK;
 }
 
-// Capture the whole IPM loop into a graph:
+// Queue, on the stream h->st that is being captured, the whole IPM loop:
 //   WHILE (c_ipm):  G beta -> certificate (writes c_ipm) -> prepare (writes c_cg)
 //                   WHILE (c_cg): K p passes -> pcg_update (writes c_cg)
 //                   step length -> step update
+ipm_status capture_solve_loop(sdft_ipm* h) {
+  ipm_status s = make_cond(h, &h->c_ipm, 1u);
+  if (s != IPM_OK) return s;
+  return add_while(h, h->c_ipm, h->cap[1], [h]() -> ipm_status {
+    ipm_status r = make_cond(h, &h->c_cg, 0u);
+    if (r != IPM_OK) return r;
+    if ((r = queue_residual_and_test(h, LoopCtl{h->c_ipm, 1})) != IPM_OK) return r;
+    if ((r = queue_prepare(h, LoopCtl{h->c_cg, 1})) != IPM_OK) return r;
+    r = add_while(h, h->c_cg, h->cap[2], [h]() -> ipm_status {
+      return queue_pcg_iteration(h, LoopCtl{h->c_cg, 1});
+    });
+    if (r != IPM_OK) return r;
+    return queue_step(h);
+  });
+}
+
+// The solve loop of one handle as a graph of its own (the start point is set
+// before each launch, outside the graph).
 ipm_status build_graph(sdft_ipm* h) {
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
@@ -678,20 +798,7 @@ ipm_status build_graph(sdft_ipm* h) {
   ipm_status s;
   {
     StreamSwap sw(h, h->cap[0]);
-    s = make_cond(h, &h->c_ipm, 1u);
-    if (s == IPM_OK) {
-      s = add_while(h, h->c_ipm, h->cap[1], [h]() -> ipm_status {
-        ipm_status r = make_cond(h, &h->c_cg, 0u);
-        if (r != IPM_OK) return r;
-        if ((r = queue_residual_and_test(h, LoopCtl{h->c_ipm, 1})) != IPM_OK) return r;
-        if ((r = queue_prepare(h, LoopCtl{h->c_cg, 1})) != IPM_OK) return r;
-        r = add_while(h, h->c_cg, h->cap[2], [h]() -> ipm_status {
-          return queue_pcg_iteration(h, LoopCtl{h->c_cg, 1});
-        });
-        if (r != IPM_OK) return r;
-        return queue_step(h);
-      });
-    }
+    s = capture_solve_loop(h);
   }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap[0], &g);
@@ -701,6 +808,29 @@ ipm_status build_graph(sdft_ipm* h) {
   CK(cudaGraphInstantiate(&h->gexec, h->graph, 0));
   h->graph_valid = true;
   return IPM_OK;
+}
+
+ipm_status fill_result(sdft_ipm* h, ipm_result* res, double seconds) {
+  const DevScalars& sc = *h->h_sc;
+  ipm_status final_status = sc.ipm_status == 0 ? IPM_OK : (sc.ipm_status == 4 ? IPM_MAXITER : IPM_NUMERICAL);
+  if (final_status == IPM_OK && sc.cg_cap_hit) final_status = IPM_KRYLOV_MAXITER;
+  if (res) {
+    res->status = final_status;
+    res->ipm_iters = sc.ipm_it;
+    res->cg_iters_total = sc.cg_total;
+    res->cg_iters_max = sc.cg_max;
+    res->primal = sc.primal;
+    res->dual = sc.dual;
+    res->rel_gap = sc.gap;
+    res->mu = sc.mu;
+    res->lambda = sc.lambda;
+    res->lambda_max = sc.cmax;
+    res->kkt_products = sc.cg_total + sc.ipm_it + 1;
+    res->seconds = seconds;
+  }
+  if (final_status == IPM_NUMERICAL) h->err = "non-finite value or breakdown of positive definiteness";
+  if (final_status == IPM_MAXITER) h->err = "IPM iteration cap reached before gap_tol";
+  return final_status;
 }
 
 }  // namespace
@@ -743,26 +873,7 @@ ipm_status ipm_solve(sdft_ipm* h, ipm_result* res) {
   if ((s = read_scalars(h)) != IPM_OK) return s;
   prof_collect(h);
   h->sigma_ready = true;
-  const DevScalars& sc = *h->h_sc;
-  ipm_status final_status = sc.ipm_status == 0 ? IPM_OK : (sc.ipm_status == 4 ? IPM_MAXITER : IPM_NUMERICAL);
-  if (final_status == IPM_OK && sc.cg_cap_hit) final_status = IPM_KRYLOV_MAXITER;
-  if (res) {
-    res->status = final_status;
-    res->ipm_iters = sc.ipm_it;
-    res->cg_iters_total = sc.cg_total;
-    res->cg_iters_max = sc.cg_max;
-    res->primal = sc.primal;
-    res->dual = sc.dual;
-    res->rel_gap = sc.gap;
-    res->mu = sc.mu;
-    res->lambda = sc.lambda;
-    res->lambda_max = sc.cmax;
-    res->kkt_products = sc.cg_total + sc.ipm_it + 1;
-    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
-  if (final_status == IPM_NUMERICAL) h->err = "non-finite value or breakdown of positive definiteness";
-  if (final_status == IPM_MAXITER) h->err = "IPM iteration cap reached before gap_tol";
-  return final_status;
+  return fill_result(h, res, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
 }
 
 ipm_status gapply(sdft_ipm* h, const double* p, double* q) {
@@ -927,3 +1038,150 @@ namespace sdft {
 // Message returned by ipm_last_error(NULL) (used by entry points without a handle).
 void record_error(const char* msg) { g_create_error = msg; }
 }  // namespace sdft
+
+// ---------------------------------------------------------------------------
+// Batched solve: many independent problems, one graph launch.  Each problem is
+// a full handle; the batch graph forks one branch per problem (start point +
+// its nested IPM / PCG WHILE loops) and joins them, so the problems' kernels run
+// concurrently and the whole batch needs a single launch and a single wait.
+// ---------------------------------------------------------------------------
+struct sdft_ipm_batch {
+  std::vector<sdft_ipm*> members;
+  cudaStream_t st = nullptr;       // caller's stream
+  cudaStream_t cap = nullptr;      // capture origin
+  std::vector<cudaEvent_t> ev;     // join events (one per member) + the fork event
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool valid = false;
+  std::string err;
+};
+
+namespace {
+
+ipm_status batch_fail(sdft_ipm_batch* b, const std::string& msg, ipm_status st) {
+  if (b) b->err = msg;
+  g_create_error = msg;
+  return st;
+}
+
+#define CKB(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return batch_fail(b, std::string(#call) + ": " + cudaGetErrorString(e_), \
+                                             IPM_ERR_CUDA);                                         \
+  } while (0)
+
+ipm_status build_batch_graph(sdft_ipm_batch* b) {
+  if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  b->valid = false;
+  const int count = (int)b->members.size();
+  CKB(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+  ipm_status s = IPM_OK;
+  CKB(cudaEventRecord(b->ev[count], b->cap));          // fork point
+  for (int i = 0; i < count && s == IPM_OK; ++i) {
+    sdft_ipm* h = b->members[i];
+    CKB(cudaStreamWaitEvent(h->cap[0], b->ev[count], 0));
+    {
+      StreamSwap sw(h, h->cap[0]);
+      Reduce red{h->d_partials, h->d_counter};
+      cudaError_t e = k_init_point(h->lay, h->w, red, h->d_sc, h->opt.sigma, h->st);
+      if (e != cudaSuccess) s = batch_fail(b, std::string("init: ") + cudaGetErrorString(e), IPM_ERR_CUDA);
+      if (s == IPM_OK) s = capture_solve_loop(h);
+      if (s != IPM_OK && b->err.empty()) b->err = h->err;
+    }
+    if (s == IPM_OK) {
+      CKB(cudaEventRecord(b->ev[i], h->cap[0]));
+      CKB(cudaStreamWaitEvent(b->cap, b->ev[i], 0));    // join
+    }
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (s != IPM_OK) { if (g) cudaGraphDestroy(g); return s; }
+  CKB(e);
+  b->graph = g;
+  CKB(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+  b->valid = true;
+  return IPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ipm_status ipm_create_batch(sdft_ipm_batch** out, int count, const int* ndims, const int64_t* dims,
+                            const uint8_t* const* masks, const double* const* ys, const double* lambdas,
+                            const ipm_options* opt, void* stream) {
+  g_create_error.clear();
+  if (!out) return fail_arg(nullptr, "out must not be NULL");
+  *out = nullptr;
+  if (count < 1 || !ndims || !dims || !masks || !ys || !lambdas)
+    return fail_arg(nullptr, "count must be positive and every array non-NULL");
+  sdft_ipm_batch* b = new sdft_ipm_batch();
+  b->st = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    sdft_ipm* h = nullptr;
+    ipm_status s = ipm_create(&h, ndims[i], dims + 3 * (size_t)i, masks[i], ys[i], lambdas[i], opt, stream);
+    if (s != IPM_OK) {
+      const std::string msg = "problem " + std::to_string(i) + ": " + g_create_error;
+      ipm_destroy_batch(b);
+      g_create_error = msg;
+      return s;
+    }
+    b->members.push_back(h);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  b->ev.resize(count + 1, nullptr);
+  for (int i = 0; i <= count && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("batch streams/events: ") + cudaGetErrorString(e);
+    ipm_destroy_batch(b);
+    return IPM_ERR_CUDA;
+  }
+  *out = b;
+  return IPM_OK;
+}
+
+ipm_status ipm_solve_batch(sdft_ipm_batch* b, ipm_result* results) {
+  if (!b) return fail_arg(nullptr, "batch is NULL");
+  const auto t0 = std::chrono::steady_clock::now();
+  ipm_status s;
+  if (!b->valid && (s = build_batch_graph(b)) != IPM_OK) return s;
+  CKB(cudaGraphLaunch(b->gexec, b->st));
+  CKB(cudaStreamSynchronize(b->st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  ipm_status worst = IPM_OK;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    sdft_ipm* h = b->members[i];
+    if ((s = read_scalars(h)) != IPM_OK) return batch_fail(b, h->err, s);
+    h->point_set = false;
+    h->sigma_ready = true;
+    const ipm_status si = fill_result(h, results ? &results[i] : nullptr, secs);
+    if (si != IPM_OK && (worst == IPM_OK || worst == IPM_KRYLOV_MAXITER)) worst = si;
+  }
+  if (worst != IPM_OK) b->err = "at least one problem did not reach gap_tol (see its result)";
+  return worst;
+}
+
+sdft_ipm* ipm_batch_member(sdft_ipm_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->members.size()) return nullptr;
+  return b->members[i];
+}
+
+int ipm_batch_size(const sdft_ipm_batch* b) { return b ? (int)b->members.size() : 0; }
+
+const char* ipm_batch_last_error(const sdft_ipm_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void ipm_destroy_batch(sdft_ipm_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (sdft_ipm* h : b->members) ipm_destroy(h);
+  delete b;
+}
+
+}  // extern "C"
