@@ -355,6 +355,7 @@ def run_ours(args):
             cpu = {"value": t, "unit": "s", "cores": _cores(), "kind": "oracle",
                    "sample": f"one full oracle solve (numpy FP64, direct DFT) of the same {args.workload} "
                              "workload to gap 1e-6"}
+    tiles = binding.ipm_describe(h)
     binding.ipm_destroy(h)
     if rank == 0:
         line = {
@@ -369,6 +370,7 @@ def run_ours(args):
                       "kkt_products": res["kkt_products"], "rel_gap": res["rel_gap"], "primal": res["primal"],
                       "step_ms": [round(x, 3) for x in step_ms]},
             "kkt_matvec": kkt,
+            "fft_tiles": tiles,
         }
         print(json.dumps(line))
     if dist:

@@ -248,6 +248,57 @@ const char* ipm_batch_last_error(const sdft_ipm_batch* b);
 /* Destroy the batch and every member handle.  NULL is accepted. */
 void ipm_destroy_batch(sdft_ipm_batch* b);
 
+/* ---- learned warm start ---------------------------------------------------
+ * Not in the paper (which cold-starts its IPM).  A 4-layer 3D convolution
+ * network (3x3x3 kernels, 8 -> 32 -> 32 -> 32 -> 4 channels, BF16 weights and
+ * activations, FP32 accumulation on tensor cores) runs over the grid of
+ * half-spectrum slots of a handle.  Its inputs per slot are
+ * [c0, c1, soft(c0,1), soft(c1,1), |c|, kl/(Hl-1), f0, f1] with (c0, c1) the
+ * slot's coordinates of M_perp^T b / lambda and f_i = min(k_i, N_i - k_i)/(N_i/2);
+ * its outputs y correct the soft-threshold guess, beta0 = lambda (soft(c) + y[0:2]),
+ * and give logits y[2:4] of "coordinate non-zero".  ws_predict turns them into a
+ * strictly interior start point with every s_i nu_i = mu0 = mu_scale lambda^2:
+ * z = |beta0| + (mu0/lambda)(2 - p), s1 = z + beta0, s2 = z - beta0, nu = mu0 / s.
+ * The cold start of ipm_solve remains the fallback: a handle solves from the
+ * predicted point only on the next ipm_solve after ws_predict. */
+typedef struct sdft_ws sdft_ws;
+
+/* A network with He-uniform weights from a counter-based hash of seed. */
+ipm_status ws_create(sdft_ws** out, uint64_t seed, void* stream);
+void ws_destroy(sdft_ws* net);
+/* Number of FP32 parameters; copy them out / in (host or device pointers). */
+int64_t ws_num_params(const sdft_ws* net);
+ipm_status ws_get_params(sdft_ws* net, float* dst);
+ipm_status ws_set_params(sdft_ws* net, const float* src);
+/* Gradients of the last ws_train_step (same layout as the parameters). */
+ipm_status ws_get_grads(sdft_ws* net, float* dst);
+/* Outputs y of the network on handle h (FP32, 8 per slot, 4 used; y may be NULL). */
+ipm_status ws_forward(sdft_ws* net, sdft_ipm* h, float* y);
+/* Predict and set the start point of h's next ipm_solve (mu_scale > 0). */
+ipm_status ws_predict(sdft_ws* net, sdft_ipm* h, double mu_scale);
+/* One training step on problem h with target beta_star (device, beta layout,
+ * e.g. from ipm_get_point after a solve): loss = mean squared error of y[0:2]
+ * against beta* / lambda - soft(c/lambda, 1) plus 0.1 x mean cross-entropy of the
+ * logits against 1[|beta*| > 1e-6 lambda], over LASSO coordinates.  Gradients by
+ * the hand-written backward kernels; an Adam step (betas 0.9, 0.999) when lr > 0.
+ * *loss (may be NULL) receives the loss before the step. */
+ipm_status ws_train_step(sdft_ws* net, sdft_ipm* h, const double* beta_star, float lr, double* loss);
+/* The convolution kernels on caller buffers (device pointers, BF16 as uint16):
+ * x [V][cin], w [27][cout][cin] (tap (a+1)*9 + (b+1)*3 + (c+1) for offset (a,b,c)),
+ * bias [cout] or NULL, aux [V][cout] or NULL (output multiplied by aux > 0),
+ * y [V][cout] FP32; (cin, cout) in {16, 32} x {8, 32}; V = d0 d1 d2. */
+ipm_status ws_conv_forward(int cin, int cout, int d0, int d1, int d2, const uint16_t* x, const uint16_t* w,
+                           const float* bias, int relu, const uint16_t* aux, float* y, void* stream);
+/* Weight and bias gradients of such a convolution: dw[t][o][i] = sum_v dy[v][o]
+ * x[v + off(t)][i] for o < mout (dy [V][m], m in {16, 32}), db[o] = sum_v dy[v][o]. */
+ipm_status ws_conv_wgrad(int cin, int m, int mout, int d0, int d1, int d2, const uint16_t* x, const uint16_t* dy,
+                         float* dw, float* db, void* stream);
+
+/* The chosen FFT tile plan of every pass (FP64 and FP32 variants) as a JSON
+ * object written into buf (at most len bytes, NUL-terminated); returns the
+ * full length.  For logs and benchmarks. */
+int ipm_describe(const sdft_ipm* h, char* buf, int len);
+
 /* Message of the last failure on this handle (or of the last failed create
  * when h is NULL).  Owned by the library. */
 const char* ipm_last_error(const sdft_ipm* h);

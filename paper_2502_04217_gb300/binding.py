@@ -75,7 +75,19 @@ _SIGNATURES = {
     "ipm_batch_member": (_P, [_P, ctypes.c_int]),
     "ipm_batch_last_error": (ctypes.c_char_p, [_P]),
     "ipm_destroy_batch": (None, [_P]),
+    "ws_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_uint64, _P]),
+    "ws_destroy": (None, [_P]),
+    "ws_num_params": (ctypes.c_int64, [_P]),
+    "ws_get_params": (ctypes.c_int, [_P, _P]),
+    "ws_set_params": (ctypes.c_int, [_P, _P]),
+    "ws_get_grads": (ctypes.c_int, [_P, _P]),
+    "ws_forward": (ctypes.c_int, [_P, _P, _P]),
+    "ws_predict": (ctypes.c_int, [_P, _P, ctypes.c_double]),
+    "ws_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
+    "ws_conv_forward": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
+    "ws_conv_wgrad": (ctypes.c_int, [ctypes.c_int] * 6 + [_P, _P, _P, _P, _P]),
     "gapply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
+    "ipm_describe": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int]),
     "ipm_last_error": (ctypes.c_char_p, [_P]),
     "ipm_destroy": (None, [_P]),
 }
@@ -263,10 +275,68 @@ def ipm_destroy_batch(b):
     load().ipm_destroy_batch(b)
 
 
+def ws_create(seed=0, stream=None):
+    n = _P()
+    _check(load().ws_create(ctypes.byref(n), int(seed), stream), None)
+    return n.value
+
+
+def ws_destroy(n):
+    load().ws_destroy(n)
+
+
+def ws_num_params(n):
+    return int(load().ws_num_params(n))
+
+
+def ws_get_params(n, dst):
+    return _check(load().ws_get_params(n, addr(dst)), None)
+
+
+def ws_set_params(n, src):
+    return _check(load().ws_set_params(n, addr(src)), None)
+
+
+def ws_get_grads(n, dst):
+    return _check(load().ws_get_grads(n, addr(dst)), None)
+
+
+def ws_forward(n, h, y=None):
+    return _check(load().ws_forward(n, h, addr(y)), None)
+
+
+def ws_predict(n, h, mu_scale=1e-3):
+    return _check(load().ws_predict(n, h, float(mu_scale)), None)
+
+
+def ws_train_step(n, h, beta_star, lr):
+    loss = ctypes.c_double()
+    _check(load().ws_train_step(n, h, addr(beta_star), float(lr), ctypes.byref(loss)), None)
+    return loss.value
+
+
+def ws_conv_forward(cin, cout, dims, x, w, bias, relu, aux, y, stream=None):
+    return _check(load().ws_conv_forward(cin, cout, *[int(d) for d in dims], addr(x), addr(w), addr(bias),
+                                         int(relu), addr(aux), addr(y), stream), None)
+
+
+def ws_conv_wgrad(cin, m, mout, dims, x, dy, dw, db, stream=None):
+    return _check(load().ws_conv_wgrad(cin, m, mout, *[int(d) for d in dims], addr(x), addr(dy), addr(dw),
+                                       addr(db), stream), None)
+
+
 def gapply_noalloc(dims, mask, p, q, stream=None):
     """Handle-free, allocation-free q = M_perp^T M_perp p (device mask, p, q)."""
     d = (ctypes.c_int64 * len(dims))(*[int(v) for v in dims])
     return _check(load().gapply_noalloc(len(dims), d, addr(mask), addr(p), addr(q), stream), None)
+
+
+def ipm_describe(h):
+    """The FFT tile plan of the handle (dict)."""
+    import json
+    buf = ctypes.create_string_buffer(4096)
+    load().ipm_describe(h, buf, 4096)
+    return json.loads(buf.value.decode())
 
 
 def ipm_last_error(h=None):

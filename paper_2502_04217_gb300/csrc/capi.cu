@@ -1012,6 +1012,28 @@ ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms) {
   return IPM_OK;
 }
 
+int ipm_describe(const sdft_ipm* h, char* buf, int len) {
+  if (!h || !buf || len <= 0) return 0;
+  std::string out = "{";
+  auto one = [&](const char* name, const PassCfg& c) {
+    char tmp[256];
+    snprintf(tmp, sizeof(tmp), "\"%s\": {\"L\": %d, \"E\": %d, \"P\": %d, \"threads\": %d, \"blocks\": %u, "
+             "\"smem\": %zu}", name, c.plan.L, c.E, 1 << c.lgP, c.threads, c.grid.x * c.grid.y, c.smem);
+    if (out.size() > 1) out += ", ";
+    out += tmp;
+  };
+  for (int t = 0; t < 2; ++t) {
+    const PassSet& ps = t ? h->pass32 : h->pass64;
+    const std::string pre = t ? "fp32_" : "fp64_";
+    one((pre + "middle").c_str(), ps.mid);
+    if (h->lay.d >= 2) one((pre + "row").c_str(), ps.row_fwd);
+    if (h->lay.d == 3) one((pre + "col").c_str(), ps.col_fwd);
+  }
+  out += "}";
+  snprintf(buf, (size_t)len, "%s", out.c_str());
+  return (int)out.size();
+}
+
 const char* ipm_last_error(const sdft_ipm* h) {
   if (!h) return g_create_error.c_str();
   return h->err.c_str();
@@ -1185,3 +1207,19 @@ void ipm_destroy_batch(sdft_ipm_batch* b) {
 }
 
 }  // extern "C"
+
+namespace sdft {
+// Internal view of a handle for the warm-start code (warmstart.cu).
+bool handle_view(sdft_ipm* h, HandleView* v) {
+  if (!h || !v) return false;
+  v->lay = h->lay;
+  v->w = h->w;
+  v->sc = h->d_sc;
+  v->st = h->st;
+  v->partials = h->d_partials;
+  v->counter = h->d_counter;
+  return true;
+}
+// The next ipm_solve starts from the point now in the handle's vectors.
+void handle_point_set(sdft_ipm* h) { h->point_set = true; }
+}  // namespace sdft

@@ -31,6 +31,16 @@ struct LoopCtl {
   int use;
 };
 
+// What other parts of the library (the warm start) may use of a handle.
+struct HandleView {
+  Layout lay;
+  IpmVectors w;
+  DevScalars* sc;
+  cudaStream_t st;
+  double* partials;
+  unsigned* counter;
+};
+
 cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, DevScalars* sc, cudaStream_t st);
 cudaError_t k_observed_norm(const double* y, const uint8_t* mask, long long n, Reduce red, DevScalars* sc, cudaStream_t st);
 cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Reduce red, DevScalars* sc, cudaStream_t st);

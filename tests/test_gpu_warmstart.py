@@ -1,0 +1,161 @@
+"""Learned warm start: BF16 tensor-core kernels against the FP64 CPU reference,
+and what the trained network gains over the cold start (needs a GPU).
+
+Tolerances: conv inputs are BF16-exact, so the kernels differ from the FP64
+reference only by FP32 accumulation over at most 27 x 32 = 864 products
+(relative ~1e-6; we allow 1e-4 of the output scale).  The whole-network
+gradient also rounds every activation and gradient to BF16 (8-bit mantissa,
+relative 2^-9 per rounding, four layers): we require relative norm error below
+5 % and cosine similarity above 0.995 against the FP64 reference fed the same
+BF16-rounded weights.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import warmstart as ows
+from oracle.lasso import Problem
+from paper_2502_04217_gb300 import binding
+from paper_2502_04217_gb300.synth import make_problem
+
+from layout import ghost_mask, oracle_to_lib
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+def dev_bf16(a):
+    return bf16(a).cuda().contiguous()
+
+
+def as_u16(t):
+    return t.view(torch.int16)
+
+
+@pytest.mark.parametrize("cin,cout,dims", [(32, 32, (3, 5, 70)), (16, 32, (2, 3, 13)), (32, 8, (4, 2, 64)),
+                                           (16, 8, (1, 1, 5)), (32, 32, (2, 2, 129))])
+def test_conv_forward_matches_reference(cin, cout, dims):
+    rng = np.random.default_rng(1)
+    x = bf16(rng.standard_normal(dims + (cin,)))
+    w = bf16(0.2 * rng.standard_normal((27, cout, cin)))
+    b = rng.standard_normal(cout).astype(np.float32)
+    aux = bf16(rng.standard_normal(dims + (cout,)))
+    for relu, use_aux in [(0, False), (1, False), (0, True)]:
+        y = torch.empty(int(np.prod(dims)) * cout, dtype=torch.float32, device="cuda")
+        binding.ws_conv_forward(cin, cout, dims, as_u16(x.cuda().contiguous()), as_u16(w.cuda().contiguous()),
+                                torch.as_tensor(b).cuda(), relu, as_u16(aux.cuda().contiguous()) if use_aux else None, y)
+        W = w.float().numpy().reshape(3, 3, 3, cout, cin).transpose(0, 1, 2, 4, 3)
+        ref = ows.conv3d(x.float().numpy().astype(np.float64), W.astype(np.float64), b.astype(np.float64))
+        if relu:
+            ref = np.maximum(ref, 0)
+        if use_aux:
+            ref = ref * (aux.float().numpy() > 0)
+        got = y.cpu().numpy().reshape(dims + (cout,))
+        assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("cin,m,mout,dims", [(32, 32, 32, (3, 4, 70)), (16, 32, 32, (2, 3, 17)),
+                                             (32, 16, 8, (3, 2, 65)), (16, 16, 16, (1, 1, 9))])
+def test_conv_weight_gradient_matches_reference(cin, m, mout, dims):
+    rng = np.random.default_rng(2)
+    x = bf16(rng.standard_normal(dims + (cin,)))
+    dy = bf16(rng.standard_normal(dims + (m,)))
+    dw = torch.empty(27 * mout * cin, dtype=torch.float32, device="cuda")
+    db = torch.empty(mout, dtype=torch.float32, device="cuda")
+    binding.ws_conv_wgrad(cin, m, mout, dims, as_u16(x.cuda().contiguous()), as_u16(dy.cuda().contiguous()), dw, db)
+    W0 = np.zeros((3, 3, 3, cin, m))
+    _, dW, dB = ows.conv3d_backward(x.float().numpy().astype(np.float64), W0, dy.float().numpy().astype(np.float64))
+    ref = dW.reshape(27, cin, m).transpose(0, 2, 1)[:, :mout, :]
+    got = dw.cpu().numpy().reshape(27, mout, cin)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 1e-4 * scale
+    assert np.abs(db.cpu().numpy() - dB[:mout]).max() <= 1e-4 * max(1.0, np.abs(dB).max())
+
+
+def _layers(params_flat):
+    """Split the FP32 parameter vector into the oracle's (W, b) list, weights rounded to BF16."""
+    shapes = [(16, 32, 8, 32), (32, 32, 32, 32), (32, 32, 32, 32), (32, 8, 32, 4)]  # cin, cout, cin_real, cout_real
+    out, o = [], 0
+    for cin, cout, cir, cor in shapes:
+        W = params_flat[o:o + 27 * cout * cin].reshape(27, cout, cin)
+        o += 27 * cout * cin
+        b = params_flat[o:o + cout]
+        o += cout
+        Wb = torch.as_tensor(W).to(torch.bfloat16).float().numpy().astype(np.float64)
+        out.append((Wb.reshape(3, 3, 3, cout, cin).transpose(0, 1, 2, 4, 3)[:, :, :, :cir, :cor].copy(),
+                    b[:cor].astype(np.float64)))
+    return out
+
+
+def test_network_gradient_matches_reference():
+    dims = (8, 12, 16)
+    w = make_problem("custom", dims=dims, missing=0.15, seed=60)
+    opt = binding.default_options(lambda_relative=1, gap_tol=1e-8)
+    h = binding.ipm_create(dims, w.mask, w.y, 0.1, opt)
+    net = binding.ws_create(seed=7)
+    try:
+        res = binding.ipm_solve(h)
+        H, n = binding.ipm_sizes(h)
+        pt = [torch.empty(2 * H, dtype=torch.float64, device="cuda") for _ in range(6)]
+        binding.ipm_get_point(h, pt)
+        bstar = pt[0]
+        loss = binding.ws_train_step(net, h, bstar, 0.0)
+        npar = binding.ws_num_params(net)
+        params = np.empty(npar, dtype=np.float32)
+        grads = np.empty(npar, dtype=np.float32)
+        binding.ws_get_params(net, params)
+        binding.ws_get_grads(net, grads)
+        y = torch.empty(H * 8, dtype=torch.float32, device="cuda")
+        binding.ws_forward(net, h, y)
+        # reference on the same slot grid
+        prob = Problem(dims, w.mask.astype(bool), w.y, res["lambda"])
+        c_lib = oracle_to_lib(h, prob.c, dims).cpu().numpy()
+        x = ows.features(c_lib, res["lambda"], dims)
+        x = torch.as_tensor(x.astype(np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+        layers = _layers(params)
+        yr, acts = ows.forward(x, layers)
+        t, sup = ows.targets(c_lib, bstar.cpu().numpy(), res["lambda"], dims, ghost_mask(h, dims))
+        lref, dy = ows.loss_and_grad(yr, t, sup)
+        gref = ows.backward(acts, layers, dy)
+        ygot = y.cpu().numpy().reshape(yr.shape[:3] + (8,))[..., :4]
+        assert np.linalg.norm(ygot - yr) <= 0.02 * np.linalg.norm(yr)
+        assert abs(loss - lref) <= 0.02 * abs(lref)
+        got, ref = [], []
+        o = 0
+        for (cin, cout, cir, cor), (dWr, dbr) in zip([(16, 32, 8, 32), (32, 32, 32, 32), (32, 32, 32, 32), (32, 8, 32, 4)],
+                                                     gref):
+            G = grads[o:o + 27 * cout * cin].reshape(3, 3, 3, cout, cin).transpose(0, 1, 2, 4, 3)[:, :, :, :cir, :cor]
+            o += 27 * cout * cin
+            gb = grads[o:o + cout][:cor]
+            o += cout
+            got += [G.ravel(), gb]
+            ref += [dWr.ravel(), dbr]
+        got, ref = np.concatenate(got), np.concatenate(ref)
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref))
+        assert rel < 0.05 and cos > 0.995, (rel, cos)
+    finally:
+        binding.ws_destroy(net)
+        binding.ipm_destroy(h)
+
+
+def test_training_steps_reduce_the_loss():
+    dims = (16, 16, 16)
+    w = make_problem("custom", dims=dims, missing=0.1, seed=61)
+    opt = binding.default_options(lambda_relative=1, gap_tol=1e-8)
+    h = binding.ipm_create(dims, w.mask, w.y, 0.1, opt)
+    net = binding.ws_create(seed=8)
+    try:
+        binding.ipm_solve(h)
+        H, n = binding.ipm_sizes(h)
+        pt = [torch.empty(2 * H, dtype=torch.float64, device="cuda") for _ in range(6)]
+        binding.ipm_get_point(h, pt)
+        losses = [binding.ws_train_step(net, h, pt[0], 3e-3) for _ in range(30)]
+        assert losses[-1] < 0.5 * losses[0]
+    finally:
+        binding.ws_destroy(net)
+        binding.ipm_destroy(h)
