@@ -38,6 +38,9 @@ WORKLOADS = {
     "3d": ("3d 256^3 mixed IPM (FP32 FFT products in PCG, FP64 residual/diagonals/reductions): 5000 N(0,1) "
            "frequencies, background 1e-3, noise 0.01, radius-2 balls on a period-8 lattice, "
            "lambda = 0.05 lambda_max, gap 1e-6", "mixed"),
+    "warm512": ("512^3, 100000 frequencies, background 1e-3 and noise 0.01, radius-2 balls on a period-8 lattice, "
+                "lambda = 0.05 lambda_max, gap 1e-6: learned warm start (network inference included) + mixed "
+                "precision solve, against the cold-start FP64 solve of the same instance", "mixed"),
     "batch": ("batch of 48 independent 3D problems, sides drawn from {32,48,64,96,128}, 0.25% frequencies, "
               "Bragg-ball masks (period 8-16, radius 1-2, random offsets), noise 0.01, lambda = 0.05 lambda_max, "
               "gap 1e-6, mixed precision, all solved by one graph launch", "mixed"),
@@ -52,9 +55,10 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kkt", action="store_true")
-    ap.add_argument("--workload", choices=["1d", "2d", "3d", "batch"], default="2d",
+    ap.add_argument("--workload", choices=["1d", "2d", "3d", "batch", "warm512"], default="2d",
                     help="2d: 512^2 FP64 (default); 1d: n=256 FP64; 3d: 256^3 mixed precision; "
-                         "batch: 48 uneven 3D problems in one graph launch, mixed precision")
+                         "batch: 48 uneven 3D problems in one graph launch, mixed precision; "
+                         "warm512: 512^3, learned warm start + mixed precision against the cold FP64 solve")
     return ap.parse_args()
 
 
@@ -579,12 +583,84 @@ def run_batch(args):
     return 0
 
 
+def run_warm512(args):
+    """Config 5: warm-started mixed solve (inference included) vs cold FP64 solve, 512^3."""
+    import numpy as np
+    import torch
+
+    from paper_2502_04217_gb300 import binding
+    from paper_2502_04217_gb300 import warmstart as wsm
+    from paper_2502_04217_gb300.synth import make_problem
+
+    ws_n, rank, local = _dist()
+    torch.cuda.set_device(local)
+    binding.load()
+    stream = torch.cuda.current_stream()
+    w = make_problem("3d512", index=rank)
+    net = wsm.load(stream=stream.cuda_stream)
+    o64 = binding.default_options(precision=binding.IPM_FP64, gap_tol=GAP_TOL, lambda_relative=1)
+    o32 = binding.default_options(precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
+    mask_d = torch.from_numpy(np.ascontiguousarray(w.mask)).cuda()
+    y_d = torch.from_numpy(np.ascontiguousarray(w.y)).cuda()
+    h64 = binding.ipm_create(w.dims, mask_d, y_d, w.lam_rel, o64, stream=stream.cuda_stream)
+    h32 = binding.ipm_create(w.dims, mask_d, y_d, w.lam_rel, o32, stream=stream.cuda_stream)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    def warm():
+        binding.ws_predict(net, h32, 0.1)
+        return binding.ipm_solve(h32)
+
+    for _ in range(args.warmup):
+        warm()
+    binding.ipm_solve(h64)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    wt, rw = [], None
+    for _ in range(args.steps):
+        t, rw = timed(warm)
+        wt.append(t)
+    t64, r64 = timed(lambda: binding.ipm_solve(h64))
+    tcold32, rc32 = timed(lambda: binding.ipm_solve(h32))
+    clk = clocks.stop()
+    value = sum(wt) / len(wt)
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws_n, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32+f64", "data": "synthetic",
+        "config": {"workload": _workload_desc("warm512"), "dims": list(w.dims), "gap_tol": GAP_TOL,
+                   "network": "4-layer 3x3x3 conv, 32 channels, BF16, trained on 128^3 instances (weights file)",
+                   "l2": "inputs far larger than L2 (512^3)"},
+        "warm_vs_cold_fp64": value / t64, "cold_fp64_s": t64, "cold_mixed_s": tcold32,
+        "solve": {"warm_ipm_iters": rw["ipm_iters"], "cold_fp64_ipm_iters": r64["ipm_iters"],
+                  "cold_mixed_ipm_iters": rc32["ipm_iters"], "warm_rel_gap": rw["rel_gap"],
+                  "cold_fp64_rel_gap": r64["rel_gap"],
+                  "objective_rel_diff": abs(rw["primal"] - r64["primal"]) / abs(r64["primal"]),
+                  "step_s": [round(x, 4) for x in wt]},
+        "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }))
+    binding.ipm_destroy(h64)
+    binding.ipm_destroy(h32)
+    binding.ws_destroy(net)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "warm512":
+        return run_warm512(args)
     return run_ours(args)
 
 

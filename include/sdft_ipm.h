@@ -91,6 +91,12 @@ typedef struct {
                            launchable                                                         */
   int tile_p;           /* 0 (default): chosen as above; else force this many pencils per
                            tile (a power of two) wherever launchable                          */
+  int refine_every;     /* IPM_MIXED only.  0 (default): PCG runs on FP32 products and the
+                           IPM recomputes its residuals in FP64 every iteration.  k > 0: in
+                           addition, every k PCG iterations and whenever PCG converges, the
+                           PCG residual is replaced by rhs - K x computed with FP64 products
+                           and PCG restarts from x; it stops only when that FP64 residual
+                           passes the test (bounded by max_cg)                                */
 } ipm_options;
 
 typedef struct {
@@ -105,7 +111,9 @@ typedef struct {
   double lambda;        /* the lambda actually used                                  */
   double lambda_max;    /* ||M_perp^T b||_inf                                        */
   double seconds;       /* wall time of ipm_solve                                    */
-  int kkt_products;     /* products with M_perp^T M_perp (PCG plus one per IPM iter) */
+  int kkt_products;     /* products with M_perp^T M_perp (PCG, one per IPM iteration,
+                           one per FP64 residual replacement)                          */
+  int refinements;      /* FP64 residual replacements inside PCG (refine_every > 0)  */
 } ipm_result;
 
 /* Fill *opt with the defaults listed above. */

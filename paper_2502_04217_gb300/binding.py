@@ -27,14 +27,16 @@ class ipm_options(ctypes.Structure):
                 ("cg_relative", ctypes.c_int), ("max_ipm", ctypes.c_int), ("max_cg", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("sigma_slow", ctypes.c_double), ("tau", ctypes.c_double),
                 ("lambda_relative", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("tile_e", ctypes.c_int), ("tile_p", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("tile_e", ctypes.c_int), ("tile_p", ctypes.c_int),
+                ("refine_every", ctypes.c_int)]
 
 
 class ipm_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("ipm_iters", ctypes.c_int), ("cg_iters_total", ctypes.c_int),
                 ("cg_iters_max", ctypes.c_int), ("primal", ctypes.c_double), ("dual", ctypes.c_double),
                 ("rel_gap", ctypes.c_double), ("mu", ctypes.c_double), ("lambda_", ctypes.c_double),
-                ("lambda_max", ctypes.c_double), ("seconds", ctypes.c_double), ("kkt_products", ctypes.c_int)]
+                ("lambda_max", ctypes.c_double), ("seconds", ctypes.c_double), ("kkt_products", ctypes.c_int),
+                ("refinements", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -388,6 +388,7 @@ struct GSpec {
   double* dst = nullptr;         // MAPOUT_BETA
   double out_scale = 1.0;
   bool pcg = false;              // MAPIN_PCG / MAPOUT_K inside PCG (p, zv, q of the handle)
+  bool refine = false;           // only when the device asks for an FP64 residual replacement
   const double* p_in = nullptr;  // kkt_apply: p and q given by the caller
   double* q_out = nullptr;
 };
@@ -414,6 +415,7 @@ ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
       a.pcg_mode = g.pcg ? 1 : 0;
     }
     a.check_done = g.pcg ? 1 : 0;
+    a.check_refine = g.refine ? 1 : 0;
   };
   ipm_status s;
   if (L.d == 1) {
@@ -517,6 +519,7 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (o.precision != IPM_FP64 && o.precision != IPM_MIXED) return fail_arg(h, "precision must be IPM_FP64 or IPM_MIXED");
   if (!(o.gap_tol > 0) || !(o.cg_tol > 0)) return fail_arg(h, "gap_tol and cg_tol must be positive");
   if (o.max_ipm < 0 || o.max_cg < 1 || o.cg_chunk < 1) return fail_arg(h, "iteration caps must be positive");
+  if (o.refine_every < 0) return fail_arg(h, "refine_every must be >= 0");
   if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
   if (!(o.tau > 0 && o.tau < 1)) return fail_arg(h, "tau must lie in (0,1)");
   return IPM_OK;
@@ -543,6 +546,7 @@ void ipm_default_options(ipm_options* o) {
   o->autotune = 1;
   o->tile_e = 0;
   o->tile_p = 0;
+  o->refine_every = 0;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -593,7 +597,7 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   double** vec2[] = {&h->w.beta, &h->w.z, &h->w.s1, &h->w.s2, &h->w.nu1, &h->w.nu2, &h->w.c, &h->w.Gb,
                      &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->w.is1, &h->w.is2, &h->d_tmp};
   for (double** p : vec2) CKC(dalloc(h, p, v2));
-  double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q};
+  double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q, &h->w.rhs};
   for (double** p : vec4) CKC(dalloc(h, p, v4));
   CKC(dalloc(h, &h->d_U, (size_t)L.H * 2 * sizeof(double)));
   CKC(cudaMemsetAsync(h->d_U, 0, (size_t)L.H * 2 * sizeof(double), h->st));
@@ -752,8 +756,24 @@ ipm_status queue_pcg_iteration(sdft_ipm* h, LoopCtl cg_loop) {
   ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, k);
   if (s != IPM_OK) return s;
   Reduce red{h->d_partials, h->d_counter};
-  ProfScope ps(h, 3);
-  CK(k_pcg_update(h->lay, h->w, red, h->d_sc, h->opt.max_cg, cg_loop, h->st));
+  const bool refine = h->opt.precision == IPM_MIXED && h->opt.refine_every > 0;
+  {
+    ProfScope ps(h, 3);
+    CK(k_pcg_update(h->lay, h->w, red, h->d_sc, h->opt.max_cg, refine ? h->opt.refine_every : 0, cg_loop, h->st));
+  }
+  if (refine) {
+    // q = K x with FP64 products, then r = rhs - q (kernels return at once unless asked)
+    GSpec g;
+    g.mapin = MAPIN_BETA;
+    g.src = h->w.x;
+    g.mapout = MAPOUT_K;
+    g.p_in = h->w.x;
+    g.q_out = h->w.q;
+    g.refine = true;
+    if ((s = run_g(h, false, g)) != IPM_OK) return s;
+    ProfScope ps(h, 3);
+    CK(k_refine(h->lay, h->w, red, h->d_sc, cg_loop, h->st));
+  }
   return IPM_OK;
 }
 
@@ -825,8 +845,9 @@ ipm_status fill_result(sdft_ipm* h, ipm_result* res, double seconds) {
     res->mu = sc.mu;
     res->lambda = sc.lambda;
     res->lambda_max = sc.cmax;
-    res->kkt_products = sc.cg_total + sc.ipm_it + 1;
+    res->kkt_products = sc.cg_total + sc.ipm_it + 1 + sc.refinements;
     res->seconds = seconds;
+    res->refinements = sc.refinements;
   }
   if (final_status == IPM_NUMERICAL) h->err = "non-finite value or breakdown of positive definiteness";
   if (final_status == IPM_MAXITER) h->err = "IPM iteration cap reached before gap_tol";

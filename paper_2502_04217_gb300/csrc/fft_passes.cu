@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(512, 1) row_pass_kernel(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
   count_launch(a.sc);
-  if (a.check_done && a.sc->cg_done) return;
+  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP, L = a.plan.L;
   const long long row0 = (long long)blockIdx.x * P;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(512, 1) col_pass_kernel(PassArgs a) {
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   count_launch(a.sc);
-  if (a.check_done && a.sc->cg_done) return;
+  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP, L = a.plan.L;
   const int N1 = a.lay.N1;
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(512, 1) middle_pass_kernel(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
   count_launch(a.sc);
-  if (a.check_done && a.sc->cg_done) return;
+  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP;
   const int h = a.plan.L, Nl = a.lay.Nl, M = a.lay.M;

@@ -42,6 +42,9 @@ struct DevScalars {
   int cg_total;      // PCG iterations over the solve
   int cg_max;        // largest PCG count of one IPM iteration
   int cg_cap_hit;    // some PCG solve stopped at max_cg
+  int refine_now;    // mixed precision: recompute the PCG residual in FP64 after this update
+  int refine_exit;   // ... because PCG had stopped (1) or periodically (0)
+  int refinements;   // FP64 residual replacements over the solve
   unsigned long long launches;   // kernels launched by the library (every kernel adds 1)
 };
 
@@ -75,6 +78,7 @@ struct PassArgs {
   double* q;             // MAPOUT_K: K p (4H)
   int pcg_mode;          // MAPOUT_K inside PCG: form alpha = rho / p^T q
   int check_done;        // return at once when sc->cg_done
+  int check_refine;      // return at once unless sc->refine_now
   const uint32_t* maskw; // middle pass: bit-packed mask, word (xl/32)*M + x'
   double inv_n;          // 1/n, applied with the mask
   const double* yreal;   // middle pass "from real": the signal on the grid (row-major)

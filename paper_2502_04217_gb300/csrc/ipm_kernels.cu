@@ -95,6 +95,9 @@ __device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double 
   sc->cg_max = 0;
   sc->cg_cap_hit = 0;
   sc->cg_done = 1;
+  sc->refine_now = 0;
+  sc->refine_exit = 0;
+  sc->refinements = 0;
 }
 
 // Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu; control reset
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     w.pa[i] = pa; w.pb[i] = pb; w.pc[i] = pc;
     w.x[i] = 0.0; w.x[n2 + i] = 0.0;
     w.r[i] = rb; w.r[n2 + i] = rc;
+    w.rhs[i] = rb; w.rhs[n2 + i] = rc;
     w.zv[i] = zb; w.zv[n2 + i] = zz;
     w.p[i] = zb; w.p[n2 + i] = zz;
     v[0] += rb * zb + rc * zz;
@@ -231,6 +235,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     sc->cg_status = 0;
     sc->cg_stop = cg_relative ? cg_tol * sqrt(fmax(rho, 0.0)) : cg_tol;
     sc->cg_done = (sqrt(fmax(rho, 0.0)) <= sc->cg_stop) ? 1 : 0;
+    sc->refine_now = 0;
     if (!isfinite(rho)) { sc->cg_status = 2; sc->cg_done = 1; }
     set_cond(cg_loop, sc->cg_done ? 0u : 1u);
   }
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) precond_kernel(long long n2, const d
 // One PCG update after q = K p: x += alpha p, r -= alpha q, z = P^{-1} r, rho' = r^T z,
 // beta_cg = rho'/rho, stop test; the PCG loop condition is !cg_done.
 __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
-                                                              DevScalars* sc, int max_cg, LoopCtl cg_loop) {
+                                                              DevScalars* sc, int max_cg, int refine_every, LoopCtl cg_loop) {
   __shared__ double scratch[32];
   count_launch(sc);
   if (sc->cg_done) {
@@ -301,9 +306,48 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmV
     sc->beta_cg = rho_new / sc->rho;
     sc->rho = rho_new;
     sc->cg_iter += 1;
+    const bool conv = sqrt(fmax(rho_new, 0.0)) <= sc->cg_stop;
     if (!isfinite(rho_new)) { sc->cg_status = 2; sc->cg_done = 1; }
-    else if (sqrt(fmax(rho_new, 0.0)) <= sc->cg_stop) sc->cg_done = 1;
+    else if (conv) sc->cg_done = 1;
     else if (sc->cg_iter >= max_cg) { sc->cg_status = 1; sc->cg_done = 1; }
+    // mixed precision: replace the recurrence residual by the FP64 one every
+    // refine_every iterations and whenever PCG has converged on FP32 products
+    sc->refine_now = 0;
+    if (refine_every > 0 && sc->cg_status == 0 && sc->cg_iter < max_cg &&
+        (conv || sc->cg_iter % refine_every == 0)) {
+      sc->refine_now = 1;
+      sc->refine_exit = conv ? 1 : 0;
+    }
+    set_cond(cg_loop, sc->cg_done ? 0u : 1u);
+  }
+}
+
+// FP64 residual replacement (mixed precision, after q = K x in FP64):
+// r = rhs - q, z = P^{-1} r, rho = r^T z, and PCG restarts (beta_cg = 0).  After
+// a converged FP32 phase, PCG stops only if the FP64 residual passes the test.
+__global__ void __launch_bounds__(kThreads) refine_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
+                                                          DevScalars* sc, LoopCtl cg_loop) {
+  __shared__ double scratch[32];
+  count_launch(sc);
+  if (!sc->refine_now) return;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double rb = w.rhs[i] - w.q[i], rz = w.rhs[n2 + i] - w.q[n2 + i];
+    const double a = w.pa[i], b = w.pb[i], c = w.pc[i];
+    const double zb = a * rb - b * rz, zz = -b * rb + c * rz;
+    w.r[i] = rb; w.r[n2 + i] = rz;
+    w.zv[i] = zb; w.zv[n2 + i] = zz;
+    v[0] += rb * zb + rz * zz;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double rho = v[0];
+    sc->rho = rho;
+    sc->beta_cg = 0.0;
+    sc->refine_now = 0;
+    sc->refinements += 1;
+    if (!isfinite(rho)) { sc->cg_status = 2; sc->cg_done = 1; }
+    else sc->cg_done = (sqrt(fmax(rho, 0.0)) <= sc->cg_stop) ? 1 : 0;
     set_cond(cg_loop, sc->cg_done ? 0u : 1u);
   }
 }
@@ -497,9 +541,14 @@ cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* 
   precond_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w.pa, w.pb, w.pc, r, z, sc);
   return cudaGetLastError();
 }
-cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
-                         cudaStream_t st) {
-  pcg_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, max_cg, loop);
+cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, int refine_every,
+                         LoopCtl loop, cudaStream_t st) {
+  pcg_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, max_cg,
+                                                              refine_every, loop);
+  return cudaGetLastError();
+}
+cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st) {
+  refine_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, loop);
   return cudaGetLastError();
 }
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st) {

@@ -14,6 +14,7 @@ struct IpmVectors {
   double *pa, *pb, *pc;                       // P^{-1} = [pa, -pb; -pb, pc] per element
   double *is1, *is2;                          // 1/s1, 1/s2 at the current iterate (step kernels)
   double *x, *r, *zv, *p, *q;                 // PCG vectors, 2 blocks each (4H)
+  double *rhs;                                // right-hand side of the current Newton system (4H)
 };
 
 // grid size used by every elementwise kernel (also sizes the partials buffer)
@@ -53,8 +54,9 @@ cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* s
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
                          IpmVectors w, DevScalars* sc, cudaStream_t st);
 cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st);
-cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
-                         cudaStream_t st);
+cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, int refine_every,
+                         LoopCtl loop, cudaStream_t st);
+cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st);
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st);
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           cudaStream_t st);

@@ -313,3 +313,23 @@ def test_autotuned_solve_matches_default_tiles():
     (r0, v0), (r1, v1) = out
     assert abs(r0["primal"] - r1["primal"]) <= 1e-10 * abs(r0["primal"])
     assert np.abs(v0 - v1).max() <= 1e-7 * np.abs(v0).max()
+
+
+@pytest.mark.parametrize("refine_every", [1, 5])
+def test_mixed_precision_with_fp64_residual_replacement(refine_every):
+    """IPM_MIXED with FP64 residual replacement inside PCG reaches a tight gap and
+    agrees with the FP64 solve; the replacements actually ran."""
+    w = _workload((48, 32), seed=18)
+    r64, v64, _ = _solve_both(w, 0.1, 1e-9)
+    h = _handle(w, binding.IPM_MIXED, lam_rel=0.1, gap_tol=1e-9, refine_every=refine_every)
+    try:
+        r = binding.ipm_solve(h)
+        H, n = binding.ipm_sizes(h)
+        v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+        binding.ipm_get_spectrum(h, v)
+        v = v.cpu().numpy()
+    finally:
+        binding.ipm_destroy(h)
+    assert r["rel_gap"] <= 1e-9 and r["refinements"] > 0
+    assert abs(r["primal"] - r64["primal"]) <= 1e-8 * abs(r64["primal"])
+    assert np.abs(v - v64).max() <= 1e-5 * np.abs(v64).max()
