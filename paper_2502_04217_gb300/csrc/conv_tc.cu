@@ -1,0 +1,453 @@
+// 3x3x3 convolution of the warm-start network on the 5th-generation tensor
+// cores: implicit GEMM with TMA-staged input lines, tcgen05.mma from shared
+// memory into a TMEM accumulator, and a tcgen05.ld epilogue.
+//
+//   y[v, o] = bias[o] + sum_{t in 27 taps} sum_i x[v + off(t), i] w[t, o, i]
+//
+// Tiling.  One tile = 128 consecutive voxels along D2 (the MMA's M) at fixed
+// (i0, i1); N = output channels (8 is padded to 16), K = 27 taps x CIN.  For a
+// tile at (i0, i1, z0) the taps read the nine input lines (i0 + a, i1 + b),
+// a, b in {-1, 0, 1}, over z0 - 1 .. z0 + 128.  A CTA walks a segment of
+// consecutive i1 at fixed (i0, z0): each step needs one new "triple" of lines
+// (i0 - 1 .. i0 + 1, i1 + 1), which one TMA copy per 8-channel chunk brings
+// into a ring of four triple slots (zero fill outside the grid).
+//
+// Shared-memory layout of the ring (no swizzle, K-major core matrices): for
+// channel chunk c, slot s, line a, voxel row r the 16 bytes of channels
+// 8c .. 8c + 7 sit at  c*PLANE + s*TRIPLE + a*LINE + r*16.  Consecutive voxels
+// are 16 bytes apart, so the A operand of tap (a, b, dz) for the 128 rows of a
+// tile is a plain descriptor view starting at row dz of line a of the slot
+// that holds i1 + b: no data is moved per tap.  Core matrices adjacent in K
+// (the next chunk) are PLANE bytes apart (leading byte offset), 8-row groups
+// 128 bytes apart (stride byte offset).  The weights (B operand, N x K) use the
+// same scheme: [27][CIN/8][N][16 bytes].
+//
+// Roles (192 threads): warp 0 issues the TMA copies, warp 1 owns the TMEM
+// allocation and one lane issues the MMAs (27 x CIN/16 per tile, M = 128,
+// N, K = 16), warps 2..5 drain the accumulator (warp w reads TMEM lanes
+// 32 (w mod 4) ..) and write bias + ReLU (+ ReLU mask of the data gradient)
+// in BF16 and/or FP32.  Two accumulator buffers in TMEM let the MMAs of one
+// tile overlap the epilogue of the previous one.
+//
+// Every wait on an mbarrier has an iteration limit; on expiry the kernel
+// records an error code, stops issuing work, waits (again bounded) for its own
+// copies and MMAs, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+
+#include "conv_tc.h"
+
+namespace sdft {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kTileM = 128;                 // voxels per tile (MMA M)
+constexpr int kLineRows = 136;              // voxel rows per staged line (z0 - 1 .. z0 + 134)
+constexpr int kLineBytes = kLineRows * 16;  // one 8-channel chunk of one line
+constexpr int kTripleBytes = 3 * kLineBytes;
+constexpr int kSlots = 4;
+constexpr int kPlaneBytes = kSlots * kTripleBytes;
+constexpr int kSegment = 32;                // i1 steps per work item
+constexpr int kThreads = 192;
+constexpr unsigned kWaitLimit = 1u << 24;   // polls of one mbarrier wait (with back-off: seconds)
+
+__device__ unsigned g_conv_tc_error;        // 0, or the code of the first wait that expired
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete; false after the limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (unsigned i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (i >= 32) __nanosleep(128);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 4D tiled TMA load (coordinates: channel, z, i1, i0; out-of-range -> zeros)
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
+// 8 rows x 16 bytes; lbo = byte distance of K-adjacent core matrices,
+// sbo = byte distance of 8-row groups; descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator (bits 4-5),
+// BF16 A and B (bits 7-9, 10-12), both K-major, N >> 3 (bits 17-22), M >> 4
+// (bits 24-28).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Arrive on `bar` once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+// Work item -> (i0, z-tile, first i1, steps)
+struct Item {
+  int i0, z0, y0, steps;
+};
+__device__ __forceinline__ Item item_of(long long it, const ConvTcArgs& a, int ztiles, int nseg) {
+  Item r;
+  const int seg = (int)(it % nseg);
+  const long long col = it / nseg;
+  r.z0 = (int)(col % ztiles) * kTileM;
+  r.i0 = (int)(col / ztiles);
+  r.y0 = seg * kSegment;
+  r.steps = min(kSegment, a.D1 - r.y0);
+  return r;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, ConvTcArgs a) {
+  constexpr int N = COUT < 16 ? 16 : COUT;     // MMA N (multiple of 16 for M = 128)
+  constexpr int KC = CIN / 8;                  // 8-channel chunks
+  constexpr int HALO = KC * kPlaneBytes;
+  constexpr int WBYTES = 27 * KC * N * 16;
+  constexpr uint32_t kTmemCols = 2 * N < 32 ? 32 : 2 * N;
+  constexpr uint32_t kIdesc = idesc_bf16(kTileM, N);
+  constexpr uint32_t kTxBytes = KC * kTripleBytes;
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* halo = smem;
+  unsigned char* wsm = smem + HALO;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + HALO + WBYTES);
+  // bars: full[4], empty[4], accf[2], acce[2], done; then the TMEM address and the abort flag
+  uint32_t& s_tmem = *reinterpret_cast<uint32_t*>(bars + 13);
+  volatile int& s_abort = *reinterpret_cast<volatile int*>(bars + 14);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // TMA destinations must be 128-byte aligned: refuse to run otherwise
+  if (smem_u32(smem) & 127u) {
+    if (threadIdx.x == 0) atomicCAS(&g_conv_tc_error, 0u, 6u);
+    return;
+  }
+  const int ztiles = (a.D2 + kTileM - 1) / kTileM;
+  const int nseg = (a.D1 + kSegment - 1) / kSegment;
+  const long long nitems = (long long)a.D0 * ztiles * nseg;
+
+  // weights -> [27][KC][N][16 B], zero rows for o >= COUT
+  for (int idx = threadIdx.x; idx < 27 * KC * N; idx += blockDim.x) {
+    const int o = idx % N, tc = idx / N, c = tc % KC, t = tc / KC;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (o < COUT) v = *reinterpret_cast<const uint4*>(a.w + ((size_t)(t * COUT + o) * CIN + c * 8));
+    *reinterpret_cast<uint4*>(wsm + (size_t)idx * 16) = v;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) { mbar_init(smem_u32(&bars[i]), 1); mbar_init(smem_u32(&bars[4 + i]), 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&bars[8 + i]), 1); mbar_init(smem_u32(&bars[10 + i]), 128); }
+    mbar_init(smem_u32(&bars[12]), 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights: generic writes -> MMA reads
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  auto fail = [&](unsigned code) {
+    s_abort = 1;
+    atomicCAS(&g_conv_tc_error, 0u, code);
+  };
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      unsigned long long q = 0;   // triple sequence number
+      for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
+        const Item m = item_of(it, a, ztiles, nseg);
+        for (int j = 0; j < m.steps + 2 && !s_abort; ++j, ++q) {
+          const int slot = (int)(q & 3);
+          const uint32_t use = (uint32_t)(q >> 2);
+          if (use > 0 && !mbar_wait(smem_u32(&bars[4 + slot]), (use - 1) & 1)) { fail(1); break; }
+          const uint32_t full = smem_u32(&bars[slot]);
+          mbar_expect_tx(full, kTxBytes);
+          for (int c = 0; c < KC; ++c)
+            tma_load_4d(smem_u32(halo + c * kPlaneBytes + slot * kTripleBytes), &xmap, c * 8, m.z0 - 1,
+                        m.y0 - 1 + j, m.i0 - 1, full);
+        }
+      }
+      // own copies in flight: the last (up to) four triples must have landed
+      for (unsigned long long k = (q > 4 ? q - 4 : 0); k < q; ++k)
+        if (!mbar_wait(smem_u32(&bars[k & 3]), (uint32_t)((k >> 2) & 1))) { fail(2); break; }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      unsigned long long q = 0;   // first triple of the current item
+      unsigned long long tile = 0;
+      for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
+        const Item m = item_of(it, a, ztiles, nseg);
+        for (int s = 0; s < m.steps && !s_abort; ++s, ++tile) {
+          bool ok = true;
+          for (int b = 0; b < 3 && ok; ++b) {
+            const unsigned long long k = q + s + b;
+            ok = mbar_wait(smem_u32(&bars[k & 3]), (uint32_t)((k >> 2) & 1));
+          }
+          const int buf = (int)(tile & 1);
+          const uint32_t use = (uint32_t)(tile >> 1);
+          if (ok && use > 0) ok = mbar_wait(smem_u32(&bars[10 + buf]), (use - 1) & 1);
+          if (!ok) { fail(3); break; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * N);
+          const uint32_t hb = smem_u32(halo), wb = smem_u32(wsm);
+          int t = 0;
+#pragma unroll 1
+          for (int ta = 0; ta < 3; ++ta) {          // offset along i0 (line within the triple)
+#pragma unroll 1
+            for (int tb = 0; tb < 3; ++tb) {        // offset along i1 (which triple)
+              const int slot = (int)((q + s + tb) & 3);
+#pragma unroll
+              for (int tz = 0; tz < 3; ++tz, ++t) { // offset along D2 (row shift)
+                const uint32_t abase = hb + slot * kTripleBytes + ta * kLineBytes + tz * 16;
+#pragma unroll
+                for (int kc = 0; kc < CIN / 16; ++kc) {
+                  const uint64_t ad = smem_desc(abase + kc * 2 * kPlaneBytes, kPlaneBytes, 128);
+                  const uint64_t bd = smem_desc(wb + (uint32_t)((t * KC + kc * 2) * N * 16), N * 16, 128);
+                  mma_bf16(d, ad, bd, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
+                }
+              }
+            }
+          }
+          mma_commit(smem_u32(&bars[8 + buf]));           // accumulator ready
+          mma_commit(smem_u32(&bars[4 + ((q + s) & 3)]));  // triple i1 - 1 no longer needed
+          if (s == m.steps - 1) {
+            mma_commit(smem_u32(&bars[4 + ((q + s + 1) & 3)]));
+            mma_commit(smem_u32(&bars[4 + ((q + s + 2) & 3)]));
+          }
+        }
+        q += m.steps + 2;
+      }
+      // every MMA issued by this thread has completed before TMEM is freed
+      mma_commit(smem_u32(&bars[12]));
+      if (!mbar_wait(smem_u32(&bars[12]), 0)) fail(4);
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    float bias[N];
+#pragma unroll
+    for (int o = 0; o < N; ++o) bias[o] = (a.bias && o < COUT) ? a.bias[o] : 0.f;
+    unsigned long long tile = 0;
+    for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
+      const Item m = item_of(it, a, ztiles, nseg);
+      for (int s = 0; s < m.steps; ++s, ++tile) {
+        const int buf = (int)(tile & 1);
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[8 + buf]), (uint32_t)((tile >> 1) & 1)));
+        if (!ok) { fail(5); break; }
+        tc_fence_after();
+        float v[N];
+        tmem_load<N>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * N), v);
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bars[10 + buf]));
+        const int z = m.z0 + row;
+        if (z < a.D2) {
+          const size_t vox = ((size_t)m.i0 * a.D1 + (m.y0 + s)) * a.D2 + z;
+#pragma unroll
+          for (int o = 0; o < COUT; ++o) {
+            float y = v[o] + bias[o];
+            if (a.relu) y = fmaxf(y, 0.f);
+            v[o] = y;
+          }
+          if (a.aux) {
+            const uint4* ax = reinterpret_cast<const uint4*>(a.aux + vox * COUT);
+#pragma unroll
+            for (int c = 0; c < COUT / 8; ++c) {
+              const uint4 u = ax[c];
+              const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[k] & 0xFFFFu))) > 0.f)) v[c * 8 + 2 * k] = 0.f;
+                if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[k] >> 16))) > 0.f)) v[c * 8 + 2 * k + 1] = 0.f;
+              }
+            }
+          }
+          if (a.ybf) {
+            uint4* yo = reinterpret_cast<uint4*>(a.ybf + vox * COUT);
+#pragma unroll
+            for (int c = 0; c < COUT / 8; ++c)
+              yo[c] = make_uint4(pack_bf16(v[c * 8], v[c * 8 + 1]), pack_bf16(v[c * 8 + 2], v[c * 8 + 3]),
+                                 pack_bf16(v[c * 8 + 4], v[c * 8 + 5]), pack_bf16(v[c * 8 + 6], v[c * 8 + 7]));
+          }
+          if (a.yf) {
+            float4* yo = reinterpret_cast<float4*>(a.yf + vox * COUT);
+#pragma unroll
+            for (int c = 0; c < COUT / 4; ++c) yo[c] = make_float4(v[c * 4], v[c * 4 + 1], v[c * 4 + 2], v[c * 4 + 3]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+template <int CIN, int COUT>
+cudaError_t launch(const ConvTcArgs& a, cudaStream_t st) {
+  constexpr int N = COUT < 16 ? 16 : COUT;
+  constexpr size_t smem = (size_t)(CIN / 8) * kPlaneBytes + (size_t)27 * (CIN / 8) * N * 16 + 16 * sizeof(uint64_t);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // the activation tensor [D0][D1][D2][CIN] as a 4D map (innermost first)
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)a.D2, (cuuint64_t)a.D1, (cuuint64_t)a.D0};
+  const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)a.D2 * CIN * 2, (cuuint64_t)a.D1 * a.D2 * CIN * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kLineRows, 1, 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.x), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const long long ztiles = (a.D2 + kTileM - 1) / kTileM, nseg = (a.D1 + kSegment - 1) / kSegment;
+  const long long nitems = (long long)a.D0 * ztiles * nseg;
+  const int grid = (int)(nitems < sms ? nitems : sms);
+  conv_tc_kernel<CIN, COUT><<<grid, kThreads, smem, st>>>(map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool conv_tc_supported(int cin, int cout, int D0, int D1, int D2) {
+  return (cin == 16 || cin == 32) && (cout == 8 || cout == 32) && D2 >= 64 && D0 >= 1 && D1 >= 1;
+}
+
+cudaError_t conv_tc(int cin, int cout, const ConvTcArgs& a, cudaStream_t st) {
+  if (!conv_tc_supported(cin, cout, a.D0, a.D1, a.D2)) return cudaErrorNotSupported;
+  if (cin == 32 && cout == 32) return launch<32, 32>(a, st);
+  if (cin == 16 && cout == 32) return launch<16, 32>(a, st);
+  if (cin == 32 && cout == 8) return launch<32, 8>(a, st);
+  return launch<16, 8>(a, st);
+}
+
+cudaError_t conv_tc_take_error(unsigned* code, cudaStream_t st) {
+  unsigned zero = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyFromSymbol(code, g_conv_tc_error, sizeof(unsigned));
+  if (e == cudaSuccess && *code) e = cudaMemcpyToSymbol(g_conv_tc_error, &zero, sizeof(unsigned));
+  return e;
+}
+
+}  // namespace sdft

@@ -12,8 +12,10 @@
 // (D0, D1, D2) = (Hl, N0, N1) in 3D, (Hl, 1, N0) in 2D, (Hl, 1, 1) in 1D, so the
 // voxel index equals the slot index of the beta layout.
 //
-// Tensor cores: implicit-GEMM convolution with mma.sync m16n8k16 (BF16 in, FP32
-// accumulate).  Forward: M = 64 voxels along D2 per block (16 per warp),
+// Tensor cores: on grids with at least 64 voxels along D2 the convolutions run
+// on tcgen05 (conv_tc.cu: TMA-staged lines, MMA into TMEM).  The kernels below
+// use mma.sync m16n8k16 (BF16 in, FP32 accumulate) and serve the small grids
+// and the weight gradient.  Forward: M = 64 voxels along D2 per block (16 per warp),
 // N = output channels, K = 27 taps x input channels, input halo tile and all
 // weights staged in shared memory.  The data gradient is the same kernel on the
 // mirrored, channel-transposed weights with the ReLU mask of the layer input
@@ -26,6 +28,7 @@
 #include <vector>
 
 #include "../../include/sdft_ipm.h"
+#include "conv_tc.h"
 #include "internal.h"
 #include "kernels.h"
 
@@ -423,7 +426,14 @@ cudaError_t conv_fwd(const ConvArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The tcgen05 kernel (conv_tc.cu) takes every layer shape once D2 >= 64; the
+// mma.sync kernel above covers the small grids.
 cudaError_t conv_fwd_any(int cin, int cout, const ConvArgs& a, cudaStream_t st) {
+  if (conv_tc_supported(cin, cout, a.D0, a.D1, a.D2)) {
+    const ConvTcArgs t{a.x, a.w, a.bias, a.D0, a.D1, a.D2, a.relu, a.aux, a.ybf, a.yf};
+    const cudaError_t e = conv_tc(cin, cout, t, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (cin == 16 && cout == 32) return conv_fwd<16, 32>(a, st);
   if (cin == 32 && cout == 32) return conv_fwd<32, 32>(a, st);
   if (cin == 32 && cout == 8) return conv_fwd<32, 8>(a, st);
@@ -536,6 +546,16 @@ ipm_status repack(sdft_ws* n) {
 }
 
 // Forward pass on the handle's c: features -> 4 convolutions -> y (FP32 [V][8]).
+// Synchronise st, then report an expired pipeline wait of the tensor-core convolution.
+ipm_status sync_check(cudaStream_t st) {
+  unsigned code = 0;
+  CKW(conv_tc_take_error(&code, st));
+  if (code)
+    return ws_err("tensor-core convolution: a pipeline wait expired (code " + std::to_string(code) + ")",
+                  IPM_ERR_CUDA);
+  return IPM_OK;
+}
+
 ipm_status forward(sdft_ws* n, const HandleView& hv) {
   int D0, D1, D2;
   grid_dims(hv.lay, D0, D1, D2);
@@ -664,8 +684,7 @@ ipm_status ws_forward(sdft_ws* n, sdft_ipm* h, float* y) {
   ipm_status s = forward(n, hv);
   if (s != IPM_OK) return s;
   if (y) CKW(cudaMemcpyAsync(y, n->y, (size_t)hv.lay.H * 8 * sizeof(float), cudaMemcpyDefault, n->st));
-  CKW(cudaStreamSynchronize(n->st));
-  return IPM_OK;
+  return sync_check(n->st);
 }
 
 ipm_status ws_predict(sdft_ws* n, sdft_ipm* h, double mu_scale) {
@@ -676,7 +695,7 @@ ipm_status ws_predict(sdft_ws* n, sdft_ipm* h, double mu_scale) {
   if (s != IPM_OK) return s;
   point_kernel<<<blocks_for(2 * hv.lay.H, 256), 256, 0, n->st>>>(hv.lay, n->y, hv.w.c, hv.sc, mu_scale, hv.w);
   CKW(cudaGetLastError());
-  CKW(cudaStreamSynchronize(n->st));
+  if ((s = sync_check(n->st)) != IPM_OK) return s;
   handle_point_set(h);
   return IPM_OK;
 }
@@ -715,8 +734,7 @@ ipm_status ws_train_step(sdft_ws* n, sdft_ipm* h, const double* beta_star, float
     if ((s = repack(n)) != IPM_OK) return s;
   }
   if (loss) CKW(cudaMemcpyAsync(loss, n->dsc, sizeof(double), cudaMemcpyDeviceToHost, n->st));
-  CKW(cudaStreamSynchronize(n->st));
-  return IPM_OK;
+  return sync_check(n->st);
 }
 
 // Low-level kernels on caller buffers (checked against the CPU reference by the tests).
@@ -729,7 +747,7 @@ ipm_status ws_conv_forward(int cin, int cout, int d0, int d1, int d2, const uint
   cudaError_t e = conv_fwd_any(cin, cout, a, (cudaStream_t)stream);
   if (e == cudaErrorInvalidValue) return ws_err("ws_conv_forward: channels must be (16|32, 8|32)", IPM_ERR_ARG);
   if (e != cudaSuccess) return ws_err(cudaGetErrorString(e), IPM_ERR_CUDA);
-  return IPM_OK;
+  return sync_check((cudaStream_t)stream);
 }
 
 ipm_status ws_conv_wgrad(int cin, int m, int mout, int d0, int d1, int d2, const uint16_t* x, const uint16_t* dy,

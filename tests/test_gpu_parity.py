@@ -209,6 +209,21 @@ def test_mixed_precision_solve_reaches_gap():
     assert np.abs(v32 - v64).max() <= 1e-4 * np.abs(v64).max()
 
 
+@pytest.mark.parametrize("dims", [(512,), (64, 48), (32, 24, 16)])
+def test_mixed_cg_matches_fp64_pcg(dims):
+    """Mixed precision runs the same PCG with FP32 FFT products and FP64 Krylov
+    vectors and barrier terms; the IPM takes the same path as the FP64 solve:
+    same IPM iterations (+-1), Krylov counts within 10 %, and the same solution."""
+    w = _workload(dims, seed=21)
+    r64, v64, _ = _solve_both(w, 0.1, 1e-8)
+    r32, v32, _ = _solve_both(w, 0.1, 1e-8, precision=binding.IPM_MIXED)
+    assert r32["status"] == binding.IPM_OK and r32["rel_gap"] <= 1e-8
+    assert abs(r32["ipm_iters"] - r64["ipm_iters"]) <= 1
+    assert abs(r32["cg_iters_total"] - r64["cg_iters_total"]) <= 0.1 * r64["cg_iters_total"] + 2
+    assert abs(r32["primal"] - r64["primal"]) <= 1e-7 * abs(r64["primal"])
+    assert np.abs(v32 - v64).max() <= 1e-4 * np.abs(v64).max()
+
+
 def test_empty_mask_rejected():
     w = _workload((8, 8), seed=11)
     w.mask[:] = 0

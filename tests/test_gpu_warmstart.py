@@ -36,8 +36,13 @@ def as_u16(t):
     return t.view(torch.int16)
 
 
+# D2 >= 64 runs the tcgen05 kernel (128-voxel tiles along D2, segments of 32
+# steps along D1: ragged tiles, several segments, zero padding on every face);
+# smaller D2 the mma.sync kernel.
 @pytest.mark.parametrize("cin,cout,dims", [(32, 32, (3, 5, 70)), (16, 32, (2, 3, 13)), (32, 8, (4, 2, 64)),
-                                           (16, 8, (1, 1, 5)), (32, 32, (2, 2, 129))])
+                                           (16, 8, (1, 1, 5)), (32, 32, (2, 2, 129)), (32, 32, (3, 40, 256)),
+                                           (16, 32, (2, 33, 128)), (32, 8, (3, 4, 200)), (16, 8, (2, 2, 64)),
+                                           (32, 32, (1, 1, 384))])
 def test_conv_forward_matches_reference(cin, cout, dims):
     rng = np.random.default_rng(1)
     x = bf16(rng.standard_normal(dims + (cin,)))
