@@ -41,6 +41,12 @@ WORKLOADS = {
     "warm512": ("512^3, 100000 frequencies, background 1e-3 and noise 0.01, radius-2 balls on a period-8 lattice, "
                 "lambda = 0.05 lambda_max, gap 1e-6: learned warm start (network inference included) + mixed "
                 "precision solve, against the cold-start FP64 solve of the same instance", "mixed"),
+    "infer256": ("warm-start network inference (features + four 3x3x3 convolutions 8->32->32->32->4, BF16 "
+                 "tensor cores) on the slot grid 129 x 256 x 256 of the 256^3 workload", "bf16"),
+    "kkt256": ("products with the condensed KKT matrix K (FP32 FFT passes of G, FP64 p, q and diagonal) on the 256^3 "
+               "workload, mixed precision, back to back through kkt_apply", "mixed"),
+    "conv256": ("one 32->32 3x3x3 convolution layer (bias, ReLU, BF16 in, FP32 out) of the warm-start network on "
+                "the 129 x 256 x 256 slot grid of the 256^3 workload, tcgen05 tensor cores", "bf16"),
     "batch": ("batch of 48 independent 3D problems, sides drawn from {32,48,64,96,128}, 0.25% frequencies, "
               "Bragg-ball masks (period 8-16, radius 1-2, random offsets), noise 0.01, lambda = 0.05 lambda_max, "
               "gap 1e-6, mixed precision, all solved by one graph launch", "mixed"),
@@ -55,10 +61,12 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kkt", action="store_true")
-    ap.add_argument("--workload", choices=["1d", "2d", "3d", "batch", "warm512"], default="2d",
+    ap.add_argument("--workload", choices=["1d", "2d", "3d", "batch", "warm512", "infer256", "conv256", "kkt256"], default="2d",
                     help="2d: 512^2 FP64 (default); 1d: n=256 FP64; 3d: 256^3 mixed precision; "
                          "batch: 48 uneven 3D problems in one graph launch, mixed precision; "
-                         "warm512: 512^3, learned warm start + mixed precision against the cold FP64 solve")
+                         "warm512: 512^3, learned warm start + mixed precision against the cold FP64 solve; "
+                         "infer256: the warm-start network alone on the 256^3 slot grid (tensor-core roofline); "
+                         "conv256: one of its 32->32 convolution layers; kkt256: KKT products at 256^3 (mixed)")
     return ap.parse_args()
 
 
@@ -156,9 +164,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2502_04217_gb300.synth import make_problem
-    if args.workload in ("3d", "batch"):
-        print(json.dumps({"impl": "reference", "unavailable": "a full direct-DFT oracle solve of this workload takes "
-                          "hours on the host cores; its CPU baseline is reported (extrapolated) in the GPU line"}))
+    if args.workload in ("3d", "batch", "warm512", "infer256", "conv256", "kkt256"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle on this workload takes hours on the host "
+                          "cores; its CPU baseline is reported (extrapolated from a bounded sample) in the GPU line"}))
         return 0
     w = make_problem(args.workload)
     for _ in range(args.warmup):
@@ -410,10 +418,10 @@ def _traffic(kernel, workload):
         return None
 
 
-def _kkt_throughput(binding, torch, np):
-    """Back-to-back products with K on the 256^3 workload in mixed precision."""
+def _kkt_throughput(binding, torch, np, reps=20, w=None):
+    """Back-to-back products with K on the 256^3 workload in mixed precision (inside the NVTX range "kkt")."""
     from paper_2502_04217_gb300.synth import make_problem
-    w = make_problem("3d")
+    w = w if w is not None else make_problem("3d")
     opt = binding.default_options(precision=binding.IPM_MIXED, lambda_relative=1)
     stream = torch.cuda.current_stream()
     h = binding.ipm_create(w.dims, w.mask, w.y, w.lam_rel, opt, stream=stream.cuda_stream)
@@ -427,22 +435,23 @@ def _kkt_throughput(binding, torch, np):
         q = torch.empty_like(p)
         for _ in range(3):
             binding.kkt_apply(h, p, q)
-        reps = 20
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("kkt")
         e0.record(stream)
         for _ in range(reps):
             binding.kkt_apply(h, p, q)
         e1.record(stream)
         e1.synchronize()
+        torch.cuda.nvtx.range_pop()
         t = e0.elapsed_time(e1) / 1e3 / reps
         # compulsory bytes of one product: p, q (FP64, 2 blocks), Lambda1, Lambda2 (FP64), mask bits
         algo = (4 * H * 8) * 2 + (2 * H * 8) * 2 + n / 8
         peak = _peaks().get("hbm_gbs", 6800.0)
         return {"workload": "3d 256^3 mixed (FP32 FFT, FP64 diagonal)", "matvecs_per_s": 1.0 / t,
                 "ms_per_matvec": t * 1e3, "algorithmic_bytes": algo, "algorithmic_gbs": algo / t / 1e9,
-                "hbm_peak_gbs": peak, "frac_of_hbm": algo / t / 1e9 / peak}
+                "hbm_peak_gbs": peak, "frac_of_hbm": algo / t / 1e9 / peak, "tiles": binding.ipm_describe(h)}
     finally:
         binding.ipm_destroy(h)
 
@@ -584,7 +593,7 @@ def run_batch(args):
 
 
 def run_warm512(args):
-    """Config 5: warm-started mixed solve (inference included) vs cold FP64 solve, 512^3."""
+    """Warm-started mixed solve (network inference included) vs cold FP64 solve, 512^3."""
     import numpy as np
     import torch
 
@@ -615,12 +624,13 @@ def run_warm512(args):
         return e0.elapsed_time(e1) / 1e3, out
 
     def warm():
-        binding.ws_predict(net, h32, 0.1)
+        binding.ws_predict(net, h32, wsm.MU_SCALE)
         return binding.ipm_solve(h32)
 
     for _ in range(args.warmup):
         warm()
     binding.ipm_solve(h64)
+    binding.ipm_profile_enable(h32, False)        # resets the device launch counter
     clocks = ClockSampler(local)
     clocks.start()
     torch.cuda.synchronize()
@@ -628,28 +638,310 @@ def run_warm512(args):
     for _ in range(args.steps):
         t, rw = timed(warm)
         wt.append(t)
+    launches, _ = binding.ipm_profile_get(h32, 5)
+    launches += 6 * args.steps                     # features, 4 convolutions, start point per step
+    t_inf = timed(lambda: binding.ws_forward(net, h32, None))[0]
     t64, r64 = timed(lambda: binding.ipm_solve(h64))
     tcold32, rc32 = timed(lambda: binding.ipm_solve(h32))
     clk = clocks.stop()
     value = sum(wt) / len(wt)
-    print(json.dumps({
-        "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws_n, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16+f32+f64", "data": "synthetic",
-        "config": {"workload": _workload_desc("warm512"), "dims": list(w.dims), "gap_tol": GAP_TOL,
-                   "network": "4-layer 3x3x3 conv, 32 channels, BF16, trained on 128^3 instances (weights file)",
-                   "l2": "inputs far larger than L2 (512^3)"},
-        "warm_vs_cold_fp64": value / t64, "cold_fp64_s": t64, "cold_mixed_s": tcold32,
-        "solve": {"warm_ipm_iters": rw["ipm_iters"], "cold_fp64_ipm_iters": r64["ipm_iters"],
-                  "cold_mixed_ipm_iters": rc32["ipm_iters"], "warm_rel_gap": rw["rel_gap"],
-                  "cold_fp64_rel_gap": r64["rel_gap"],
-                  "objective_rel_diff": abs(rw["primal"] - r64["primal"]) / abs(r64["primal"]),
-                  "step_s": [round(x, 4) for x in wt]},
-        "clocks": clk, "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
-    }))
+
+    # kernel classes of one warm solve (per-launch events), dominant FFT pass class -> HBM roofline
+    binding.ipm_profile_enable(h32, True)
+    binding.ws_predict(net, h32, wsm.MU_SCALE)
+    rp = binding.ipm_solve(h32)
+    cls_names = ["fft_row", "fft_col", "fft_middle", "pcg_update", "ipm_other"]
+    breakdown = {}
+    for k, nm in enumerate(cls_names):
+        nl, ms = binding.ipm_profile_get(h32, k)
+        breakdown[nm] = {"launches": nl, "ms": ms}
+    binding.ipm_profile_enable(h32, False)
+    fft = {k: v for k, v in breakdown.items() if k.startswith("fft") and v["launches"]}
+    dom = max(fft, key=lambda k: fft[k]["ms"])
+    _, flops, nbytes = _pass_model(w.dims, "mixed", rp["ipm_iters"], rp["cg_iters_total"])[dom]
+    dom_s = breakdown[dom]["ms"] / 1e3
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    roofline = {"bound": "hbm", "achieved": nbytes / dom_s / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": nbytes / dom_s / 1e9 / peak, "traffic": _traffic(dom, "warm512"), "kernel": dom,
+                "per_launch_us": 1e6 * dom_s / breakdown[dom]["launches"], "algorithmic_bytes": nbytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "breakdown_ms": {k: round(v["ms"], 3) for k, v in breakdown.items()},
+                "breakdown_launches": {k: v["launches"] for k, v in breakdown.items()}}
+
+    # end to end: problem from pinned host buffers, spectrum back to the host
+    mask_h = mask_d.cpu().pin_memory()
+    y_h = y_d.cpu().pin_memory()
+    H, n = binding.ipm_sizes(h32)
+    spec_h = torch.empty(2 * H, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for i in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binding.ipm_set_problem(h32, mask_h, y_h, w.lam_rel)
+        warm()
+        binding.ipm_get_spectrum(h32, spec_h)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_t.append(t1 - t0)
+    e2e = {"value": sum(e2e_t) / len(e2e_t), "unit": "s", "h2d_bytes_per_step": int(mask_h.numel() + y_h.numel() * 8),
+           "d2h_bytes_per_step": int(spec_h.numel() * 8)}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        ws_ = make_problem("custom", dims=(128, 128, 128), missing=0.06, seed=3)
+        t_g = _oracle_g_seconds(ws_)
+        scale = (512 / 128) ** 4            # direct DFT along each axis: n * (N0 + N1 + N2)
+        cpu = {"value": t_g * scale * rw["kkt_products"], "unit": "s", "cores": _cores(), "kind": "oracle",
+               "extrapolated": True,
+               "sample": f"one oracle product with M_perp^T M_perp at 128^3 ({t_g:.2f} s, direct DFT), scaled by "
+                         f"n (N0 + N1 + N2) to 512^3 and by the {rw['kkt_products']} products of the warm solve"}
     binding.ipm_destroy(h64)
     binding.ipm_destroy(h32)
     binding.ws_destroy(net)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws_n, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * value, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
+            "config": {"workload": _workload_desc("warm512"), "dims": list(w.dims), "gap_tol": GAP_TOL,
+                       "network": "4-layer 3x3x3 conv, 32 channels, BF16, trained on 128^3 instances (weights file)",
+                       "mu_scale": wsm.MU_SCALE, "l2": "inputs far larger than L2 (512^3)"},
+            "warm_vs_cold_fp64": value / t64, "cold_fp64_s": t64, "cold_mixed_s": tcold32, "inference_s": t_inf,
+            "solve": {"warm_ipm_iters": rw["ipm_iters"], "cold_fp64_ipm_iters": r64["ipm_iters"],
+                      "cold_mixed_ipm_iters": rc32["ipm_iters"], "warm_rel_gap": rw["rel_gap"],
+                      "cold_fp64_rel_gap": r64["rel_gap"],
+                      "objective_rel_diff": abs(rw["primal"] - r64["primal"]) / abs(r64["primal"]),
+                      "step_s": [round(x, 4) for x in wt]},
+            "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        }))
+    return 0
+
+
+def _oracle_layers(binding, net):
+    """The network's parameters in the oracle's layout: [(W (3,3,3,cin,cout), b)] over real channels."""
+    import numpy as np
+    from paper_2502_04217_gb300 import warmstart as wsm
+    p = np.empty(binding.ws_num_params(net), dtype=np.float32)
+    binding.ws_get_params(net, p)
+    out, o = [], 0
+    for cin, cout, cir, cor in wsm.LAYERS:
+        W = p[o:o + 27 * cout * cin].reshape(3, 3, 3, cout, cin).transpose(0, 1, 2, 4, 3)
+        o += 27 * cout * cin
+        b = p[o:o + cout]
+        o += cout
+        out.append((W[:, :, :, :cir, :cor].astype(np.float64).copy(), b[:cor].astype(np.float64)))
+    return out
+
+
+def run_kkt256(args):
+    """Products with K at 256^3 in mixed precision: time per product, HBM roofline over its compulsory bytes."""
+    import numpy as np
+    import torch
+
+    from paper_2502_04217_gb300 import binding
+    from paper_2502_04217_gb300.synth import make_problem
+
+    ws_n, rank, local = _dist()
+    torch.cuda.set_device(local)
+    binding.load()
+    w = make_problem("3d", index=rank)
+    clocks = ClockSampler(local)
+    clocks.start()
+    k = _kkt_throughput(binding, torch, np, reps=max(args.steps, 5), w=w)
+    clk = clocks.stop()
+    value = k["ms_per_matvec"] / 1e3
+    peak = k["hbm_peak_gbs"]
+    roofline = {"bound": "hbm", "achieved": k["algorithmic_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": k["frac_of_hbm"], "traffic": _traffic("kkt_apply (5 passes)", "kkt256"),
+                "kernel": "kkt_apply: row(inv) -> col(inv) -> middle -> col(fwd) -> row(fwd, K diagonal)",
+                "algorithmic_bytes": k["algorithmic_bytes"],
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        t_g = _oracle_g_seconds(w)
+        cpu = {"value": t_g, "unit": "s", "cores": _cores(), "kind": "oracle",
+               "sample": "one oracle product with M_perp^T M_perp at 256^3 (direct DFT), the dominant part of a "
+                         "product with K"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "KKT matvec time (256^3, mixed precision)", "value": value, "unit": "s", "n_gpus": ws_n,
+            "steps": max(args.steps, 5), "warmup": 3, "ms_per_step": 1e3 * value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": _workload_desc("kkt256"), "dims": list(w.dims),
+                       "l2": "p, q, Lambda (1.35 GB per product) far larger than L2"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "gpu_launches": 5 * max(args.steps, 5),
+            "clocks": clk, "kkt_matvec": k,
+            "e2e_note": "kkt_apply works on device vectors; the solve lines carry the host path",
+        }))
+    return 0
+
+
+def _conv_layer_roofline(binding, torch, D, reps, timed):
+    """Per-launch time of one 32 -> 32 tcgen05 convolution on grid D and its tensor roofline."""
+    V = D[0] * D[1] * D[2]
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(V * 32, device="cuda", generator=g).to(torch.bfloat16)
+    wt = (0.05 * torch.randn(27 * 32 * 32, device="cuda", generator=g)).to(torch.bfloat16)
+    bias = torch.zeros(32, device="cuda")
+    yb = torch.empty(V * 32, device="cuda")
+    layer = lambda: binding.ws_conv_forward(32, 32, D, x.view(torch.int16), wt.view(torch.int16), bias, 1, None, yb)
+    for _ in range(3):
+        timed(layer)
+    lt = [timed(layer) for _ in range(reps)]
+    t_layer = sum(lt) / len(lt)
+    flops = 2.0 * V * 27 * 32 * 32
+    peak = _peaks().get("bf16_tflops", 1900.0)
+    achieved = flops / t_layer / 1e12
+    del x, yb
+    return ({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+             "traffic": _traffic("conv_tc_kernel<32,32>", "conv256"),
+             "kernel": "conv_tc_kernel<32,32>: one 32->32 layer, tcgen05.mma M=128 N=32 K=16, FP32 output",
+             "per_launch_us": 1e6 * t_layer, "algorithmic_flops": flops,
+             "algorithmic_bytes": V * 32 * 2 + V * 32 * 4 + 27 * 32 * 32 * 2,
+             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; of measured)"}, lt)
+
+
+def run_conv256(args):
+    """One 32 -> 32 convolution layer on the 129 x 256 x 256 grid (tcgen05 kernel alone)."""
+    import torch
+
+    from paper_2502_04217_gb300 import binding
+
+    ws_n, rank, local = _dist()
+    torch.cuda.set_device(local)
+    binding.load()
+    stream = torch.cuda.current_stream()
+    D = (129, 256, 256)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    roofline, lt = _conv_layer_roofline(binding, torch, D, args.steps, timed)
+    clk = clocks.stop()
+    value = sum(lt) / len(lt)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        import numpy as np
+        from oracle import warmstart as ows
+        rng = np.random.default_rng(0)
+        sub = (8, 32, 32)
+        xs, Ws = rng.standard_normal(sub + (32,)), 0.05 * rng.standard_normal((3, 3, 3, 32, 32))
+        t0 = time.perf_counter()
+        ows.conv3d(xs, Ws, np.zeros(32))
+        t_s = time.perf_counter() - t0
+        vs, V = sub[0] * sub[1] * sub[2], D[0] * D[1] * D[2]
+        cpu = {"value": t_s * V / vs, "unit": "s", "cores": _cores(), "kind": "oracle", "extrapolated": True,
+               "sample": f"oracle conv3d (numpy FP64) on an 8x32x32 block ({t_s:.3f} s), scaled by voxel count"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": "3x3x3 convolution layer time (32->32 channels)", "value": value, "unit": "s", "n_gpus": ws_n,
+            "steps": args.steps, "warmup": 3, "ms_per_step": 1e3 * value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": _workload_desc("conv256"), "grid": list(D),
+                       "l2": "input 541 MB and output 1.08 GB, both larger than L2"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps + 3, "clocks": clk,
+            "e2e_note": "a single layer works on device buffers only; the network line (infer256) has the host path",
+            "layer_s": [round(t, 6) for t in lt],
+        }))
+    return 0
+
+
+def run_infer256(args):
+    """The warm-start network forward on the 256^3 slot grid; roofline of the 32->32 tcgen05 convolution."""
+    import numpy as np
+    import torch
+
+    from paper_2502_04217_gb300 import binding
+    from paper_2502_04217_gb300 import warmstart as wsm
+    from paper_2502_04217_gb300.synth import make_problem
+
+    ws_n, rank, local = _dist()
+    torch.cuda.set_device(local)
+    binding.load()
+    stream = torch.cuda.current_stream()
+    w = make_problem("3d", index=rank)
+    opt = binding.default_options(precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
+    h = binding.ipm_create(w.dims, w.mask, w.y, w.lam_rel, opt, stream=stream.cuda_stream)
+    net = wsm.load(stream=stream.cuda_stream)
+    H, n = binding.ipm_sizes(h)
+    V = H                                   # one voxel per half-spectrum slot
+    D = (w.dims[-1] // 2 + 1, w.dims[0], w.dims[1])
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 512 MB > L2
+
+    def timed(fn):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    fwd = lambda: binding.ws_forward(net, h, None)
+    for _ in range(args.warmup):
+        timed(fwd)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    ts = [timed(fwd) for _ in range(args.steps)]
+    clk = clocks.stop()
+    value = sum(ts) / len(ts)
+    net_flops = 2.0 * V * 27 * sum(cir * cor for _, _, cir, cor in wsm.LAYERS)
+
+    # dominant kernel: one 32 -> 32 layer (bias, ReLU) on the same grid, per-launch events
+    roofline, lt = _conv_layer_roofline(binding, torch, D, max(5, args.steps), timed)
+    roofline["network_tflops"] = net_flops / value / 1e12
+
+    # end to end: problem from pinned host buffers, prediction back to the host
+    mask_h = torch.from_numpy(np.ascontiguousarray(w.mask)).pin_memory()
+    y_h = torch.from_numpy(np.ascontiguousarray(w.y)).pin_memory()
+    out_h = torch.empty(V * 8, dtype=torch.float32).pin_memory()
+    e2e_t = []
+    for i in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binding.ipm_set_problem(h, mask_h, y_h, w.lam_rel)
+        binding.ws_forward(net, h, out_h)
+        t1 = time.perf_counter()
+        if i > 0:
+            e2e_t.append(t1 - t0)
+    e2e = {"value": sum(e2e_t) / len(e2e_t), "unit": "s", "h2d_bytes_per_step": int(mask_h.numel() + y_h.numel() * 8),
+           "d2h_bytes_per_step": int(out_h.numel() * 4)}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        from oracle import warmstart as ows
+        layers = _oracle_layers(binding, net)
+        sub = (8, 32, 32)
+        xs = np.random.default_rng(0).standard_normal(sub + (8,))
+        t0 = time.perf_counter()
+        ows.forward(xs, layers)
+        t_s = time.perf_counter() - t0
+        vs = sub[0] * sub[1] * sub[2]
+        cpu = {"value": t_s * V / vs, "unit": "s", "cores": _cores(), "kind": "oracle", "extrapolated": True,
+               "sample": f"oracle network forward (numpy FP64) on an {sub[0]}x{sub[1]}x{sub[2]} block of random "
+                         f"features ({t_s:.2f} s), scaled by voxel count to the {D[0]}x{D[1]}x{D[2]} grid"}
+    binding.ws_destroy(net)
+    binding.ipm_destroy(h)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "warm-start network inference time (features + 4 convolutions)", "value": value, "unit": "s",
+            "n_gpus": ws_n, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * value,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": _workload_desc("infer256"), "grid": list(D),
+                       "l2": "flushed between steps (512 MB write outside the timed events)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk,
+            "step_s": [round(t, 5) for t in ts], "layer_s": [round(t, 5) for t in lt],
+        }))
     return 0
 
 
@@ -661,6 +953,12 @@ def main():
         return run_batch(args)
     if args.workload == "warm512":
         return run_warm512(args)
+    if args.workload == "infer256":
+        return run_infer256(args)
+    if args.workload == "conv256":
+        return run_conv256(args)
+    if args.workload == "kkt256":
+        return run_kkt256(args)
     return run_ours(args)
 
 

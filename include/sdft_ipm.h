@@ -87,8 +87,8 @@ typedef struct {
                            the device and keep the fastest (cached per shape for the
                            process); 0: a fixed heuristic                                     */
   int tile_e;           /* 0 (default): chosen as above; else force this per-thread element
-                           budget (4 or 8, or 6 or 12 for lengths with a factor 3) wherever
-                           launchable                                                         */
+                           budget (4, 8 or 16, or 6 or 12 for lengths with a factor 3)
+                           wherever launchable                                                */
   int tile_p;           /* 0 (default): chosen as above; else force this many pencils per
                            tile (a power of two) wherever launchable                          */
   int refine_every;     /* IPM_MIXED only.  0 (default): PCG runs on FP32 products and the

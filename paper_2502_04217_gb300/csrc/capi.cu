@@ -51,14 +51,16 @@ bool factor_ok(int L) {
   return m == 1;
 }
 
-// Radices for length L: with element budget E per thread, 8s (E = 8), then 4s
-// (E divisible by 4), then 2s, and a single 3 last when L has a factor 3.
+// Radices for length L: with element budget E per thread, 16s (E = 16), then 8s
+// (E divisible by 8), then 4s (E divisible by 4), then 2s, and a single 3 last
+// when L has a factor 3.
 FftPlan make_plan(int L, int E) {
   FftPlan p{};
   p.L = L;
   int m = L;
   bool three = (m % 3 == 0);
   if (three) m /= 3;
+  while (E % 16 == 0 && m % 16 == 0) { p.radix[p.nst++] = 16; m /= 16; }
   while (E % 8 == 0 && m % 8 == 0) { p.radix[p.nst++] = 8; m /= 8; }
   while (E % 4 == 0 && m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
@@ -195,10 +197,12 @@ ipm_status make_tables(sdft_ipm* h, int L, const void** t64, const void** t32) {
 // Tile configuration of a pass: FFT length L, `rows` shared-memory rows, npen
 // pencils, element budget E per thread, P pencils per tile.  Returns false when
 // the combination is not launchable (P * L must be a multiple of E, at most 512
-// threads, at most 200 KB of shared memory).
+// threads (256 for E = 16, whose kernels keep 16 values per thread and are
+// compiled for that block size), at most 200 KB of shared memory).
 bool make_cfg(PassCfg& c, int L, int rows, long long npen, bool fp32, int E, int P) {
   const int esz = fp32 ? 8 : 16;
-  if ((P * L) % E != 0 || (P * L) / E > 512 || (P * L) / E < 1) return false;
+  const int max_threads = E == 16 ? 256 : 512;
+  if ((P * L) % E != 0 || (P * L) / E > max_threads || (P * L) / E < 1) return false;
   const int PP = (P >= (fp32 ? 16 : 8)) ? P + 1 : P;
   if ((size_t)rows * PP * esz > 200 * 1024) return false;
   c.E = E;
@@ -255,7 +259,7 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
     // forced shape (tests and experiments): keep the default for what is not forced
     const int E = h->opt.tile_e > 0 ? h->opt.tile_e : c.E;
     const int P = h->opt.tile_p > 0 ? h->opt.tile_p : (1 << c.lgP);
-    const bool e_ok = (L % 3 == 0) ? (E == 6 || E == 12) : (E == 4 || E == 8);
+    const bool e_ok = (L % 3 == 0) ? (E == 6 || E == 12) : (E == 4 || E == 8 || E == 16);
     PassCfg t = c;
     if (e_ok && make_cfg(t, L, rows, npen, fp32, E, P)) {
       c = t;
@@ -274,13 +278,15 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
       return IPM_OK;
     }
   }
-  const int Es[2] = {(L % 3 == 0) ? 12 : 8, (L % 3 == 0) ? 6 : 4};
+  const bool three = (L % 3 == 0);
+  const int Es[3] = {three ? 12 : 16, three ? 6 : 8, three ? 0 : 4};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   PassCfg best_c = c;
   for (int E : Es) {
+    if (E == 0) continue;
     for (int P = 1; P <= 32; P *= 2) {
       PassCfg t = c;
       if (!make_cfg(t, L, rows, npen, fp32, E, P)) continue;

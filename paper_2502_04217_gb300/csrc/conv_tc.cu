@@ -10,7 +10,7 @@
 // a, b in {-1, 0, 1}, over z0 - 1 .. z0 + 128.  A CTA walks a segment of
 // consecutive i1 at fixed (i0, z0): each step needs one new "triple" of lines
 // (i0 - 1 .. i0 + 1, i1 + 1), which one TMA copy per 8-channel chunk brings
-// into a ring of four triple slots (zero fill outside the grid).
+// into a ring of triple slots (zero fill outside the grid).
 //
 // Shared-memory layout of the ring (no swizzle, K-major core matrices): for
 // channel chunk c, slot s, line a, voxel row r the 16 bytes of channels
@@ -49,9 +49,15 @@ constexpr int kTileM = 128;                 // voxels per tile (MMA M)
 constexpr int kLineRows = 136;              // voxel rows per staged line (z0 - 1 .. z0 + 134)
 constexpr int kLineBytes = kLineRows * 16;  // one 8-channel chunk of one line
 constexpr int kTripleBytes = 3 * kLineBytes;
-constexpr int kSlots = 4;
-constexpr int kPlaneBytes = kSlots * kTripleBytes;
 constexpr int kSegment = 32;                // i1 steps per work item
+
+// Ring slots: a step uses three triples, the others are prefetched (the TMA
+// runs slots - 3 steps ahead of the MMAs); as many as fit next to the weights.
+template <int CIN>
+struct Ring {
+  static constexpr int kSlots = CIN == 32 ? 6 : 8;
+  static constexpr int kPlaneBytes = kSlots * kTripleBytes;
+};
 constexpr int kThreads = 192;
 constexpr unsigned kWaitLimit = 1u << 24;   // polls of one mbarrier wait (with back-off: seconds)
 
@@ -193,6 +199,8 @@ template <int CIN, int COUT>
 __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap xmap, ConvTcArgs a) {
   constexpr int N = COUT < 16 ? 16 : COUT;     // MMA N (multiple of 16 for M = 128)
   constexpr int KC = CIN / 8;                  // 8-channel chunks
+  constexpr int S = Ring<CIN>::kSlots;
+  constexpr int kPlaneBytes = Ring<CIN>::kPlaneBytes;
   constexpr int HALO = KC * kPlaneBytes;
   constexpr int WBYTES = 27 * KC * N * 16;
   constexpr uint32_t kTmemCols = 2 * N < 32 ? 32 : 2 * N;
@@ -203,9 +211,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   unsigned char* halo = smem;
   unsigned char* wsm = smem + HALO;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + HALO + WBYTES);
-  // bars: full[4], empty[4], accf[2], acce[2], done; then the TMEM address and the abort flag
-  uint32_t& s_tmem = *reinterpret_cast<uint32_t*>(bars + 13);
-  volatile int& s_abort = *reinterpret_cast<volatile int*>(bars + 14);
+  // bars: full[S], empty[S], accf[2], acce[2], done; then the TMEM address and the abort flag
+  uint64_t* full_b = bars;
+  uint64_t* empty_b = bars + S;
+  uint64_t* accf_b = bars + 2 * S;
+  uint64_t* acce_b = bars + 2 * S + 2;
+  uint64_t* done_b = bars + 2 * S + 4;
+  uint32_t& s_tmem = *reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+  volatile int& s_abort = *reinterpret_cast<volatile int*>(bars + 2 * S + 6);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // TMA destinations must be 128-byte aligned: refuse to run otherwise
@@ -225,9 +238,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     *reinterpret_cast<uint4*>(wsm + (size_t)idx * 16) = v;
   }
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) { mbar_init(smem_u32(&bars[i]), 1); mbar_init(smem_u32(&bars[4 + i]), 1); }
-    for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&bars[8 + i]), 1); mbar_init(smem_u32(&bars[10 + i]), 128); }
-    mbar_init(smem_u32(&bars[12]), 1);
+    for (int i = 0; i < S; ++i) { mbar_init(smem_u32(&full_b[i]), 1); mbar_init(smem_u32(&empty_b[i]), 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&accf_b[i]), 1); mbar_init(smem_u32(&acce_b[i]), 128); }
+    mbar_init(smem_u32(done_b), 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -255,70 +268,72 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
         const Item m = item_of(it, a, ztiles, nseg);
         for (int j = 0; j < m.steps + 2 && !s_abort; ++j, ++q) {
-          const int slot = (int)(q & 3);
-          const uint32_t use = (uint32_t)(q >> 2);
-          if (use > 0 && !mbar_wait(smem_u32(&bars[4 + slot]), (use - 1) & 1)) { fail(1); break; }
-          const uint32_t full = smem_u32(&bars[slot]);
+          const int slot = (int)(q % S);
+          const uint32_t use = (uint32_t)(q / S);
+          if (use > 0 && !mbar_wait(smem_u32(&empty_b[slot]), (use - 1) & 1)) { fail(1); break; }
+          const uint32_t full = smem_u32(&full_b[slot]);
           mbar_expect_tx(full, kTxBytes);
           for (int c = 0; c < KC; ++c)
             tma_load_4d(smem_u32(halo + c * kPlaneBytes + slot * kTripleBytes), &xmap, c * 8, m.z0 - 1,
                         m.y0 - 1 + j, m.i0 - 1, full);
         }
       }
-      // own copies in flight: the last (up to) four triples must have landed
-      for (unsigned long long k = (q > 4 ? q - 4 : 0); k < q; ++k)
-        if (!mbar_wait(smem_u32(&bars[k & 3]), (uint32_t)((k >> 2) & 1))) { fail(2); break; }
+      // own copies in flight: the last (up to) S triples must have landed
+      for (unsigned long long k = (q > S ? q - S : 0); k < q; ++k)
+        if (!mbar_wait(smem_u32(&full_b[k % S]), (uint32_t)((k / S) & 1))) { fail(2); break; }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       unsigned long long q = 0;   // first triple of the current item
       unsigned long long tile = 0;
+      const uint32_t hb = smem_u32(halo);
+      const uint64_t adesc0 = smem_desc(0, kPlaneBytes, 128);
+      const uint64_t bdesc0 = smem_desc(smem_u32(wsm), N * 16, 128);
       for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
         const Item m = item_of(it, a, ztiles, nseg);
         for (int s = 0; s < m.steps && !s_abort; ++s, ++tile) {
           bool ok = true;
           for (int b = 0; b < 3 && ok; ++b) {
             const unsigned long long k = q + s + b;
-            ok = mbar_wait(smem_u32(&bars[k & 3]), (uint32_t)((k >> 2) & 1));
+            ok = mbar_wait(smem_u32(&full_b[k % S]), (uint32_t)((k / S) & 1));
           }
           const int buf = (int)(tile & 1);
           const uint32_t use = (uint32_t)(tile >> 1);
-          if (ok && use > 0) ok = mbar_wait(smem_u32(&bars[10 + buf]), (use - 1) & 1);
+          if (ok && use > 0) ok = mbar_wait(smem_u32(&acce_b[buf]), (use - 1) & 1);
           if (!ok) { fail(3); break; }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(buf * N);
-          const uint32_t hb = smem_u32(halo), wb = smem_u32(wsm);
-          int t = 0;
-#pragma unroll 1
-          for (int ta = 0; ta < 3; ++ta) {          // offset along i0 (line within the triple)
-#pragma unroll 1
-            for (int tb = 0; tb < 3; ++tb) {        // offset along i1 (which triple)
-              const int slot = (int)((q + s + tb) & 3);
+          // descriptors: one base per triple slot; the taps and K steps add
+          // compile-time offsets to the 16-byte address field
+          uint64_t aslot[3];
 #pragma unroll
-              for (int tz = 0; tz < 3; ++tz, ++t) { // offset along D2 (row shift)
-                const uint32_t abase = hb + slot * kTripleBytes + ta * kLineBytes + tz * 16;
+          for (int tb = 0; tb < 3; ++tb) aslot[tb] = adesc0 + (uint64_t)((hb + (uint32_t)((q + s + tb) % S) * kTripleBytes) >> 4);
+#pragma unroll
+          for (int ta = 0; ta < 3; ++ta)          // offset along i0 (line within the triple)
+#pragma unroll
+            for (int tb = 0; tb < 3; ++tb)        // offset along i1 (which triple)
+#pragma unroll
+              for (int tz = 0; tz < 3; ++tz)      // offset along D2 (row shift)
 #pragma unroll
                 for (int kc = 0; kc < CIN / 16; ++kc) {
-                  const uint64_t ad = smem_desc(abase + kc * 2 * kPlaneBytes, kPlaneBytes, 128);
-                  const uint64_t bd = smem_desc(wb + (uint32_t)((t * KC + kc * 2) * N * 16), N * 16, 128);
+                  const int t = ta * 9 + tb * 3 + tz;
+                  const uint64_t ad = aslot[tb] + (uint64_t)((ta * kLineBytes + tz * 16 + kc * 2 * kPlaneBytes) >> 4);
+                  const uint64_t bd = bdesc0 + (uint64_t)(((t * KC + kc * 2) * N * 16) >> 4);
                   mma_bf16(d, ad, bd, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
                 }
-              }
-            }
-          }
-          mma_commit(smem_u32(&bars[8 + buf]));           // accumulator ready
-          mma_commit(smem_u32(&bars[4 + ((q + s) & 3)]));  // triple i1 - 1 no longer needed
+          mma_commit(smem_u32(&accf_b[buf]));               // accumulator ready
+          mma_commit(smem_u32(&empty_b[(q + s) % S]));       // triple i1 - 1 no longer needed
           if (s == m.steps - 1) {
-            mma_commit(smem_u32(&bars[4 + ((q + s + 1) & 3)]));
-            mma_commit(smem_u32(&bars[4 + ((q + s + 2) & 3)]));
+            mma_commit(smem_u32(&empty_b[(q + s + 1) % S]));
+            mma_commit(smem_u32(&empty_b[(q + s + 2) % S]));
           }
         }
         q += m.steps + 2;
       }
       // every MMA issued by this thread has completed before TMEM is freed
-      mma_commit(smem_u32(&bars[12]));
-      if (!mbar_wait(smem_u32(&bars[12]), 0)) fail(4);
+      mma_commit(smem_u32(done_b));
+      if (!mbar_wait(smem_u32(done_b), 0)) fail(4);
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
@@ -332,13 +347,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       const Item m = item_of(it, a, ztiles, nseg);
       for (int s = 0; s < m.steps; ++s, ++tile) {
         const int buf = (int)(tile & 1);
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&bars[8 + buf]), (uint32_t)((tile >> 1) & 1)));
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_b[buf]), (uint32_t)((tile >> 1) & 1)));
         if (!ok) { fail(5); break; }
         tc_fence_after();
         float v[N];
         tmem_load<N>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * N), v);
         tc_fence_before();
-        mbar_arrive(smem_u32(&bars[10 + buf]));
+        mbar_arrive(smem_u32(&acce_b[buf]));
         const int z = m.z0 + row;
         if (z < a.D2) {
           const size_t vox = ((size_t)m.i0 * a.D1 + (m.y0 + s)) * a.D2 + z;
@@ -402,7 +417,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 template <int CIN, int COUT>
 cudaError_t launch(const ConvTcArgs& a, cudaStream_t st) {
   constexpr int N = COUT < 16 ? 16 : COUT;
-  constexpr size_t smem = (size_t)(CIN / 8) * kPlaneBytes + (size_t)27 * (CIN / 8) * N * 16 + 16 * sizeof(uint64_t);
+  constexpr int S = Ring<CIN>::kSlots;
+  constexpr size_t smem =
+      (size_t)(CIN / 8) * Ring<CIN>::kPlaneBytes + (size_t)27 * (CIN / 8) * N * 16 + (2 * S + 8) * sizeof(uint64_t);
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   // the activation tensor [D0][D1][D2][CIN] as a 4D map (innermost first)

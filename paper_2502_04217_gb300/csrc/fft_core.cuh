@@ -6,7 +6,8 @@
 // (pencil index fastest, PP = P or P + 1 to spread banks), so the threads of a
 // warp, which walk p fastest, touch consecutive words.
 //
-// Each thread owns E complex values per stage (E/R butterflies of radix R).
+// Each thread owns E complex values per stage (E/R butterflies of radix R;
+// R in {2, 3, 4, 8, 16}, the radix-16 butterfly done as 4 x 4 in registers).
 // A stage reads all its inputs into registers, synchronises, then writes its
 // outputs into the same buffer (Stockham autosort, decimation in time):
 //     for butterfly j of a stage of radix R after Ns = R_1 ... R_{s-1}:
@@ -82,11 +83,48 @@ template <bool INV, typename V> __device__ __forceinline__ void dft3(V* a) {
   a[2] = csub(m, isd);
 }
 
+// a * W16^e (forward: W16 = exp(-2 pi i / 16); inverse: its conjugate), e = 0..9
+template <int e, bool INV, typename V> __device__ __forceinline__ V mul_w16(V a) {
+  using T = decltype(V::x);
+  constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173, h = 0.70710678118654752440;
+  constexpr double cs[10] = {1.0, c1, h, s1, 0.0, -s1, -h, -c1, -1.0, -c1};
+  constexpr double sn[10] = {0.0, s1, h, c1, 1.0, c1, h, s1, 0.0, -s1};
+  if constexpr (e == 0) return a;
+  else {
+    const T c = (T)cs[e], sg = INV ? (T)sn[e] : -(T)sn[e];   // W = c + i sg
+    return cmake<V>(a.x * c - a.y * sg, a.x * sg + a.y * c);
+  }
+}
+
+// 16-point DFT in registers as 4 x 4: with n = n1 + 4 n2 and k = k1 + 4 k2,
+// X[k] = sum_n1 W4^{n1 k2} W16^{n1 k1} sum_n2 a[n1 + 4 n2] W4^{n2 k1}.
+template <bool INV, typename V> __device__ __forceinline__ void dft16(V* a) {
+  V t[4][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    V u[4] = {a[n1], a[n1 + 4], a[n1 + 8], a[n1 + 12]};
+    dft4<INV>(u);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) t[n1][k1] = u[k1];
+  }
+  t[1][1] = mul_w16<1, INV>(t[1][1]); t[1][2] = mul_w16<2, INV>(t[1][2]); t[1][3] = mul_w16<3, INV>(t[1][3]);
+  t[2][1] = mul_w16<2, INV>(t[2][1]); t[2][2] = mul_w16<4, INV>(t[2][2]); t[2][3] = mul_w16<6, INV>(t[2][3]);
+  t[3][1] = mul_w16<3, INV>(t[3][1]); t[3][2] = mul_w16<6, INV>(t[3][2]); t[3][3] = mul_w16<9, INV>(t[3][3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    V u[4] = {t[0][k1], t[1][k1], t[2][k1], t[3][k1]};
+    dft4<INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = u[k2];
+  }
+}
+
 template <int R, bool INV, typename V> __device__ __forceinline__ void dft_r(V* a) {
   if constexpr (R == 2) dft2<INV>(a);
   else if constexpr (R == 3) dft3<INV>(a);
   else if constexpr (R == 4) dft4<INV>(a);
-  else dft8<INV>(a);
+  else if constexpr (R == 8) dft8<INV>(a);
+  else dft16<INV>(a);
 }
 
 // One Stockham stage of radix R over the tile.  nwork = P * L / E threads
@@ -138,6 +176,9 @@ __device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, i
   int lgNs = 0;
   for (int s = 0; s < plan.nst; ++s) {
     const int R = plan.radix[s];
+    if constexpr (E % 16 == 0) {
+      if (R == 16) fft_stage<E, 16, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
+    }
     if constexpr (E % 8 == 0) {
       if (R == 8) fft_stage<E, 8, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
     }
@@ -148,8 +189,84 @@ __device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, i
     if constexpr (E % 3 == 0) {
       if (R == 3) fft_stage<E, 3, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
     }
-    lgNs += (R == 8) ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));   // radix 3 is last
+    lgNs += (R == 16) ? 4 : (R == 8) ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));   // radix 3 is last
   }
+}
+
+// ---- compile-time lengths ------------------------------------------------
+// For the common power-of-two lengths the stage schedule (the same as the
+// host plan: 16s, then 8s, 4s, 2s as E allows) is fixed at compile time, so
+// every stride, mask and twiddle step below is a constant.
+__host__ __device__ constexpr int stage_radix_c(int L, int E, int s) {
+  int m = L, r = 2;
+  for (int i = 0; i <= s; ++i) {
+    r = (E % 16 == 0 && m % 16 == 0) ? 16 : (E % 8 == 0 && m % 8 == 0) ? 8 : (E % 4 == 0 && m % 4 == 0) ? 4 : 2;
+    if (i < s) m /= r;
+  }
+  return r;
+}
+__host__ __device__ constexpr int stage_count_c(int L, int E) {
+  int m = L, n = 0;
+  while (m > 1) { m /= stage_radix_c(m, E, 0); ++n; }
+  return n;
+}
+__host__ __device__ constexpr int log2_c(int v) { return v <= 1 ? 0 : 1 + log2_c(v / 2); }
+
+template <int E, int R, bool INV, int L, int LGNS, typename V>
+__device__ __forceinline__ void fft_stage_c(V* buf, int lgP, int PP, const V* __restrict__ tw, int tid, int nwork) {
+  constexpr int B = E / R, Ns = 1 << LGNS, LR = L / R, TWS = L / (Ns * R);
+  V a[B][R];
+  const bool active = tid < nwork;
+  const int pmask = (1 << lgP) - 1, sLR = LR * PP, sNs = Ns * PP;
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int w = tid + b * nwork;
+      const int p = w & pmask, j = w >> lgP, k = j & (Ns - 1);
+      const V* src = buf + j * PP + p;
+      const int kt = k * TWS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        V v = src[r * sLR];
+        if (r > 0 && Ns > 1) {
+          const V t = __ldg(tw + kt * r);
+          v = INV ? cmulconj(v, t) : cmul(v, t);
+        }
+        a[b][r] = v;
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int w = tid + b * nwork;
+      const int p = w & pmask, j = w >> lgP, k = j & (Ns - 1);
+      dft_r<R, INV>(a[b]);
+      V* dst = buf + (((j >> LGNS) << LGNS) * R + k) * PP + p;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * sNs] = a[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int E, bool INV, int L, int S, int LGNS, typename V>
+__device__ __forceinline__ void fft_stages_c(V* buf, int lgP, int PP, const V* __restrict__ tw, int tid, int nwork) {
+  if constexpr (S < stage_count_c(L, E)) {
+    constexpr int R = stage_radix_c(L, E, S);
+    fft_stage_c<E, R, INV, L, LGNS>(buf, lgP, PP, tw, tid, nwork);
+    fft_stages_c<E, INV, L, S + 1, LGNS + log2_c(R)>(buf, lgP, PP, tw, tid, nwork);
+  }
+}
+
+// Full transform with the length fixed at compile time (LC > 0) or taken from
+// the plan (LC = 0).
+template <int E, bool INV, int LC, typename V>
+__device__ __forceinline__ void fft_tile_l(V* buf, const FftPlan& plan, int lgP, int PP, const V* __restrict__ tw,
+                                           int tid, int nwork) {
+  if constexpr (LC > 0) fft_stages_c<E, INV, LC, 0, 0>(buf, lgP, PP, tw, tid, nwork);
+  else fft_tile<E, INV>(buf, plan, lgP, PP, tw, tid, nwork);
 }
 
 }  // namespace sdft

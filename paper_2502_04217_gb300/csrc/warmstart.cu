@@ -545,7 +545,6 @@ ipm_status repack(sdft_ws* n) {
   return IPM_OK;
 }
 
-// Forward pass on the handle's c: features -> 4 convolutions -> y (FP32 [V][8]).
 // Synchronise st, then report an expired pipeline wait of the tensor-core convolution.
 ipm_status sync_check(cudaStream_t st) {
   unsigned code = 0;
@@ -556,6 +555,7 @@ ipm_status sync_check(cudaStream_t st) {
   return IPM_OK;
 }
 
+// Forward pass on the handle's c: features -> 4 convolutions -> y (FP32 [V][8]).
 ipm_status forward(sdft_ws* n, const HandleView& hv) {
   int D0, D1, D2;
   grid_dims(hv.lay, D0, D1, D2);

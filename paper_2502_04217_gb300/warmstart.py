@@ -21,6 +21,13 @@ from .synth import lattice_mask, make_problem
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart.f32")
+# mu0 = MU_SCALE lambda^2 of the predicted start point: of {0.3, 0.5, 0.7, 1, 1.5, 2}
+# the value with the fewest IPM iterations on held-out 512^3 instances (8 vs 9-11
+# for the others and the cold start); 0.3 does as well on 256^3.
+MU_SCALE = 0.5
+
+# (stored cin, stored cout, real cin, real cout) of the four convolutions
+LAYERS = [(16, 32, 8, 32), (32, 32, 32, 32), (32, 32, 32, 32), (32, 8, 32, 4)]
 
 
 def instance(side, i, seed=0):

@@ -22,8 +22,8 @@ from layout import ghost_mask, lib_to_half, oracle_to_half, oracle_to_lib, to_de
 pytestmark = pytest.mark.gpu
 
 SIZES = [(8,), (12,), (96,), (256,), (512,),
-         (8, 6), (16, 12), (48, 64), (64, 48), (96, 32),
-         (4, 6, 8), (8, 8, 8), (16, 12, 8), (12, 16, 24), (32, 24, 16)]
+         (8, 6), (16, 12), (48, 64), (64, 48), (96, 32), (512, 16),
+         (4, 6, 8), (8, 8, 8), (16, 12, 8), (12, 16, 24), (32, 24, 16), (128, 256, 16), (16, 128, 256)]
 
 
 def _workload(dims, seed=0, missing=0.15):
@@ -282,14 +282,16 @@ def test_pcg_cap_reported():
         binding.ipm_destroy(h)
 
 
-@pytest.mark.parametrize("tile_e,tile_p", [(4, 1), (4, 4), (8, 1), (8, 16), (4, 32)])
-@pytest.mark.parametrize("dims", [(512,), (96, 32), (64, 48), (12, 16, 24), (32, 24, 16)])
+@pytest.mark.parametrize("tile_e,tile_p", [(4, 1), (4, 4), (8, 1), (8, 16), (4, 32), (16, 1), (16, 8)])
+@pytest.mark.parametrize("dims", [(512,), (96, 32), (64, 48), (12, 16, 24), (32, 24, 16), (256, 128),
+                                  (16, 128, 256)])
 def test_every_tile_shape_matches_oracle(dims, tile_e, tile_p):
     """The autotuner may pick any launchable tile shape: each one must compute the
-    same product.  Lengths with a factor 3 map E=4 -> 6 and E=8 -> 12."""
+    same product.  Lengths with a factor 3 map E=4 -> 6 and E=8, 16 -> 12
+    (E=16: radix-16 stages, then 8, 4, 2)."""
     for precision in (binding.IPM_FP64, binding.IPM_MIXED):
         w = _workload(dims, seed=15)
-        three = {4: 6, 8: 12}
+        three = {4: 6, 8: 12, 16: 12}
         h = None
         try:
             # one option set per call; lengths with a factor 3 ignore the power-of-two budgets and
