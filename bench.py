@@ -61,6 +61,9 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-kkt", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the IPM and PCG loops from the host (use_graph = 0: the same kernels, launched one by "
+                         "one; ncu cannot profile kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--workload", choices=["1d", "2d", "3d", "batch", "warm512", "infer256", "conv256", "kkt256"], default="2d",
                     help="2d: 512^2 FP64 (default); 1d: n=256 FP64; 3d: 256^3 mixed precision; "
                          "batch: 48 uneven 3D problems in one graph launch, mixed precision; "
@@ -254,7 +257,7 @@ def run_ours(args):
     w = make_problem(args.workload, index=rank)
     prec = WORKLOADS[args.workload][1]
     opt = binding.default_options(precision=binding.IPM_MIXED if prec == "mixed" else binding.IPM_FP64,
-                                  gap_tol=GAP_TOL, lambda_relative=1)
+                                  gap_tol=GAP_TOL, lambda_relative=1, use_graph=0 if args.host_loop else 1)
     mask_d = torch.from_numpy(np.ascontiguousarray(w.mask)).cuda()
     y_d = torch.from_numpy(np.ascontiguousarray(w.y)).cuda()
     h = binding.ipm_create(w.dims, mask_d, y_d, w.lam_rel, opt, stream=stream.cuda_stream)
@@ -376,7 +379,8 @@ def run_ours(args):
             "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": _workload_desc(args.workload), "dims": list(w.dims), "gap_tol": GAP_TOL,
                        "l2": "flushed between steps (512 MB write outside the timed events)",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "launch": "host-driven loops" if args.host_loop else "one CUDA graph per solve"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "solve": {"ipm_iters": res["ipm_iters"], "cg_iters_total": res["cg_iters_total"],
                       "kkt_products": res["kkt_products"], "rel_gap": res["rel_gap"], "primal": res["primal"],
@@ -472,17 +476,9 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     binding.load()
     allw = batch_workloads(48)
-    # greedy split by cost ~ n log n: each rank takes the next-largest problem while lightest
-    order = sorted(range(len(allw)), key=lambda i: -int(np.prod(allw[i].dims)))
-    loads = [0.0] * ws_n
-    mine = []
-    for i in order:
-        r = min(range(ws_n), key=lambda k: loads[k])
-        n = float(np.prod(allw[i].dims))
-        loads[r] += n * np.log2(n)
-        if r == rank:
-            mine.append(i)
-    ws = [allw[i] for i in sorted(mine)]
+    # the 48 problems are split across ranks (cost n log2 n, largest first to the lightest rank)
+    from paper_2502_04217_gb300 import shard
+    ws = [allw[i] for i in shard.rank_share([w.dims for w in allw], ws_n, rank)]
     stream = torch.cuda.current_stream()
     opt = binding.default_options(precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
     b = binding.ipm_create_batch([(w.dims, w.mask, w.y, w.lam_rel) for w in ws], opt, stream=stream.cuda_stream)
@@ -517,11 +513,7 @@ def run_batch(args):
         dist.barrier()
     clk = clocks.stop()
     launches = sum(binding.ipm_profile_get(h, 5)[0] for h in members)
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = shard.max_over_ranks(sum(step_ms), dist, device="cuda")
     value = total_ms / 1e3 / args.steps
     # aggregate algorithmic bytes of all FFT passes of all members, per batch
     nbytes = 0.0
@@ -575,7 +567,7 @@ def run_batch(args):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws_n, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
-            "scaling": "weak" if ws_n > 1 else "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": _workload_desc("batch"), "problems": len(allw),
                        "problems_this_rank": len(ws), "voxels": int(sum(np.prod(w.dims) for w in allw)),

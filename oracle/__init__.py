@@ -22,6 +22,8 @@ ipm       the primal-dual interior-point method: Newton system (Eq. (augkkt)),
           back-substitution and step rule (Sec. 3.3-3.5).
 brute     independent solvers for tiny instances used as pins: active-set
           enumeration and proximal gradient; soft-thresholding closed form.
+warmstart the learned warm start (not in the paper): features, the 3D
+          convolution network, its loss and gradients, in plain numpy FP64.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, numpy/scipy library routines, invariants the paper
