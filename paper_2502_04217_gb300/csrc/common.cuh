@@ -11,6 +11,44 @@ namespace sdft {
 // ---------------------------------------------------------------------------
 // Complex helpers (double2 / float2 as interleaved re, im)
 // ---------------------------------------------------------------------------
+// Exact double <-> float conversions in integer arithmetic.  On this GPU a
+// conversion with a 64-bit operand runs on the FP64 pipe (1/64 of FP32), where it
+// costs as much as an FP64 FMA; the FP32 pass kernels convert every element of
+// their FP64 vectors, so these take the integer pipe instead.  Normal numbers
+// only (round to nearest even for d2f, with the carry into the exponent and
+// overflow to infinity done by the addition); zeros, subnormals, infinities and
+// NaN take the hardware conversion.
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e >= 1 && e <= 254) {
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const unsigned r = (unsigned)(m >> 29);               // leading 23 mantissa bits
+    const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);   // the 29 bits dropped
+    unsigned f = ((unsigned)e << 23) | r;
+    f += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+    return __uint_as_float(f | (hi & 0x80000000u));
+  }
+  return (float)x;
+}
+__device__ __forceinline__ double f2d_int(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e != 0u && e != 255u) {
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+  }
+  return (double)x;
+}
+template <typename T> __device__ __forceinline__ T from_double(double x);
+template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_int(x); }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return f2d_int(x); }
+
 template <typename T> struct cvec;
 template <> struct cvec<double> { using type = double2; };
 template <> struct cvec<float> { using type = float2; };

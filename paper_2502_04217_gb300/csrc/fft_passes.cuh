@@ -20,6 +20,8 @@
 // Included by fft_passes_f32.cu and fft_passes_f64.cu (one precision each).
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace sdft {
@@ -34,27 +36,30 @@ template <typename V>
 __device__ __forceinline__ V map_in(int cls, double b0, double b1) {
   using T = decltype(V::x);
   if (cls == EDGE_TWIN) return cmake<V>((T)0, (T)0);
-  if (cls == EDGE_SC) return cmake<V>((T)b0, (T)0);
+  if (cls == EDGE_SC) return cmake<V>(from_double<T>(b0), (T)0);
   const T s = (cls == INTERIOR) ? (T)kSqrtHalf : (T)kSqrt2;
-  return cmake<V>((T)b0 * s, (T)b1 * s);
+  return cmake<V>(from_double<T>(b0) * s, from_double<T>(b1) * s);
 }
 
 template <typename V>
 __device__ __forceinline__ void map_out(int cls, V w, double scale, double& o0, double& o1) {
   using T = decltype(V::x);
   if (cls == EDGE_TWIN) { o0 = 0.0; o1 = 0.0; return; }
-  if (cls == EDGE_SC) { o0 = (double)(w.x * (T)scale); o1 = 0.0; return; }
+  if (cls == EDGE_SC) { o0 = to_double(w.x * (T)scale); o1 = 0.0; return; }
   const T s = (T)(kSqrt2 * scale);
-  o0 = (double)(w.x * s);
-  o1 = (double)(w.y * s);
+  o0 = to_double(w.x * s);
+  o1 = to_double(w.y * s);
 }
 
-// Load the complex value of slot g for the first pass.
+// Load the complex value of slot g for the first pass.  The FP64 vectors stream
+// through with the evict-first hint (ld/st .cs) so that the pass-to-pass work
+// buffer (67.6 MB in FP32 at 256^3) keeps its place in L2.
 template <typename V>
 __device__ __forceinline__ V load_slot(const PassArgs& a, long long g) {
+  if (a.mapin == MAPIN_NONE) return reinterpret_cast<const V*>(a.buf)[g];
   const int cls = slot_class(a.lay, g);
   if (a.mapin == MAPIN_BETA) {
-    const double2 b = reinterpret_cast<const double2*>(a.src)[g];
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(a.src) + g);
     return map_in<V>(cls, b.x, b.y);
   }
   if (a.mapin == MAPIN_PCG) {
@@ -63,12 +68,12 @@ __device__ __forceinline__ V load_slot(const PassArgs& a, long long g) {
     const double bc = a.sc->beta_cg;
     double2* p2 = reinterpret_cast<double2*>(a.p);
     const double2* z2 = reinterpret_cast<const double2*>(a.zv);
-    double2 pb = p2[g], pz = p2[H2 + g];
-    const double2 zb = z2[g], zz = z2[H2 + g];
+    double2 pb = __ldcs(p2 + g), pz = __ldcs(p2 + H2 + g);
+    const double2 zb = __ldcs(z2 + g), zz = __ldcs(z2 + H2 + g);
     pb.x = zb.x + bc * pb.x; pb.y = zb.y + bc * pb.y;
     pz.x = zz.x + bc * pz.x; pz.y = zz.y + bc * pz.y;
-    p2[g] = pb;
-    p2[H2 + g] = pz;
+    __stcs(p2 + g, pb);
+    __stcs(p2 + H2 + g, pz);
     return map_in<V>(cls, pb.x, pb.y);
   }
   return reinterpret_cast<const V*>(a.buf)[g];
@@ -76,7 +81,7 @@ __device__ __forceinline__ V load_slot(const PassArgs& a, long long g) {
 
 // Store the complex value of slot g for the last pass; inside PCG also adds this
 // slot's share of p^T q to acc (FP64 work only where it is needed).
-template <typename V>
+template <typename V, bool PQ>
 __device__ __forceinline__ void store_slot(const PassArgs& a, long long g, V w, double& acc) {
   if (a.mapout == MAPOUT_NONE) {
     reinterpret_cast<V*>(a.buf)[g] = w;
@@ -86,25 +91,25 @@ __device__ __forceinline__ void store_slot(const PassArgs& a, long long g, V w, 
   double o0, o1;
   if (a.mapout == MAPOUT_BETA) {
     map_out(cls, w, a.out_scale, o0, o1);
-    reinterpret_cast<double2*>(a.dst)[g] = make_double2(o0, o1);
+    __stcs(reinterpret_cast<double2*>(a.dst) + g, make_double2(o0, o1));
     return;
   }
   // MAPOUT_K: q = [G p_b + L1 p_b + L2 p_z ; L2 p_b + L1 p_z]
   map_out(cls, w, 1.0, o0, o1);
   const long long H2 = a.lay.H;
   const double2* p2 = reinterpret_cast<const double2*>(a.p);
-  const double2 pb = p2[g], pz = p2[H2 + g];
-  const double2 l1 = reinterpret_cast<const double2*>(a.lam1)[g];
-  const double2 l2 = reinterpret_cast<const double2*>(a.lam2)[g];
+  const double2 pb = __ldcs(p2 + g), pz = __ldcs(p2 + H2 + g);
+  const double2 l1 = __ldcs(reinterpret_cast<const double2*>(a.lam1) + g);
+  const double2 l2 = __ldcs(reinterpret_cast<const double2*>(a.lam2) + g);
   double2 qb, qz;
   qb.x = o0 + l1.x * pb.x + l2.x * pz.x;
   qb.y = o1 + l1.y * pb.y + l2.y * pz.y;
   qz.x = l2.x * pb.x + l1.x * pz.x;
   qz.y = l2.y * pb.y + l1.y * pz.y;
   double2* q2 = reinterpret_cast<double2*>(a.q);
-  q2[g] = qb;
-  q2[H2 + g] = qz;
-  if (a.pcg_mode) acc += pb.x * qb.x + pb.y * qb.y + pz.x * qz.x + pz.y * qz.y;
+  __stcs(q2 + g, qb);
+  __stcs(q2 + H2 + g, qz);
+  if constexpr (PQ) acc += pb.x * qb.x + pb.y * qb.y + pz.x * qz.x + pz.y * qz.y;
 }
 
 __device__ __forceinline__ void finish_pq(const PassArgs& a, double acc, double* scratch) {
@@ -147,11 +152,15 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) row_pass_kernel(PassAr
   __syncthreads();
   fft_tile_l<E, INV, LC>(buf, a.plan, a.lgP, PP, reinterpret_cast<const V*>(a.tw), threadIdx.x, a.nwork);
   double acc = 0.0;
-  for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
-    const int p = idx / L, e = idx - p * L;
-    const long long row = row0 + p;
-    if (row < a.npencils) store_slot<V>(a, row * L + e, buf[e * PP + p], acc);
-  }
+  auto store_all = [&](auto pq) {
+    for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
+      const int p = idx / L, e = idx - p * L;
+      const long long row = row0 + p;
+      if (row < a.npencils) store_slot<V, decltype(pq)::value>(a, row * L + e, buf[e * PP + p], acc);
+    }
+  };
+  if (a.pcg_mode) store_all(std::true_type{});
+  else store_all(std::false_type{});
   if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
 }
 
@@ -262,6 +271,7 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
     }
     __syncthreads();
     fft_tile_l<E, true, LC>(buf, a.plan, a.lgP, PP, twh, tid, nwork);
+    const T invn = (T)a.inv_n;
     // mask and 1/n: Re z_j <-> sample 2j, Im z_j <-> sample 2j+1 of pencil x'
     if (tid < nwork) {
 #pragma unroll
@@ -270,8 +280,8 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
         const int p = w & (P - 1), j = w >> a.lgP;
         const int xp = x0 + p;
         const uint32_t mw = (xp < M) ? __ldg(&a.maskw[(size_t)((2 * j) >> 5) * M + xp]) : 0u;
-        const T m0 = ((mw >> ((2 * j) & 31)) & 1u) ? (T)a.inv_n : (T)0;
-        const T m1 = ((mw >> ((2 * j + 1) & 31)) & 1u) ? (T)a.inv_n : (T)0;
+        const T m0 = ((mw >> ((2 * j) & 31)) & 1u) ? invn : (T)0;
+        const T m1 = ((mw >> ((2 * j + 1) & 31)) & 1u) ? invn : (T)0;
         V z = buf[j * PP + p];
         z.x *= m0;
         z.y *= m1;
@@ -283,23 +293,27 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
   fft_tile_l<E, false, LC>(buf, a.plan, a.lgP, PP, twh, tid, nwork);
   // R2C post-processing: X'_k = (Z_k + conj Z_{h-k})/2 - i W^k (Z_k - conj Z_{h-k})/2, X'_h = Re Z_0 - Im Z_0
   double acc = 0.0;
-  if (tid < nwork) {
+  auto store_all = [&](auto pq) {
+    if (tid < nwork) {
 #pragma unroll
-    for (int b = 0; b < E; ++b) {
-      const int w = tid + b * nwork;
-      const int p = w & (P - 1), k = w >> a.lgP;
-      const int xp = x0 + p;
-      const V zk = buf[k * PP + p];
-      const V zc = cconj(buf[((h - k) % h) * PP + p]);
-      const V s = cscale(cadd(zk, zc), (T)0.5);
-      const V d = cscale(csub(zk, zc), (T)0.5);
-      const V X = csub(s, cmul_i(cmul(__ldg(&twN[k]), d)));
-      if (xp < M) {
-        store_slot<V>(a, (long long)k * M + xp, X, acc);
-        if (k == 0) store_slot<V>(a, (long long)h * M + xp, cmake<V>(zk.x - zk.y, (T)0), acc);
+      for (int b = 0; b < E; ++b) {
+        const int w = tid + b * nwork;
+        const int p = w & (P - 1), k = w >> a.lgP;
+        const int xp = x0 + p;
+        const V zk = buf[k * PP + p];
+        const V zc = cconj(buf[((h - k) % h) * PP + p]);
+        const V s = cscale(cadd(zk, zc), (T)0.5);
+        const V d = cscale(csub(zk, zc), (T)0.5);
+        const V X = csub(s, cmul_i(cmul(__ldg(&twN[k]), d)));
+        if (xp < M) {
+          store_slot<V, decltype(pq)::value>(a, (long long)k * M + xp, X, acc);
+          if (k == 0) store_slot<V, decltype(pq)::value>(a, (long long)h * M + xp, cmake<V>(zk.x - zk.y, (T)0), acc);
+        }
       }
     }
-  }
+  };
+  if (a.pcg_mode) store_all(std::true_type{});
+  else store_all(std::false_type{});
   if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
 }
 

@@ -26,9 +26,11 @@ __device__ __forceinline__ bool first_thread() { return threadIdx.x == 0 && bloc
 // GB300 executes FP64 divides at ~58 G/s, several times the cost of these four
 // FMAs.  Outside the single-precision normal range it falls back to a divide.
 __device__ __forceinline__ double rcp(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
-  double y = (double)__frcp_rn((float)x);
+  // range test on the exponent bits (integer pipe); outside 2^+-120, 0, inf, NaN: divide
+  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
+  if (ex < -120 || ex > 120) return 1.0 / x;
+  double y = f2d_int(__frcp_rn(d2f_int(x)));      // the same values as the hardware conversions
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);
@@ -374,14 +376,12 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
   if (sc->ipm_done) return;
   const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu;
-  // ratio test min over {w / (-dw) : dw < 0}: candidates are compared as fractions
-  // (num * best_den < best_num * den, all positive), so each thread divides once
-  double bn = 1.0, bd = 0.0;          // best fraction so far; bd = 0 means +inf
+  // ratio test min over {w / (-dw) : dw < 0} in FP32 (operands converted on the
+  // integer pipe): alpha_max is then known to ~1e-7 relative, far inside the
+  // fraction-to-boundary margin tau < 1, so the step keeps s, nu > 0
+  float best = __int_as_float(0x7f800000);   // +inf
   auto consider = [&](double wv, double dw) {
-    if (dw < 0.0) {
-      const double den = -dw;
-      if (bd == 0.0 || wv * bd < bn * den) { bn = wv; bd = den; }
-    }
+    if (__double_as_longlong(dw) < 0) best = fminf(best, d2f_int(wv) / d2f_int(-dw));
   };
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i)) continue;
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
     consider(w.nu1[i], d.dn1);
     consider(w.nu2[i], d.dn2);
   }
-  double v[1] = {bd == 0.0 ? 1.0 / 0.0 : bn / bd};
+  double v[1] = {(double)best};
   const int ops[1] = {RED_MIN};
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) sc->alpha = fmin(1.0, tau * v[0]);
 }
