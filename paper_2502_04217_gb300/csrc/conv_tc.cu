@@ -26,7 +26,7 @@
 // allocation and one lane issues the MMAs (27 x CIN/16 per tile, M = 128,
 // N, K = 16), warps 2..5 drain the accumulator (warp w reads TMEM lanes
 // 32 (w mod 4) ..) and write bias + ReLU (+ ReLU mask of the data gradient)
-// in BF16 and/or FP32.  Two accumulator buffers in TMEM let the MMAs of one
+// in BF16 and/or FP32, staged through shared memory into coalesced rows.  Two accumulator buffers in TMEM let the MMAs of one
 // tile overlap the epilogue of the previous one.
 //
 // Every wait on an mbarrier has an iteration limit; on expiry the kernel
@@ -181,6 +181,29 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
 }
 
+// Write 32 rows of RB bytes (one per lane, as 16-byte chunks ch) to the
+// contiguous global rows gdst[0 .. nvalid): through a per-warp shared-memory
+// stage whose chunk positions are XOR-swizzled so that both the row-wise writes
+// and the chunk-wise reads of 8 consecutive lanes hit distinct banks.
+template <int RB>
+__device__ __forceinline__ void stage_rows(unsigned char* st, int lane, const uint4 (&ch)[RB / 16], unsigned char* gdst,
+                                           int nvalid) {
+  constexpr int NC = RB / 16;     // chunks per row
+  constexpr int RPL = 128 / RB;   // rows per 128-byte bank line
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    *reinterpret_cast<uint4*>(st + lane * RB + ((c ^ ((lane / RPL) % NC)) * 16)) = ch[c];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const int q = k * 32 + lane, vv = q / NC, c = q % NC;
+    if (vv < nvalid)
+      *reinterpret_cast<uint4*>(gdst + (size_t)q * 16) =
+          *reinterpret_cast<const uint4*>(st + vv * RB + ((c ^ ((vv / RPL) % NC)) * 16));
+  }
+}
+
 // Work item -> (i0, z-tile, first i1, steps)
 struct Item {
   int i0, z0, y0, steps;
@@ -210,8 +233,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
 
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* halo = smem;
+  constexpr int STAGE = 4 * 32 * COUT * 4;     // epilogue staging: 4 warps x 32 rows x COUT FP32
   unsigned char* wsm = smem + HALO;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + HALO + WBYTES);
+  unsigned char* stage = smem + HALO + WBYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + HALO + WBYTES + STAGE);
   // bars: full[S], empty[S], accf[2], acce[2], done; then the TMEM address and the abort flag
   uint64_t* full_b = bars;
   uint64_t* empty_b = bars + S;
@@ -356,14 +381,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         tc_fence_before();
         mbar_arrive(smem_u32(&acce_b[buf]));
         const int z = m.z0 + row;
-        if (z < a.D2) {
-          const size_t vox = ((size_t)m.i0 * a.D1 + (m.y0 + s)) * a.D2 + z;
+        const size_t line = ((size_t)m.i0 * a.D1 + (m.y0 + s)) * a.D2;
 #pragma unroll
-          for (int o = 0; o < COUT; ++o) {
-            float y = v[o] + bias[o];
-            if (a.relu) y = fmaxf(y, 0.f);
-            v[o] = y;
-          }
+        for (int o = 0; o < COUT; ++o) {
+          float y = v[o] + bias[o];
+          if (a.relu) y = fmaxf(y, 0.f);
+          v[o] = y;
+        }
+        if (z < a.D2) {
+          const size_t vox = line + z;
           if (a.aux) {
             const uint4* ax = reinterpret_cast<const uint4*>(a.aux + vox * COUT);
 #pragma unroll
@@ -377,17 +403,28 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
               }
             }
           }
+        }
+        // the warp's 32 rows are consecutive voxels: stage them in shared memory and
+        // write contiguous 512-byte spans (the rows past D2 are not written)
+        const int zw = m.z0 + quarter * 32;
+        const int nvalid = min(32, a.D2 - zw);
+        if (nvalid > 0) {
+          unsigned char* st = stage + quarter * (32 * COUT * 4);
           if (a.ybf) {
-            uint4* yo = reinterpret_cast<uint4*>(a.ybf + vox * COUT);
+            uint4 ch[COUT / 8];
 #pragma unroll
             for (int c = 0; c < COUT / 8; ++c)
-              yo[c] = make_uint4(pack_bf16(v[c * 8], v[c * 8 + 1]), pack_bf16(v[c * 8 + 2], v[c * 8 + 3]),
+              ch[c] = make_uint4(pack_bf16(v[c * 8], v[c * 8 + 1]), pack_bf16(v[c * 8 + 2], v[c * 8 + 3]),
                                  pack_bf16(v[c * 8 + 4], v[c * 8 + 5]), pack_bf16(v[c * 8 + 6], v[c * 8 + 7]));
+            stage_rows<COUT * 2>(st, lane, ch, reinterpret_cast<unsigned char*>(a.ybf + (line + zw) * COUT), nvalid);
           }
           if (a.yf) {
-            float4* yo = reinterpret_cast<float4*>(a.yf + vox * COUT);
+            uint4 ch[COUT / 4];
 #pragma unroll
-            for (int c = 0; c < COUT / 4; ++c) yo[c] = make_float4(v[c * 4], v[c * 4 + 1], v[c * 4 + 2], v[c * 4 + 3]);
+            for (int c = 0; c < COUT / 4; ++c)
+              ch[c] = make_uint4(__float_as_uint(v[c * 4]), __float_as_uint(v[c * 4 + 1]), __float_as_uint(v[c * 4 + 2]),
+                                 __float_as_uint(v[c * 4 + 3]));
+            stage_rows<COUT * 4>(st, lane, ch, reinterpret_cast<unsigned char*>(a.yf + (line + zw) * COUT), nvalid);
           }
         }
       }
@@ -419,8 +456,8 @@ template <int CIN, int COUT>
 cudaError_t launch(const ConvTcArgs& a, cudaStream_t st) {
   constexpr int N = COUT < 16 ? 16 : COUT;
   constexpr int S = Ring<CIN>::kSlots;
-  constexpr size_t smem =
-      (size_t)(CIN / 8) * Ring<CIN>::kPlaneBytes + (size_t)27 * (CIN / 8) * N * 16 + (2 * S + 8) * sizeof(uint64_t);
+  constexpr size_t smem = (size_t)(CIN / 8) * Ring<CIN>::kPlaneBytes + (size_t)27 * (CIN / 8) * N * 16 +
+                          (size_t)4 * 32 * COUT * 4 + (2 * S + 8) * sizeof(uint64_t);
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   // the activation tensor [D0][D1][D2][CIN] as a 4D map (innermost first)

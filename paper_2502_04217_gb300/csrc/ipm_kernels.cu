@@ -21,20 +21,17 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ bool first_thread() { return threadIdx.x == 0 && blockIdx.x == 0; }
 
-// 1/x by two Newton-Raphson steps y <- y + y (1 - x y) from a single-precision
-// seed (~23 correct bits -> ~46 -> full double precision, within about one ulp).
-// GB300 executes FP64 divides at ~58 G/s, several times the cost of these four
-// FMAs.  Outside the single-precision normal range it falls back to a divide.
-__device__ __forceinline__ double rcp(double x) {
-  // range test on the exponent bits (integer pipe); outside 2^+-120, 0, inf, NaN: divide
+// 1/x by ONE Newton step y <- y + y (1 - x y) from the single-precision seed
+// (conversions on the integer pipe): relative error about (1.2e-7)^2 = 1.4e-14,
+// used for the barrier scalings of the Newton system, whose perturbation at that
+// level is invisible next to the PCG tolerance.  GB300 executes FP64 divides at
+// ~58 G/s; outside 2^+-120 (and for 0, inf, NaN) this falls back to a divide.
+__device__ __forceinline__ double rcp1(double x) {
   const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
   const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
   if (ex < -120 || ex > 120) return 1.0 / x;
-  double y = f2d_int(__frcp_rn(d2f_int(x)));      // the same values as the hardware conversions
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double y = f2d_int(__frcp_rn(d2f_int(x)));
+  return fma(y, fma(-x, y, 1.0), y);
 }
 
 __device__ __forceinline__ void set_cond(const LoopCtl& c, unsigned v) {
@@ -200,19 +197,20 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, rb = 0, rc = 0, zb = 0, zz = 0, is1 = 0, is2 = 0;
     if (!is_ghost(lay, i)) {
       const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
-      is1 = rcp(s1);
-      is2 = rcp(s2);
+      is1 = rcp1(s1);
+      is2 = rcp1(s2);
       const double S1 = n1 * is1, S2 = n2_ * is2;              // Sigma_i = S_i^{-1} V_i
       const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
       const double r_z = lam - n1 - n2_;
       const double r_p1 = z + b - s1, r_p2 = z - b - s2;
-      const double rc1s = n1 - smu * is1;                       // r_c1 / s1 = (s1 nu1 - sigma mu) / s1
-      const double rc2s = n2_ - smu * is2;
-      rb = -r_d - rc1s - S1 * r_p1 + rc2s + S2 * r_p2;
-      rc = -r_z - rc1s - S1 * r_p1 - rc2s - S2 * r_p2;
+      // r_c_i / s_i + Sigma_i r_p_i = nu_i + (nu_i r_p_i - sigma mu) / s_i
+      const double A1 = fma(is1, fma(n1, r_p1, -smu), n1);
+      const double A2 = fma(is2, fma(n2_, r_p2, -smu), n2_);
+      rb = -r_d - A1 + A2;
+      rc = -r_z - A1 - A2;
       l1 = S1 + S2;
       l2 = S1 - S2;
-      const double iD = rcp(S1 + S2 + 4.0 * S1 * S2);          // D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2
+      const double iD = rcp1(fma(4.0 * S1, S2, l1));            // D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2
       pa = l1 * iD;
       pb = l2 * iD;
       pc = (1.0 + l1) * iD;
