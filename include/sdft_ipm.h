@@ -297,6 +297,14 @@ ipm_status ws_train_step(sdft_ws* net, sdft_ipm* h, const double* beta_star, flo
  * y [V][cout] FP32; (cin, cout) in {16, 32} x {8, 32}; V = d0 d1 d2. */
 ipm_status ws_conv_forward(int cin, int cout, int d0, int d1, int d2, const uint16_t* x, const uint16_t* w,
                            const float* bias, int relu, const uint16_t* aux, float* y, void* stream);
+/* Failure-detection test of the tensor-core convolution pipeline (not for
+ * production use): the NEXT ws_conv_forward / network call that runs the
+ * tcgen05 kernel skips, in every CTA, the copy of its input triple number
+ * drop_triple (>= 1) together with its barrier arrival, and every pipeline wait
+ * gives up after 2^wait_log2 polls (8..24).  That call must then return
+ * IPM_ERR_CUDA ("a pipeline wait expired") without hanging, and the context
+ * stays usable.  IPM_ERR_ARG for out-of-range arguments. */
+ipm_status ws_test_conv_stall(int drop_triple, int wait_log2);
 /* Weight and bias gradients of such a convolution: dw[t][o][i] = sum_v dy[v][o]
  * x[v + off(t)][i] for o < mout (dy [V][m], m in {16, 32}), db[o] = sum_v dy[v][o]. */
 ipm_status ws_conv_wgrad(int cin, int m, int mout, int d0, int d1, int d2, const uint16_t* x, const uint16_t* dy,

@@ -87,6 +87,7 @@ _SIGNATURES = {
     "ws_predict": (ctypes.c_int, [_P, _P, ctypes.c_double]),
     "ws_train_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]),
     "ws_conv_forward": (ctypes.c_int, [ctypes.c_int] * 5 + [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
+    "ws_test_conv_stall": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "ws_conv_wgrad": (ctypes.c_int, [ctypes.c_int] * 6 + [_P, _P, _P, _P, _P]),
     "gapply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _P, _P, _P, _P]),
     "ipm_describe": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_int]),
@@ -320,6 +321,11 @@ def ws_train_step(n, h, beta_star, lr):
 def ws_conv_forward(cin, cout, dims, x, w, bias, relu, aux, y, stream=None):
     return _check(load().ws_conv_forward(cin, cout, *[int(d) for d in dims], addr(x), addr(w), addr(bias),
                                          int(relu), addr(aux), addr(y), stream), None)
+
+
+def ws_test_conv_stall(drop_triple, wait_log2):
+    """Failure-detection test hook: the next tensor-core convolution drops one copy."""
+    return _check(load().ws_test_conv_stall(int(drop_triple), int(wait_log2)), None)
 
 
 def ws_conv_wgrad(cin, m, mout, dims, x, dy, dw, db, stream=None):

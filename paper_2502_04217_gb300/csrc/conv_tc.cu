@@ -84,9 +84,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase of parity `parity` to complete; false after the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned i = 0; i < kWaitLimit; ++i) {
+// Wait for the phase of parity `parity` to complete; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned limit = kWaitLimit) {
+  for (unsigned i = 0; i < limit; ++i) {
     if (mbar_try(bar, parity)) return true;
     if (i >= 32) __nanosleep(128);
   }
@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   volatile int& s_abort = *reinterpret_cast<volatile int*>(bars + 2 * S + 6);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned wl = a.wait_log2 > 0 ? (1u << a.wait_log2) : kWaitLimit;
   // TMA destinations must be 128-byte aligned: refuse to run otherwise
   if (smem_u32(smem) & 127u) {
     if (threadIdx.x == 0) atomicCAS(&g_conv_tc_error, 0u, 6u);
@@ -296,8 +297,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         for (int j = 0; j < m.steps + 2 && !s_abort; ++j, ++q) {
           const int slot = (int)(q % S);
           const uint32_t use = (uint32_t)(q / S);
-          if (use > 0 && !mbar_wait(smem_u32(&empty_b[slot]), (use - 1) & 1)) { fail(1); break; }
+          if (use > 0 && !mbar_wait(smem_u32(&empty_b[slot]), (use - 1) & 1, wl)) { fail(1); break; }
           const uint32_t full = smem_u32(&full_b[slot]);
+          if ((long long)q + 1 == a.drop_triple) continue;   // failure-detection test: never arrives
           mbar_expect_tx(full, kTxBytes);
           for (int c = 0; c < KC; ++c)
             tma_load_4d(smem_u32(halo + c * kPlaneBytes + slot * kTripleBytes), &xmap, c * 8, m.z0 - 1,
@@ -306,7 +308,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       }
       // own copies in flight: the last (up to) S triples must have landed
       for (unsigned long long k = (q > S ? q - S : 0); k < q; ++k)
-        if (!mbar_wait(smem_u32(&full_b[k % S]), (uint32_t)((k / S) & 1))) { fail(2); break; }
+        if ((long long)k + 1 != a.drop_triple && !mbar_wait(smem_u32(&full_b[k % S]), (uint32_t)((k / S) & 1), wl)) {
+          fail(2);
+          break;
+        }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -322,11 +327,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
           bool ok = true;
           for (int b = 0; b < 3 && ok; ++b) {
             const unsigned long long k = q + s + b;
-            ok = mbar_wait(smem_u32(&full_b[k % S]), (uint32_t)((k / S) & 1));
+            ok = mbar_wait(smem_u32(&full_b[k % S]), (uint32_t)((k / S) & 1), wl);
           }
           const int buf = (int)(tile & 1);
           const uint32_t use = (uint32_t)(tile >> 1);
-          if (ok && use > 0) ok = mbar_wait(smem_u32(&acce_b[buf]), (use - 1) & 1);
+          if (ok && use > 0) ok = mbar_wait(smem_u32(&acce_b[buf]), (use - 1) & 1, wl);
           if (!ok) { fail(3); break; }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(buf * N);
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       }
       // every MMA issued by this thread has completed before TMEM is freed
       mma_commit(smem_u32(done_b));
-      if (!mbar_wait(smem_u32(done_b), 0)) fail(4);
+      if (!mbar_wait(smem_u32(done_b), 0, wl)) fail(4);
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       const Item m = item_of(it, a, ztiles, nseg);
       for (int s = 0; s < m.steps; ++s, ++tile) {
         const int buf = (int)(tile & 1);
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_b[buf]), (uint32_t)((tile >> 1) & 1)));
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_b[buf]), (uint32_t)((tile >> 1) & 1), wl));
         if (!ok) { fail(5); break; }
         tc_fence_after();
         float v[N];
@@ -452,8 +457,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+int g_inject_drop = 0, g_inject_wait = 0;   // failure-detection test, consumed by the next launch
+
 template <int CIN, int COUT>
-cudaError_t launch(const ConvTcArgs& a, cudaStream_t st) {
+cudaError_t launch(const ConvTcArgs& a_in, cudaStream_t st) {
+  ConvTcArgs a = a_in;
+  a.drop_triple = 0;
+  a.wait_log2 = 0;
+  if (g_inject_drop > 0) {
+    a.drop_triple = g_inject_drop;
+    a.wait_log2 = g_inject_wait;
+    g_inject_drop = 0;
+  }
   constexpr int N = COUT < 16 ? 16 : COUT;
   constexpr int S = Ring<CIN>::kSlots;
   constexpr size_t smem = (size_t)(CIN / 8) * Ring<CIN>::kPlaneBytes + (size_t)27 * (CIN / 8) * N * 16 +
@@ -494,6 +509,11 @@ cudaError_t conv_tc(int cin, int cout, const ConvTcArgs& a, cudaStream_t st) {
   if (cin == 16 && cout == 32) return launch<16, 32>(a, st);
   if (cin == 32 && cout == 8) return launch<32, 8>(a, st);
   return launch<16, 8>(a, st);
+}
+
+void conv_tc_inject_stall(int drop_triple, int wait_log2) {
+  g_inject_drop = drop_triple;
+  g_inject_wait = wait_log2;
 }
 
 cudaError_t conv_tc_take_error(unsigned* code, cudaStream_t st) {

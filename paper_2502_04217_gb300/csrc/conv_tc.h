@@ -16,6 +16,11 @@ struct ConvTcArgs {
   const __nv_bfloat16* aux;   // [V][cout] or nullptr: output *= (aux > 0)
   __nv_bfloat16* ybf;         // [V][cout] BF16 output (or nullptr)
   float* yf;                  // [V][cout] FP32 output (or nullptr)
+  // failure-detection test only (zero otherwise): the producer of every CTA skips
+  // the copy (and the barrier arrival) of its triple number drop_triple - 1, and
+  // every pipeline wait gives up after 2^wait_log2 polls instead of 2^24
+  int drop_triple;
+  int wait_log2;
 };
 
 // Shapes the tensor-core kernel takes: (cin, cout) in {16, 32} x {8, 32} and
@@ -29,5 +34,8 @@ cudaError_t conv_tc(int cin, int cout, const ConvTcArgs& a, cudaStream_t st);
 // After synchronising st: code of the first expired wait since the last call
 // (0: none), then reset.
 cudaError_t conv_tc_take_error(unsigned* code, cudaStream_t st);
+
+// Failure-detection test: make the NEXT launch drop one copy (see ConvTcArgs).
+void conv_tc_inject_stall(int drop_triple, int wait_log2);
 
 }  // namespace sdft

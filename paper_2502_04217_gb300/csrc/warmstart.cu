@@ -750,6 +750,12 @@ ipm_status ws_conv_forward(int cin, int cout, int d0, int d1, int d2, const uint
   return sync_check((cudaStream_t)stream);
 }
 
+ipm_status ws_test_conv_stall(int drop_triple, int wait_log2) {
+  if (drop_triple < 1 || wait_log2 < 8 || wait_log2 > 24) return ws_err("ws_test_conv_stall: bad argument", IPM_ERR_ARG);
+  conv_tc_inject_stall(drop_triple, wait_log2);
+  return IPM_OK;
+}
+
 ipm_status ws_conv_wgrad(int cin, int m, int mout, int d0, int d1, int d2, const uint16_t* x, const uint16_t* dy,
                          float* dw, float* db, void* stream) {
   if (!x || !dy || !dw || !db || mout < 1 || mout > m || d0 < 1 || d1 < 1 || d2 < 1)

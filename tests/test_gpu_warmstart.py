@@ -63,6 +63,30 @@ def test_conv_forward_matches_reference(cin, cout, dims):
         assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
 
 
+def test_conv_pipeline_wait_expires_with_an_error():
+    """Failure detection without a GPU fault: one TMA copy of the tcgen05 pipeline
+    never arrives (a barrier nothing completes); every pipeline wait is bounded,
+    so the call returns IPM_ERR_CUDA instead of hanging, and the next call on the
+    same context computes the right result."""
+    dims, cin, cout = (3, 40, 256), 32, 32
+    rng = np.random.default_rng(3)
+    x = bf16(rng.standard_normal(dims + (cin,)))
+    w = bf16(0.2 * rng.standard_normal((27, cout, cin)))
+    b = rng.standard_normal(cout).astype(np.float32)
+    args = (as_u16(x.cuda().contiguous()), as_u16(w.cuda().contiguous()), torch.as_tensor(b).cuda(), 1, None)
+    y = torch.empty(int(np.prod(dims)) * cout, dtype=torch.float32, device="cuda")
+    binding.ws_test_conv_stall(5, 14)
+    with pytest.raises(binding.IpmError) as e:
+        binding.ws_conv_forward(cin, cout, dims, *args, y)
+    assert e.value.status == binding.IPM_ERR_CUDA and "expired" in str(e.value)
+    binding.ws_conv_forward(cin, cout, dims, *args, y)
+    W = w.float().numpy().reshape(3, 3, 3, cout, cin).transpose(0, 1, 2, 4, 3)
+    ref = np.maximum(ows.conv3d(x.float().numpy().astype(np.float64), W.astype(np.float64), b.astype(np.float64)), 0)
+    assert np.abs(y.cpu().numpy().reshape(dims + (cout,)) - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    with pytest.raises(binding.IpmError):
+        binding.ws_test_conv_stall(0, 14)
+
+
 @pytest.mark.parametrize("cin,m,mout,dims", [(32, 32, 32, (3, 4, 70)), (16, 32, 32, (2, 3, 17)),
                                              (32, 16, 8, (3, 2, 65)), (16, 16, 16, (1, 1, 9))])
 def test_conv_weight_gradient_matches_reference(cin, m, mout, dims):
