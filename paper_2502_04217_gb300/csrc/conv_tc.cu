@@ -51,12 +51,12 @@ constexpr int kLineBytes = kLineRows * 16;  // one 8-channel chunk of one line
 constexpr int kTripleBytes = 3 * kLineBytes;
 constexpr int kSegment = 32;                // i1 steps per work item
 
-// Ring slots: a step uses three triples, the others are prefetched (the TMA
-// runs slots - 3 steps ahead of the MMAs).  Measured on the 32 -> 32 layer at
-// 129 x 256 x 256: 4 slots 1.41 ms, 6 slots 1.50 ms (the deeper ring shrinks L1).
+// Ring slots: a step (two output rows) uses four triples and frees two; the
+// others are prefetched.  CIN = 32: 6 slots (one step ahead), the most that fits
+// next to the weights and the epilogue stage.
 template <int CIN>
 struct Ring {
-  static constexpr int kSlots = CIN == 32 ? 4 : 8;
+  static constexpr int kSlots = CIN == 32 ? 6 : 8;
   static constexpr int kPlaneBytes = kSlots * kTripleBytes;
 };
 constexpr int kThreads = 192;
@@ -204,9 +204,9 @@ __device__ __forceinline__ void stage_rows(unsigned char* st, int lane, const ui
   }
 }
 
-// Work item -> (i0, z-tile, first i1, steps)
+// Work item -> (i0, z-tile, first i1, output rows, steps of two rows)
 struct Item {
-  int i0, z0, y0, steps;
+  int i0, z0, y0, rows, steps;
 };
 __device__ __forceinline__ Item item_of(long long it, const ConvTcArgs& a, int ztiles, int nseg) {
   Item r;
@@ -215,7 +215,8 @@ __device__ __forceinline__ Item item_of(long long it, const ConvTcArgs& a, int z
   r.z0 = (int)(col % ztiles) * kTileM;
   r.i0 = (int)(col / ztiles);
   r.y0 = seg * kSegment;
-  r.steps = min(kSegment, a.D1 - r.y0);
+  r.rows = min(kSegment, a.D1 - r.y0);
+  r.steps = (r.rows + 1) / 2;
   return r;
 }
 
@@ -227,8 +228,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   constexpr int kPlaneBytes = Ring<CIN>::kPlaneBytes;
   constexpr int HALO = KC * kPlaneBytes;
   constexpr int WBYTES = 27 * KC * N * 16;
-  constexpr uint32_t kTmemCols = 2 * N < 32 ? 32 : 2 * N;
-  constexpr uint32_t kIdesc = idesc_bf16(kTileM, N);
+  constexpr uint32_t kTmemCols = 4 * N;         // 2 buffers x 2 output rows x N (64 or 128)
+  constexpr uint32_t kIdesc1 = idesc_bf16(kTileM, N);       // one tap block
+  constexpr uint32_t kIdesc2 = idesc_bf16(kTileM, 2 * N);   // two tap blocks side by side
   constexpr uint32_t kTxBytes = KC * kTripleBytes;
 
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -257,9 +259,17 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
   const int nseg = (a.D1 + kSegment - 1) / kSegment;
   const long long nitems = (long long)a.D0 * ztiles * nseg;
 
-  // weights -> [27][KC][N][16 B], zero rows for o >= COUT
+  // weights -> [ta][tz][KC][tb][N][16 B] (the three taps along i1 adjacent, so
+  // that two of them form one N = 2N operand); zero rows for o >= COUT
   for (int idx = threadIdx.x; idx < 27 * KC * N; idx += blockDim.x) {
-    const int o = idx % N, tc = idx / N, c = tc % KC, t = tc / KC;
+    int r = idx / N;
+    const int o = idx - r * N;
+    const int tb = r % 3;
+    r /= 3;
+    const int c = r % KC;
+    r /= KC;
+    const int tz = r % 3, ta = r / 3;
+    const int t = ta * 9 + tb * 3 + tz;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
     if (o < COUT) v = *reinterpret_cast<const uint4*>(a.w + ((size_t)(t * COUT + o) * CIN + c * 8));
     *reinterpret_cast<uint4*>(wsm + (size_t)idx * 16) = v;
@@ -294,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       unsigned long long q = 0;   // triple sequence number
       for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
         const Item m = item_of(it, a, ztiles, nseg);
-        for (int j = 0; j < m.steps + 2 && !s_abort; ++j, ++q) {
+        for (int j = 0; j < 2 * m.steps + 2 && !s_abort; ++j, ++q) {
           const int slot = (int)(q % S);
           const uint32_t use = (uint32_t)(q / S);
           if (use > 0 && !mbar_wait(smem_u32(&empty_b[slot]), (use - 1) & 1, wl)) { fail(1); break; }
@@ -320,47 +330,53 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
       unsigned long long tile = 0;
       const uint32_t hb = smem_u32(halo);
       const uint64_t adesc0 = smem_desc(0, kPlaneBytes, 128);
-      const uint64_t bdesc0 = smem_desc(smem_u32(wsm), N * 16, 128);
+      const uint64_t bdesc0 = smem_desc(smem_u32(wsm), 3 * N * 16, 128);
       for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
         const Item m = item_of(it, a, ztiles, nseg);
         for (int s = 0; s < m.steps && !s_abort; ++s, ++tile) {
+          // output rows i1 = y0 + 2s (block 1 of the accumulator) and i1 + 1 (block 0)
+          // read the input lines i1 - 1 .. i1 + 2 = triples q + 2s + 0..3
+          const unsigned long long k0 = q + 2 * (unsigned long long)s;
           bool ok = true;
-          for (int b = 0; b < 3 && ok; ++b) {
-            const unsigned long long k = q + s + b;
-            ok = mbar_wait(smem_u32(&full_b[k % S]), (uint32_t)((k / S) & 1), wl);
-          }
+          for (int b = 0; b < 4 && ok; ++b)
+            ok = mbar_wait(smem_u32(&full_b[(k0 + b) % S]), (uint32_t)(((k0 + b) / S) & 1), wl);
           const int buf = (int)(tile & 1);
           const uint32_t use = (uint32_t)(tile >> 1);
           if (ok && use > 0) ok = mbar_wait(smem_u32(&acce_b[buf]), (use - 1) & 1, wl);
           if (!ok) { fail(3); break; }
           tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)(buf * N);
-          // descriptors: one base per triple slot; the taps and K steps add
-          // compile-time offsets to the 16-byte address field
-          uint64_t aslot[3];
+          const uint32_t d = tmem + (uint32_t)(buf * 2 * N);
+          uint64_t aslot[4];
 #pragma unroll
-          for (int tb = 0; tb < 3; ++tb) aslot[tb] = adesc0 + (uint64_t)((hb + (uint32_t)((q + s + tb) % S) * kTripleBytes) >> 4);
+          for (int b = 0; b < 4; ++b) aslot[b] = adesc0 + (uint64_t)((hb + (uint32_t)((k0 + b) % S) * kTripleBytes) >> 4);
+          // line i1 + dl (dl = -1..2) meets output row i1 + j through tap tb = dl - j + 1:
+          //   dl = 0: taps (0, 1) -> rows (i1+1, i1), N = 2N at column 0 (first: initialises both blocks)
+          //   dl = -1: tap 0 -> row i1 (column N); dl = 1: taps (1, 2) -> rows (i1+1, i1), N = 2N at
+          //   column 0; dl = 2: tap 2 -> row i1 + 1 (column 0)
 #pragma unroll
           for (int ta = 0; ta < 3; ++ta)          // offset along i0 (line within the triple)
 #pragma unroll
-            for (int tb = 0; tb < 3; ++tb)        // offset along i1 (which triple)
+            for (int tz = 0; tz < 3; ++tz)        // offset along D2 (row shift)
 #pragma unroll
-              for (int tz = 0; tz < 3; ++tz)      // offset along D2 (row shift)
-#pragma unroll
-                for (int kc = 0; kc < CIN / 16; ++kc) {
-                  const int t = ta * 9 + tb * 3 + tz;
-                  const uint64_t ad = aslot[tb] + (uint64_t)((ta * kLineBytes + tz * 16 + kc * 2 * kPlaneBytes) >> 4);
-                  const uint64_t bd = bdesc0 + (uint64_t)(((t * KC + kc * 2) * N * 16) >> 4);
-                  mma_bf16(d, ad, bd, kIdesc, (t > 0 || kc > 0) ? 1u : 0u);
-                }
-          mma_commit(smem_u32(&accf_b[buf]));               // accumulator ready
-          mma_commit(smem_u32(&empty_b[(q + s) % S]));       // triple i1 - 1 no longer needed
+              for (int kc = 0; kc < CIN / 16; ++kc) {
+                const uint32_t aoff = (uint32_t)((ta * kLineBytes + tz * 16 + kc * 2 * kPlaneBytes) >> 4);
+                const uint32_t boff = (uint32_t)(((((ta * 3 + tz) * KC + kc * 2) * 3) * N * 16) >> 4);
+                constexpr uint32_t tbs = (uint32_t)((N * 16) >> 4);   // one tap block of B
+                const uint32_t first = (ta == 0 && tz == 0 && kc == 0) ? 0u : 1u;
+                mma_bf16(d, aslot[1] + aoff, bdesc0 + boff, kIdesc2, first);
+                mma_bf16(d + N, aslot[0] + aoff, bdesc0 + boff, kIdesc1, 1u);
+                mma_bf16(d, aslot[2] + aoff, bdesc0 + boff + tbs, kIdesc2, 1u);
+                mma_bf16(d, aslot[3] + aoff, bdesc0 + boff + 2 * tbs, kIdesc1, 1u);
+              }
+          mma_commit(smem_u32(&accf_b[buf]));               // accumulators of both rows ready
+          mma_commit(smem_u32(&empty_b[k0 % S]));           // lines i1 - 1 and i1 no longer needed
+          mma_commit(smem_u32(&empty_b[(k0 + 1) % S]));
           if (s == m.steps - 1) {
-            mma_commit(smem_u32(&empty_b[(q + s + 1) % S]));
-            mma_commit(smem_u32(&empty_b[(q + s + 2) % S]));
+            mma_commit(smem_u32(&empty_b[(k0 + 2) % S]));
+            mma_commit(smem_u32(&empty_b[(k0 + 3) % S]));
           }
         }
-        q += m.steps + 2;
+        q += 2 * (unsigned long long)m.steps + 2;
       }
       // every MMA issued by this thread has completed before TMEM is freed
       mma_commit(smem_u32(done_b));
@@ -373,6 +389,57 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     float bias[N];
 #pragma unroll
     for (int o = 0; o < N; ++o) bias[o] = (a.bias && o < COUT) ? a.bias[o] : 0.f;
+    // bias, ReLU, ReLU mask of the data gradient, and the staged store of one
+    // output row (i0, yrow, z0 .. z0 + 127) held as v (this lane's voxel)
+    auto emit_row = [&](float (&v)[N], const Item& m, int yrow) {
+      const int z = m.z0 + row;
+      const size_t line = ((size_t)m.i0 * a.D1 + yrow) * a.D2;
+#pragma unroll
+      for (int o = 0; o < COUT; ++o) {
+        float y = v[o] + bias[o];
+        if (a.relu) y = fmaxf(y, 0.f);
+        v[o] = y;
+      }
+      if (z < a.D2) {
+        const size_t vox = line + z;
+        if (a.aux) {
+          const uint4* ax = reinterpret_cast<const uint4*>(a.aux + vox * COUT);
+#pragma unroll
+          for (int c = 0; c < COUT / 8; ++c) {
+            const uint4 u = ax[c];
+            const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[k] & 0xFFFFu))) > 0.f)) v[c * 8 + 2 * k] = 0.f;
+              if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[k] >> 16))) > 0.f)) v[c * 8 + 2 * k + 1] = 0.f;
+            }
+          }
+        }
+      }
+      // the warp's 32 rows are consecutive voxels: stage them in shared memory and
+      // write contiguous 512-byte spans (the rows past D2 are not written)
+      const int zw = m.z0 + quarter * 32;
+      const int nvalid = min(32, a.D2 - zw);
+      if (nvalid > 0) {
+        unsigned char* st = stage + quarter * (32 * COUT * 4);
+        if (a.ybf) {
+          uint4 ch[COUT / 8];
+#pragma unroll
+          for (int c = 0; c < COUT / 8; ++c)
+            ch[c] = make_uint4(pack_bf16(v[c * 8], v[c * 8 + 1]), pack_bf16(v[c * 8 + 2], v[c * 8 + 3]),
+                               pack_bf16(v[c * 8 + 4], v[c * 8 + 5]), pack_bf16(v[c * 8 + 6], v[c * 8 + 7]));
+          stage_rows<COUT * 2>(st, lane, ch, reinterpret_cast<unsigned char*>(a.ybf + (line + zw) * COUT), nvalid);
+        }
+        if (a.yf) {
+          uint4 ch[COUT / 4];
+#pragma unroll
+          for (int c = 0; c < COUT / 4; ++c)
+            ch[c] = make_uint4(__float_as_uint(v[c * 4]), __float_as_uint(v[c * 4 + 1]), __float_as_uint(v[c * 4 + 2]),
+                               __float_as_uint(v[c * 4 + 3]));
+          stage_rows<COUT * 4>(st, lane, ch, reinterpret_cast<unsigned char*>(a.yf + (line + zw) * COUT), nvalid);
+        }
+      }
+    };
     unsigned long long tile = 0;
     for (long long it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
       const Item m = item_of(it, a, ztiles, nseg);
@@ -381,57 +448,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
         const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_b[buf]), (uint32_t)((tile >> 1) & 1), wl));
         if (!ok) { fail(5); break; }
         tc_fence_after();
-        float v[N];
-        tmem_load<N>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * N), v);
+        float v0[N], v1[N];
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 2 * N);
+        tmem_load<N>(ta + N, v0);       // row i1 = y0 + 2s (block 1)
+        tmem_load<N>(ta, v1);           // row i1 + 1 (block 0)
         tc_fence_before();
         mbar_arrive(smem_u32(&acce_b[buf]));
-        const int z = m.z0 + row;
-        const size_t line = ((size_t)m.i0 * a.D1 + (m.y0 + s)) * a.D2;
-#pragma unroll
-        for (int o = 0; o < COUT; ++o) {
-          float y = v[o] + bias[o];
-          if (a.relu) y = fmaxf(y, 0.f);
-          v[o] = y;
-        }
-        if (z < a.D2) {
-          const size_t vox = line + z;
-          if (a.aux) {
-            const uint4* ax = reinterpret_cast<const uint4*>(a.aux + vox * COUT);
-#pragma unroll
-            for (int c = 0; c < COUT / 8; ++c) {
-              const uint4 u = ax[c];
-              const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[k] & 0xFFFFu))) > 0.f)) v[c * 8 + 2 * k] = 0.f;
-                if (!(__bfloat162float(__ushort_as_bfloat16((unsigned short)(wv[k] >> 16))) > 0.f)) v[c * 8 + 2 * k + 1] = 0.f;
-              }
-            }
-          }
-        }
-        // the warp's 32 rows are consecutive voxels: stage them in shared memory and
-        // write contiguous 512-byte spans (the rows past D2 are not written)
-        const int zw = m.z0 + quarter * 32;
-        const int nvalid = min(32, a.D2 - zw);
-        if (nvalid > 0) {
-          unsigned char* st = stage + quarter * (32 * COUT * 4);
-          if (a.ybf) {
-            uint4 ch[COUT / 8];
-#pragma unroll
-            for (int c = 0; c < COUT / 8; ++c)
-              ch[c] = make_uint4(pack_bf16(v[c * 8], v[c * 8 + 1]), pack_bf16(v[c * 8 + 2], v[c * 8 + 3]),
-                                 pack_bf16(v[c * 8 + 4], v[c * 8 + 5]), pack_bf16(v[c * 8 + 6], v[c * 8 + 7]));
-            stage_rows<COUT * 2>(st, lane, ch, reinterpret_cast<unsigned char*>(a.ybf + (line + zw) * COUT), nvalid);
-          }
-          if (a.yf) {
-            uint4 ch[COUT / 4];
-#pragma unroll
-            for (int c = 0; c < COUT / 4; ++c)
-              ch[c] = make_uint4(__float_as_uint(v[c * 4]), __float_as_uint(v[c * 4 + 1]), __float_as_uint(v[c * 4 + 2]),
-                                 __float_as_uint(v[c * 4 + 3]));
-            stage_rows<COUT * 4>(st, lane, ch, reinterpret_cast<unsigned char*>(a.yf + (line + zw) * COUT), nvalid);
-          }
-        }
+        emit_row(v0, m, m.y0 + 2 * s);
+        if (2 * s + 1 < m.rows) emit_row(v1, m, m.y0 + 2 * s + 1);
       }
     }
   }
