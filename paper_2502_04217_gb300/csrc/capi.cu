@@ -306,9 +306,24 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
       a.out_scale = 1.0;
       a.sc = h->d_sc;
       const bool inv = (kind != 2);
-      CK(launch_pass(kind, inv, fp32, E, a, t.threads, t.smem, t.grid, h->st));     // warm-up
+      // row passes are the first and the last pass of a product: time an inverse
+      // one reading the beta layout and a forward one writing it, as in a product
+      // with G; the other passes work on the buffer alone
+      PassArgs a_first = a, a_last = a;
+      if (kind == 0) {
+        a_first.mapin = MAPIN_BETA;
+        a_first.src = h->w.beta;
+        a_last.mapout = MAPOUT_BETA;
+        a_last.dst = h->d_tmp;
+      }
+      auto once = [&]() -> cudaError_t {
+        cudaError_t e = launch_pass(kind, inv, fp32, E, a_first, t.threads, t.smem, t.grid, h->st);
+        if (e == cudaSuccess && kind == 0) e = launch_pass(kind, false, fp32, E, a_last, t.threads, t.smem, t.grid, h->st);
+        return e;
+      };
+      CK(once());     // warm-up
       CK(cudaEventRecord(e0, h->st));
-      for (int r = 0; r < 5; ++r) CK(launch_pass(kind, inv, fp32, E, a, t.threads, t.smem, t.grid, h->st));
+      for (int r = 0; r < 5; ++r) CK(once());
       CK(cudaEventRecord(e1, h->st));
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
