@@ -97,6 +97,13 @@ typedef struct {
                            PCG residual is replaced by rhs - K x computed with FP64 products
                            and PCG restarts from x; it stops only when that FP64 residual
                            passes the test (bounded by max_cg)                                */
+  int tile_engine;      /* FFT pass engine.  0 (default): with autotune, the faster of the two
+                           per pass shape, else the shared-memory one; 1: the shared-memory
+                           Stockham engine (every stage through shared memory); 2: the
+                           register engine (16 values per thread, first and last stage in
+                           registers straight from / to global memory) wherever the length
+                           allows it (32, 64, 128, 256 or 512; the middle pass uses Nl/2),
+                           else the shared-memory one.  tile_e is ignored by engine 2.       */
 } ipm_options;
 
 typedef struct {

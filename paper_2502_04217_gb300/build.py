@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsdft_ipm.so")
-SOURCES = ["fft_passes.cu", "fft_passes_f32.cu", "fft_passes_f64.cu", "ipm_kernels.cu", "capi.cu", "noalloc.cu",
+SOURCES = ["fft_passes.cu", "fft_passes_f32.cu", "fft_passes_f64.cu", "fft_reg_f32.cu", "fft_reg_f64.cu", "ipm_kernels.cu", "capi.cu", "noalloc.cu",
            "warmstart.cu", "conv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -33,6 +33,7 @@ struct PassCfg {
   long long npencils = 0;
   const void* tw = nullptr;
   const void* twN = nullptr;
+  int reg = 0;              // 1: register engine (fft_reg.cuh)
 };
 
 struct PassSet {
@@ -214,6 +215,30 @@ bool make_cfg(PassCfg& c, int L, int rows, long long npen, bool fp32, int E, int
   if (c.threads < 64) c.threads = 64;
   c.smem = (size_t)rows * PP * esz;
   c.npencils = npen;
+  c.reg = 0;
+  return true;
+}
+
+// Tile of the register engine: E = 16 values per thread, L / 16 threads per
+// pencil, P pencils per block (a power of two; the block a multiple of 32 threads,
+// at most 256, the kernels' launch bound).  Shared memory: row passes P padded rows (L + L/16 values), column
+// passes L x P, middle passes (2 h + 1) x P (half spectrum and exchange buffer).
+bool make_cfg_reg(PassCfg& c, int kind, int L, long long npen, bool fp32, int P) {
+  if (L != 32 && L != 64 && L != 128 && L != 256 && L != 512) return false;
+  const int esz = fp32 ? 8 : 16, threads = P * (L / 16);
+  if (threads % 32 != 0 || threads > 256) return false;
+  const size_t rows = kind == 0 ? (size_t)(L + L / 16) : kind == 1 ? (size_t)L : (size_t)(2 * L + 1);
+  const size_t smem = rows * P * esz;
+  if (smem > 200 * 1024) return false;
+  c.E = 16;
+  c.plan = make_plan(L, 16);
+  c.lgP = ilog2(P);
+  c.PP = P;
+  c.nwork = threads;
+  c.threads = threads;
+  c.smem = smem;
+  c.npencils = npen;
+  c.reg = 1;
   return true;
 }
 
@@ -240,7 +265,9 @@ dim3 pass_grid(const Layout& L, int kind, long long npen, int lgP) {
 struct TuneKey {
   int kind, L, rows, fp32;
   long long npen;
+  int engine;
   bool operator<(const TuneKey& o) const {
+    if (engine != o.engine) return engine < o.engine;
     if (kind != o.kind) return kind < o.kind;
     if (L != o.L) return L < o.L;
     if (rows != o.rows) return rows < o.rows;
@@ -249,12 +276,35 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tuned;       // -> (E, P)
+struct TuneVal {
+  int E, P, reg;
+};
+std::map<TuneKey, TuneVal> g_tuned;
 
-ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long long npen, bool fp32) {
+// `last`: for a row pass, tune the forward (last) pass of a product instead of the
+// inverse (first) one.  Row passes are timed in the form the PCG loop runs them
+// (first: p = z + beta p and the beta map; last: the K epilogue), on operands
+// filled with a non-zero pattern by the caller; column and middle passes on the
+// work buffer alone.
+ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long long npen, bool fp32,
+                     bool last = false) {
   c.kind = kind;
   plan_tile(c, L, rows, npen, fp32);
   c.grid = pass_grid(h->lay, kind, npen, c.lgP);
+  if (h->opt.tile_engine == 2) {
+    // forced register engine: the given P (else the smallest launchable one
+    // with at least 2 blocks per SM), where the length allows
+    for (int P = (h->opt.tile_p > 0 ? h->opt.tile_p : 1); P <= 32; P *= 2) {
+      PassCfg t = c;
+      if (make_cfg_reg(t, kind, L, npen, fp32, P)) {
+        c = t;
+        c.grid = pass_grid(h->lay, kind, npen, c.lgP);
+        break;
+      }
+      if (h->opt.tile_p > 0) break;
+    }
+    return IPM_OK;
+  }
   if (h->opt.tile_e > 0 || h->opt.tile_p > 0) {
     // forced shape (tests and experiments): keep the default for what is not forced
     const int E = h->opt.tile_e > 0 ? h->opt.tile_e : c.E;
@@ -268,12 +318,13 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
     return IPM_OK;
   }
   if (!h->opt.autotune) return IPM_OK;
-  const TuneKey key{kind, L, rows, fp32 ? 1 : 0, npen};
+  const TuneKey key{kind + (last ? 3 : 0), L, rows, fp32 ? 1 : 0, npen, h->opt.tile_engine};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      make_cfg(c, L, rows, npen, fp32, it->second.first, it->second.second);
+      if (it->second.reg) make_cfg_reg(c, kind, L, npen, fp32, it->second.P);
+      else make_cfg(c, L, rows, npen, fp32, it->second.E, it->second.P);
       c.grid = pass_grid(h->lay, kind, npen, c.lgP);
       return IPM_OK;
     }
@@ -285,11 +336,19 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   PassCfg best_c = c;
-  for (int E : Es) {
-    if (E == 0) continue;
-    for (int P = 1; P <= 32; P *= 2) {
+  // candidates: the shared-memory engine at every (E, P), the register engine at every P
+  std::vector<std::pair<int, int>> cands;     // (E, P); E = 0 marks the register engine
+  if (h->opt.tile_engine != 2)
+    for (int E : Es)
+      if (E != 0)
+        for (int P = 1; P <= 32; P *= 2) cands.push_back({E, P});
+  if (h->opt.tile_engine != 1)
+    for (int P = 1; P <= 32; P *= 2) cands.push_back({0, P});
+  for (const auto& cand : cands) {
+    const int E = cand.first, P = cand.second;
+    {
       PassCfg t = c;
-      if (!make_cfg(t, L, rows, npen, fp32, E, P)) continue;
+      if (E == 0 ? !make_cfg_reg(t, kind, L, npen, fp32, P) : !make_cfg(t, L, rows, npen, fp32, E, P)) continue;
       t.grid = pass_grid(h->lay, kind, npen, t.lgP);
       PassArgs a{};
       a.lay = h->lay;
@@ -305,22 +364,20 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
       a.inv_n = 1.0 / (double)h->lay.n;
       a.out_scale = 1.0;
       a.sc = h->d_sc;
-      const bool inv = (kind != 2);
-      // row passes are the first and the last pass of a product: time an inverse
-      // one reading the beta layout and a forward one writing it, as in a product
-      // with G; the other passes work on the buffer alone
-      PassArgs a_first = a, a_last = a;
-      if (kind == 0) {
-        a_first.mapin = MAPIN_BETA;
-        a_first.src = h->w.beta;
-        a_last.mapout = MAPOUT_BETA;
-        a_last.dst = h->d_tmp;
+      a.reg = t.reg;
+      const bool inv = (kind == 0 && last) ? false : (kind != 2);
+      if (kind == 0 && !last) {
+        a.mapin = MAPIN_PCG;
+        a.p = h->w.p;
+        a.zv = h->w.zv;
+      } else if (kind == 0) {
+        a.mapout = MAPOUT_K;
+        a.p = h->w.p;
+        a.q = h->w.q;
+        a.lam1 = h->w.lam1;
+        a.lam2 = h->w.lam2;
       }
-      auto once = [&]() -> cudaError_t {
-        cudaError_t e = launch_pass(kind, inv, fp32, E, a_first, t.threads, t.smem, t.grid, h->st);
-        if (e == cudaSuccess && kind == 0) e = launch_pass(kind, false, fp32, E, a_last, t.threads, t.smem, t.grid, h->st);
-        return e;
-      };
+      auto once = [&]() -> cudaError_t { return launch_pass(kind, inv, fp32, t.E, a, t.threads, t.smem, t.grid, h->st); };
       CK(once());     // warm-up
       CK(cudaEventRecord(e0, h->st));
       for (int r = 0; r < 5; ++r) CK(once());
@@ -335,7 +392,7 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
   cudaEventDestroy(e1);
   c = best_c;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[key] = {c.E, 1 << c.lgP};
+  g_tuned[key] = {c.E, 1 << c.lgP, c.reg};
   return IPM_OK;
 }
 
@@ -359,9 +416,11 @@ ipm_status plan_passes(sdft_ipm* h, PassSet& ps, bool fp32) {
     PassCfg c;
     if ((s = make_tables(h, Lr, &t64, &t32)) != IPM_OK) return s;
     c.tw = fp32 ? t32 : t64;
+    PassCfg f = c;
     if ((s = tune_tile(h, c, 0, Lr, Lr, nrows, fp32)) != IPM_OK) return s;
+    if ((s = tune_tile(h, f, 0, Lr, Lr, nrows, fp32, true)) != IPM_OK) return s;
     ps.row_inv = c;
-    ps.row_fwd = c;
+    ps.row_fwd = f;
   }
   if (L.d == 3) {
     // column tiles cover P consecutive k1 of one plane
@@ -392,6 +451,7 @@ PassArgs base_args(sdft_ipm* h, const PassCfg& c) {
   a.counter = h->d_counter;
   a.sc = h->d_sc;
   a.out_scale = 1.0;
+  a.reg = c.reg;
   return a;
 }
 
@@ -541,6 +601,7 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (!(o.gap_tol > 0) || !(o.cg_tol > 0)) return fail_arg(h, "gap_tol and cg_tol must be positive");
   if (o.max_ipm < 0 || o.max_cg < 1 || o.cg_chunk < 1) return fail_arg(h, "iteration caps must be positive");
   if (o.refine_every < 0) return fail_arg(h, "refine_every must be >= 0");
+  if (o.tile_engine < 0 || o.tile_engine > 2) return fail_arg(h, "tile_engine must be 0, 1 or 2");
   if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
   if (!(o.tau > 0 && o.tau < 1)) return fail_arg(h, "tau must lie in (0,1)");
   return IPM_OK;
@@ -568,6 +629,7 @@ void ipm_default_options(ipm_options* o) {
   o->tile_e = 0;
   o->tile_p = 0;
   o->refine_every = 0;
+  o->tile_engine = 0;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -588,16 +650,9 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   if (check_options(h, o) != IPM_OK) { g_create_error = h->err; delete h; return IPM_ERR_ARG; }
   cudaGetDevice(&h->device);
   h->st = (cudaStream_t)stream;
-  Layout& L = h->lay;
-  L.d = ndim;
   for (int i = 0; i < ndim; ++i) h->dims[i] = (int)dims[i];
-  L.Nl = (int)dims[ndim - 1];
-  L.N0 = ndim >= 2 ? (int)dims[0] : 1;
-  L.N1 = ndim == 3 ? (int)dims[1] : 1;
-  L.M = L.N0 * L.N1;
-  L.Hl = L.Nl / 2 + 1;
-  L.H = (long long)L.Hl * L.M;
-  L.n = (long long)L.Nl * L.M;
+  h->lay = layout_init(ndim, ndim >= 2 ? (int)dims[0] : 1, ndim == 3 ? (int)dims[1] : 1, (int)dims[ndim - 1]);
+  Layout& L = h->lay;
   auto cleanup_fail = [&](ipm_status s) {
     g_create_error = h->err;
     ipm_destroy(h);
@@ -631,6 +686,10 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   }
   for (cudaStream_t& c : h->cap) CKC(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
   ipm_status s;
+  // the tuner times row passes on p, z, Lambda1, Lambda2: give them normal,
+  // non-zero values (every byte 0x3F) until the vectors are cleared below
+  for (double* p : {h->w.p, h->w.zv, h->w.lam1, h->w.lam2})
+    CKC(cudaMemsetAsync(p, 0x3F, (p == h->w.lam1 || p == h->w.lam2) ? v2 : v4, h->st));
   if ((s = plan_passes(h, h->pass64, false)) != IPM_OK) return cleanup_fail(s);
   if ((s = plan_passes(h, h->pass32, true)) != IPM_OK) return cleanup_fail(s);
   // partials: 4 values per elementwise block, 1 per FFT block
@@ -1060,7 +1119,8 @@ int ipm_describe(const sdft_ipm* h, char* buf, int len) {
   auto one = [&](const char* name, const PassCfg& c) {
     char tmp[256];
     snprintf(tmp, sizeof(tmp), "\"%s\": {\"L\": %d, \"E\": %d, \"P\": %d, \"threads\": %d, \"blocks\": %u, "
-             "\"smem\": %zu}", name, c.plan.L, c.E, 1 << c.lgP, c.threads, c.grid.x * c.grid.y, c.smem);
+             "\"smem\": %zu, \"engine\": \"%s\"}", name, c.plan.L, c.E, 1 << c.lgP, c.threads, c.grid.x * c.grid.y,
+             c.smem, c.reg ? "register" : "shared");
     if (out.size() > 1) out += ", ";
     out += tmp;
   };
@@ -1069,6 +1129,7 @@ int ipm_describe(const sdft_ipm* h, char* buf, int len) {
     const std::string pre = t ? "fp32_" : "fp64_";
     one((pre + "middle").c_str(), ps.mid);
     if (h->lay.d >= 2) one((pre + "row").c_str(), ps.row_fwd);
+    if (h->lay.d >= 2) one((pre + "row_first").c_str(), ps.row_inv);
     if (h->lay.d == 3) one((pre + "col").c_str(), ps.col_fwd);
   }
   out += "}";

@@ -11,37 +11,37 @@ namespace sdft {
 // ---------------------------------------------------------------------------
 // Complex helpers (double2 / float2 as interleaved re, im)
 // ---------------------------------------------------------------------------
-// Exact double <-> float conversions in integer arithmetic.  On this GPU a
-// conversion with a 64-bit operand runs on the FP64 pipe (1/64 of FP32), where it
-// costs as much as an FP64 FMA; the FP32 pass kernels convert every element of
-// their FP64 vectors, so these take the integer pipe instead.  Normal numbers
-// only (round to nearest even for d2f, with the carry into the exponent and
-// overflow to infinity done by the addition); zeros, subnormals, infinities and
-// NaN take the hardware conversion.
+// double <-> float conversions in integer arithmetic, without branches.  On this
+// GPU a conversion with a 64-bit operand runs on the FP64 pipe (1/64 of FP32),
+// where it costs as much as an FP64 FMA; the FP32 pass kernels convert every
+// element of their FP64 vectors, so these take the integer pipe instead.
+// Normal numbers convert exactly as the hardware does (round to nearest even for
+// d2f, the carry into the exponent and the overflow to infinity done by the
+// addition); zeros and infinities keep their sign, NaN stays NaN, and values in
+// the subnormal range of the narrower side are flushed to a signed zero (below
+// 1.2e-38, far under the FP32 rounding of every product they enter).
 __device__ __forceinline__ float d2f_int(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(b >> 32);
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e >= 1 && e <= 254) {
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    const unsigned r = (unsigned)(m >> 29);               // leading 23 mantissa bits
-    const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);   // the 29 bits dropped
-    unsigned f = ((unsigned)e << 23) | r;
-    f += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
-    return __uint_as_float(f | (hi & 0x80000000u));
-  }
-  return (float)x;
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  const int e = (int)ex - 1023 + 127;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const unsigned r = (unsigned)(m >> 29);               // leading 23 mantissa bits
+  const unsigned rem = (unsigned)(m & 0x1FFFFFFFull);   // the 29 bits dropped
+  unsigned f = ((unsigned)e << 23) | r;
+  f += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  const unsigned special = (ex == 0x7ffu && m != 0ull) ? 0x7fc00000u : 0x7f800000u;   // NaN : overflow / inf
+  f = (e < 1) ? 0u : (e > 254 ? special : f);
+  return __uint_as_float(f | (hi & 0x80000000u));
 }
 __device__ __forceinline__ double f2d_int(float x) {
   const unsigned u = __float_as_uint(x);
   const unsigned e = (u >> 23) & 0xffu;
-  if (e != 0u && e != 255u) {
-    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e + (1023u - 127u)) << 52) |
-                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)b);
-  }
-  return (double)x;
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long mant = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  const unsigned long long nrm = s | ((unsigned long long)(e + (1023u - 127u)) << 52) | mant;
+  const unsigned long long b = (e == 0u) ? s : (e == 255u ? (s | 0x7FF0000000000000ull | mant) : nrm);
+  return __longlong_as_double((long long)b);
 }
 template <typename T> __device__ __forceinline__ T from_double(double x);
 template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
@@ -85,6 +85,36 @@ template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) 
 // ---------------------------------------------------------------------------
 enum SlotClass { INTERIOR = 0, EDGE_REP = 1, EDGE_SC = 2, EDGE_TWIN = 3 };
 
+// Unsigned 32-bit division by a divisor fixed at set-up, as a multiply-high, an
+// add and two shifts (integer pipe only; a run-time division needs conversions
+// that this GPU runs on its narrow FP64 pipe).  With l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, floor(n / d) = (t + ((n - t) >> 1)) >> (l - 1)
+// for every 32-bit n, where t = floor(m n / 2^32) (the shifts become 0 and 0 for
+// d = 1 and 1 and 0 for d = 2).
+struct FastDiv {
+  unsigned m;
+  int s1, s2;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < (unsigned long long)d) ++l;
+  FastDiv f;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__host__ __device__ __forceinline__ unsigned fast_div(unsigned n, FastDiv f) {
+#ifdef __CUDA_ARCH__
+  const unsigned t = __umulhi(f.m, n);
+#else
+  const unsigned t = (unsigned)(((unsigned long long)f.m * n) >> 32);
+#endif
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct Layout {
   int d;          // 1, 2 or 3
   int N0, N1;     // in-plane lengths (d=3: N0 x N1; d=2: N0, N1 = 1; d=1: 1, 1)
@@ -93,18 +123,35 @@ struct Layout {
   int M;          // in-plane count
   long long H;    // number of complex slots = Hl * M
   long long n;    // number of grid points = Nl * M
+  FastDiv divM, divN1;   // division by M and by N1 (set by layout_init)
 };
+
+// Fill a layout from the grid extents (d = 1: {Nl}; d = 2: {N0, Nl}; d = 3: {N0, N1, Nl}).
+inline Layout layout_init(int d, int N0, int N1, int Nl) {
+  Layout L{};
+  L.d = d;
+  L.N0 = N0;
+  L.N1 = N1;
+  L.Nl = Nl;
+  L.M = N0 * N1;
+  L.Hl = Nl / 2 + 1;
+  L.H = (long long)L.Hl * L.M;
+  L.n = (long long)Nl * L.M;
+  L.divM = make_fastdiv((unsigned)L.M);
+  L.divN1 = make_fastdiv((unsigned)N1);
+  return L;
+}
 
 __host__ __device__ __forceinline__ int slot_class(const Layout& L, long long s) {
   // H < 2^31 for every supported grid, so 32-bit division suffices
-  const unsigned su = (unsigned)s, Mu = (unsigned)L.M;
-  const int kl = (int)(su / Mu);
+  const unsigned su = (unsigned)s;
+  const int kl = (int)fast_div(su, L.divM);
   if (kl >= 1 && kl <= L.Nl / 2 - 1) return INTERIOR;
-  const int kp = (int)(su - (unsigned)kl * Mu);
+  const int kp = (int)(su - (unsigned)kl * (unsigned)L.M);
   if (L.d == 1) return EDGE_SC;
   int k0, k1;
   if (L.d == 2) { k0 = kp; k1 = 0; }
-  else { k0 = kp / L.N1; k1 = kp - k0 * L.N1; }
+  else { k0 = (int)fast_div((unsigned)kp, L.divN1); k1 = kp - k0 * L.N1; }
   if (k0 == 0 || 2 * k0 == L.N0) {
     if (L.d == 2) return EDGE_SC;
     if (k1 == 0 || 2 * k1 == L.N1) return EDGE_SC;

@@ -22,6 +22,7 @@
 
 #include <type_traits>
 
+#include "fft_reg.cuh"
 #include "internal.h"
 
 namespace sdft {
@@ -51,9 +52,10 @@ __device__ __forceinline__ void map_out(int cls, V w, double scale, double& o0, 
   o1 = to_double(w.y * s);
 }
 
-// Load the complex value of slot g for the first pass.  The FP64 vectors stream
-// through with the evict-first hint (ld/st .cs) so that the pass-to-pass work
-// buffer (67.6 MB in FP32 at 256^3) keeps its place in L2.
+// Load the complex value of slot g for the first pass (one slot at a time).
+// The FP64 vectors stream through with the evict-first hint (ld/st .cs) so
+// that the pass-to-pass work buffer (67.6 MB in FP32 at 256^3) keeps its place
+// in L2.
 template <typename V>
 __device__ __forceinline__ V load_slot(const PassArgs& a, long long g) {
   if (a.mapin == MAPIN_NONE) return reinterpret_cast<const V*>(a.buf)[g];
@@ -62,54 +64,150 @@ __device__ __forceinline__ V load_slot(const PassArgs& a, long long g) {
     const double2 b = __ldcs(reinterpret_cast<const double2*>(a.src) + g);
     return map_in<V>(cls, b.x, b.y);
   }
-  if (a.mapin == MAPIN_PCG) {
-    // fused PCG direction update p = z + beta_cg * p on both blocks of the slot
-    const long long H2 = a.lay.H;    // offset of the z block, in double2 units
-    const double bc = a.sc->beta_cg;
-    double2* p2 = reinterpret_cast<double2*>(a.p);
-    const double2* z2 = reinterpret_cast<const double2*>(a.zv);
-    double2 pb = __ldcs(p2 + g), pz = __ldcs(p2 + H2 + g);
-    const double2 zb = __ldcs(z2 + g), zz = __ldcs(z2 + H2 + g);
-    pb.x = zb.x + bc * pb.x; pb.y = zb.y + bc * pb.y;
-    pz.x = zz.x + bc * pz.x; pz.y = zz.y + bc * pz.y;
-    __stcs(p2 + g, pb);
-    __stcs(p2 + H2 + g, pz);
-    return map_in<V>(cls, pb.x, pb.y);
-  }
-  return reinterpret_cast<const V*>(a.buf)[g];
+  // MAPIN_PCG: fused PCG direction update p = z + beta_cg * p on both blocks of the slot
+  const long long H2 = a.lay.H;
+  const double bc = a.sc->beta_cg;
+  double2* p2 = reinterpret_cast<double2*>(a.p);
+  const double2* z2 = reinterpret_cast<const double2*>(a.zv);
+  double2 pb = __ldcs(p2 + g), pz = __ldcs(p2 + H2 + g);
+  const double2 zb = __ldcs(z2 + g), zz = __ldcs(z2 + H2 + g);
+  pb.x = zb.x + bc * pb.x; pb.y = zb.y + bc * pb.y;
+  pz.x = zz.x + bc * pz.x; pz.y = zz.y + bc * pz.y;
+  __stcs(p2 + g, pb);
+  __stcs(p2 + H2 + g, pz);
+  return map_in<V>(cls, pb.x, pb.y);
 }
 
-// Store the complex value of slot g for the last pass; inside PCG also adds this
-// slot's share of p^T q to acc (FP64 work only where it is needed).
+// FP64 operands of the K epilogue for one slot: p on both blocks and the two
+// diagonal coefficients of K.
+struct KIn {
+  double2 pb, pz, l1, l2;
+};
+
+__device__ __forceinline__ KIn k_load(const PassArgs& a, long long g) {
+  const long long H2 = a.lay.H;    // offset of the z block, in double2 units
+  const double2* p2 = reinterpret_cast<const double2*>(a.p);
+  KIn k;
+  k.pb = __ldcs(p2 + g);
+  k.pz = __ldcs(p2 + H2 + g);
+  k.l1 = __ldcs(reinterpret_cast<const double2*>(a.lam1) + g);
+  k.l2 = __ldcs(reinterpret_cast<const double2*>(a.lam2) + g);
+  return k;
+}
+
+// q = [G p_b + L1 p_b + L2 p_z ; L2 p_b + L1 p_z] for slot g from (G p_b)_g = w;
+// inside PCG also adds this slot's share of p^T q to acc.
+template <typename V, bool PQ>
+__device__ __forceinline__ void k_store(const PassArgs& a, long long g, V w, const KIn& k, double& acc) {
+  const int cls = slot_class(a.lay, g);
+  double o0, o1;
+  map_out(cls, w, 1.0, o0, o1);
+  double2 qb, qz;
+  qb.x = o0 + k.l1.x * k.pb.x + k.l2.x * k.pz.x;
+  qb.y = o1 + k.l1.y * k.pb.y + k.l2.y * k.pz.y;
+  qz.x = k.l2.x * k.pb.x + k.l1.x * k.pz.x;
+  qz.y = k.l2.y * k.pb.y + k.l1.y * k.pz.y;
+  double2* q2 = reinterpret_cast<double2*>(a.q);
+  __stcs(q2 + g, qb);
+  __stcs(q2 + a.lay.H + g, qz);
+  if constexpr (PQ) acc += k.pb.x * qb.x + k.pb.y * qb.y + k.pz.x * qz.x + k.pz.y * qz.y;
+}
+
+// Store the complex value of slot g for the last pass (one slot at a time:
+// used where the operands need no batching).
 template <typename V, bool PQ>
 __device__ __forceinline__ void store_slot(const PassArgs& a, long long g, V w, double& acc) {
   if (a.mapout == MAPOUT_NONE) {
     reinterpret_cast<V*>(a.buf)[g] = w;
     return;
   }
-  const int cls = slot_class(a.lay, g);
-  double o0, o1;
   if (a.mapout == MAPOUT_BETA) {
-    map_out(cls, w, a.out_scale, o0, o1);
+    double o0, o1;
+    map_out(slot_class(a.lay, g), w, a.out_scale, o0, o1);
     __stcs(reinterpret_cast<double2*>(a.dst) + g, make_double2(o0, o1));
     return;
   }
-  // MAPOUT_K: q = [G p_b + L1 p_b + L2 p_z ; L2 p_b + L1 p_z]
-  map_out(cls, w, 1.0, o0, o1);
-  const long long H2 = a.lay.H;
-  const double2* p2 = reinterpret_cast<const double2*>(a.p);
-  const double2 pb = __ldcs(p2 + g), pz = __ldcs(p2 + H2 + g);
-  const double2 l1 = __ldcs(reinterpret_cast<const double2*>(a.lam1) + g);
-  const double2 l2 = __ldcs(reinterpret_cast<const double2*>(a.lam2) + g);
-  double2 qb, qz;
-  qb.x = o0 + l1.x * pb.x + l2.x * pz.x;
-  qb.y = o1 + l1.y * pb.y + l2.y * pz.y;
-  qz.x = l2.x * pb.x + l1.x * pz.x;
-  qz.y = l2.y * pb.y + l1.y * pz.y;
-  double2* q2 = reinterpret_cast<double2*>(a.q);
-  __stcs(q2 + g, qb);
-  __stcs(q2 + H2 + g, qz);
-  if constexpr (PQ) acc += pb.x * qb.x + pb.y * qb.y + pz.x * qz.x + pz.y * qz.y;
+  k_store<V, PQ>(a, g, w, k_load(a, g), acc);
+}
+
+// Loads of the E elements b = 0..E-1 of a thread: `elem(b, g)` gives the global
+// slot g (false outside the grid: value 0) and `sink(b, v)` takes the value.
+// Plain work-buffer loads are all issued before the first value is used (a
+// tile waits for one memory latency, not E).  Mapped inputs (beta layout, the
+// PCG update p = z + beta p) go one slot at a time: these passes are bound by
+// HBM and the FP64 pipe, and holding several slots' FP64 operands costs more
+// registers, and so resident warps, than the latency it hides.  MAPPED kernels
+// (the first pass of a product) carry the mapping code; in the others a mapped
+// input takes the generic one-slot path.
+template <typename V, int E, bool MAPPED, typename F, typename S>
+__device__ __forceinline__ void load_vals(const PassArgs& a, F&& elem, S&& sink) {
+  using T = decltype(V::x);
+  const V zero = cmake<V>((T)0, (T)0);
+  if (a.mapin == MAPIN_NONE) {
+    const V* src = reinterpret_cast<const V*>(a.buf);
+    V v[E];
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      long long g;
+      v[b] = elem(b, g) ? src[g] : zero;
+    }
+#pragma unroll
+    for (int b = 0; b < E; ++b) sink(b, v[b]);
+    return;
+  }
+  if constexpr (!MAPPED) {
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      long long g;
+      sink(b, elem(b, g) ? load_slot<V>(a, g) : zero);
+    }
+  } else if (a.mapin == MAPIN_BETA) {
+    const double2* src = reinterpret_cast<const double2*>(a.src);
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      long long g;
+      V v = zero;
+      if (elem(b, g)) {
+        const double2 r = __ldcs(src + g);
+        v = map_in<V>(slot_class(a.lay, g), r.x, r.y);
+      }
+      sink(b, v);
+    }
+  } else {
+    // MAPIN_PCG: p = z + beta_cg p on both blocks of the slot
+    const long long H2 = a.lay.H;
+    const double bc = a.sc->beta_cg;
+    double2* p2 = reinterpret_cast<double2*>(a.p);
+    const double2* z2 = reinterpret_cast<const double2*>(a.zv);
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      long long g;
+      V v = zero;
+      if (elem(b, g)) {
+        double2 pb = __ldcs(p2 + g), pz = __ldcs(p2 + H2 + g);
+        const double2 zb = __ldcs(z2 + g), zz = __ldcs(z2 + H2 + g);
+        pb.x = zb.x + bc * pb.x;
+        pb.y = zb.y + bc * pb.y;
+        pz.x = zz.x + bc * pz.x;
+        pz.y = zz.y + bc * pz.y;
+        __stcs(p2 + g, pb);
+        __stcs(p2 + H2 + g, pz);
+        v = map_in<V>(slot_class(a.lay, g), pb.x, pb.y);
+      }
+      sink(b, v);
+    }
+  }
+}
+
+// Stores of the E values src(b) to the slots named by `elem` (one slot at a
+// time; the K epilogue loads its FP64 operands per slot, as above).
+template <typename V, int E, bool PQ, typename F, typename S>
+__device__ __forceinline__ void store_vals(const PassArgs& a, double& acc, F&& elem, S&& src) {
+#pragma unroll
+  for (int b = 0; b < E; ++b) {
+    long long g;
+    if (elem(b, g)) store_slot<V, PQ>(a, g, src(b), acc);
+  }
 }
 
 __device__ __forceinline__ void finish_pq(const PassArgs& a, double acc, double* scratch) {
@@ -140,27 +238,32 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) row_pass_kernel(PassAr
   count_launch(a.sc);
   if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
-  const int P = 1 << a.lgP, PP = a.PP, L = LC > 0 ? LC : a.plan.L;
-  const long long row0 = (long long)blockIdx.x * P;
-  for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
-    const int p = idx / L, e = idx - p * L;
-    const long long row = row0 + p;
-    V v = cmake<V>((T)0, (T)0);
-    if (row < a.npencils) v = load_slot<V>(a, row * L + e);
-    buf[e * PP + p] = v;
-  }
-  __syncthreads();
-  fft_tile_l<E, INV, LC>(buf, a.plan, a.lgP, PP, reinterpret_cast<const V*>(a.tw), threadIdx.x, a.nwork);
-  double acc = 0.0;
-  auto store_all = [&](auto pq) {
-    for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
-      const int p = idx / L, e = idx - p * L;
-      const long long row = row0 + p;
-      if (row < a.npencils) store_slot<V, decltype(pq)::value>(a, row * L + e, buf[e * PP + p], acc);
-    }
+  const int PP = a.PP, L = LC > 0 ? LC : a.plan.L, nwork = a.nwork, tid = threadIdx.x;
+  const long long row0 = (long long)blockIdx.x << a.lgP;
+  // element b of a working thread: idx = tid + b nwork, pencil idx / L, position idx % L
+  // (consecutive threads walk one row: coalesced global access)
+  auto sidx = [&](int b) {
+    const int idx = tid + b * nwork;
+    const int p = idx / L;
+    return (idx - p * L) * PP + p;
   };
-  if (a.pcg_mode) store_all(std::true_type{});
-  else store_all(std::false_type{});
+  auto elem = [&](int b, long long& g) -> bool {
+    const int idx = tid + b * nwork;
+    const int p = idx / L;
+    const long long row = row0 + p;
+    g = row * L + (idx - p * L);
+    return row < a.npencils;
+  };
+  // inverse row passes start a product (beta-layout input), forward ones end it
+  if (tid < nwork) load_vals<V, E, INV>(a, elem, [&](int b, V v) { buf[sidx(b)] = v; });
+  __syncthreads();
+  fft_tile_l<E, INV, LC>(buf, a.plan, a.lgP, PP, reinterpret_cast<const V*>(a.tw), tid, nwork);
+  double acc = 0.0;
+  if (tid < nwork) {
+    auto src = [&](int b) { return buf[sidx(b)]; };
+    if (a.pcg_mode) store_vals<V, E, true>(a, acc, elem, src);
+    else store_vals<V, E, false>(a, acc, elem, src);
+  }
   if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
 }
 
@@ -175,24 +278,31 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) col_pass_kernel(PassAr
   count_launch(a.sc);
   if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
-  const int P = 1 << a.lgP, PP = a.PP, L = LC > 0 ? LC : a.plan.L;
+  const int P = 1 << a.lgP, PP = a.PP, nwork = a.nwork, tid = threadIdx.x;
   const int N1 = a.lay.N1;
   const int k1_0 = blockIdx.x * P;
   const long long plane = (long long)blockIdx.y * a.lay.N0;     // kl * N0
-  V* g = reinterpret_cast<V*>(a.buf);
-  for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
-    const int e = idx >> a.lgP, p = idx & (P - 1);
-    const int k1 = k1_0 + p;
-    V v = cmake<V>((T)0, (T)0);
-    if (k1 < N1) v = g[(plane + e) * N1 + k1];
-    buf[e * PP + p] = v;
-  }
+  // element b of a working thread: idx = tid + b nwork, row idx >> lgP, pencil idx & (P - 1)
+  auto sidx = [&](int b) {
+    const int idx = tid + b * nwork;
+    return (idx >> a.lgP) * PP + (idx & (P - 1));
+  };
+  auto elem = [&](int b, long long& g) -> bool {
+    const int idx = tid + b * nwork;
+    const int k1 = k1_0 + (idx & (P - 1));
+    g = (plane + (idx >> a.lgP)) * N1 + k1;
+    return k1 < N1;
+  };
+  if (tid < nwork) load_vals<V, E, false>(a, elem, [&](int b, V v) { buf[sidx(b)] = v; });
   __syncthreads();
-  fft_tile_l<E, INV, LC>(buf, a.plan, a.lgP, PP, reinterpret_cast<const V*>(a.tw), threadIdx.x, a.nwork);
-  for (int idx = threadIdx.x; idx < P * L; idx += blockDim.x) {
-    const int e = idx >> a.lgP, p = idx & (P - 1);
-    const int k1 = k1_0 + p;
-    if (k1 < N1) g[(plane + e) * N1 + k1] = buf[e * PP + p];
+  fft_tile_l<E, INV, LC>(buf, a.plan, a.lgP, PP, reinterpret_cast<const V*>(a.tw), tid, nwork);
+  if (tid < nwork) {
+    V* g = reinterpret_cast<V*>(a.buf);
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+      long long gi;
+      if (elem(b, gi)) g[gi] = buf[sidx(b)];
+    }
   }
 }
 
@@ -236,14 +346,22 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
     }
     __syncthreads();
   } else {
-    // load X (Hl rows)
-    const int Hl = h + 1;
-    for (int idx = tid; idx < P * Hl; idx += blockDim.x) {
-      const int e = idx >> a.lgP, p = idx & (P - 1);
-      const int xp = x0 + p;
-      V v = cmake<V>((T)0, (T)0);
-      if (xp < M) v = load_slot<V>(a, (long long)e * M + xp);
-      buf[e * PP + p] = v;
+    // load X (Hl = h + 1 rows): rows 0..h-1 E per working thread, batched, then row h
+    if (tid < nwork) {
+      auto elem = [&](int b, long long& g) -> bool {
+        const int idx = tid + b * nwork;
+        const int xp = x0 + (idx & (P - 1));
+        g = (long long)(idx >> a.lgP) * M + xp;
+        return xp < M;
+      };
+      load_vals<V, E, false>(a, elem, [&](int b, V v) {
+        const int idx = tid + b * nwork;
+        buf[(idx >> a.lgP) * PP + (idx & (P - 1))] = v;
+      });
+      for (int p = tid; p < P; p += nwork) {
+        const int xp = x0 + p;
+        buf[h * PP + p] = (xp < M) ? load_slot<V>(a, (long long)h * M + xp) : cmake<V>((T)0, (T)0);
+      }
     }
     __syncthreads();
     // C2R pre-processing: Z_k = (X_k + conj X_{h-k}) + i (X_k - conj X_{h-k}) conj(W^k), W = exp(-2 pi i / Nl)
@@ -315,6 +433,196 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
   if (a.pcg_mode) store_all(std::true_type{});
   else store_all(std::false_type{});
   if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// Register-engine passes (fft_reg.cuh): lengths fixed at compile time, E = 16
+// values per thread, the first stage loading from and the last stage storing to
+// global memory; shared memory only for the exchanges between stages.
+// ---------------------------------------------------------------------------
+// Row pass: P rows of length L per block, TT = L / E consecutive threads per
+// row (coalesced along the row); shared memory pencil-major with one pad slot
+// per 16 elements (conflict-free for the stride-R exchange writes).
+template <typename T, int L, int E, bool INV>
+__global__ void __launch_bounds__(256) row_reg_kernel(PassArgs a) {
+  using V = typename cvec<T>::type;
+  constexpr int TT = L / E, LP = L + L / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double scratch[32];
+  count_launch(a.sc);
+  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  const int tid = threadIdx.x, t = tid % TT, p = tid / TT;
+  const long long row = ((long long)blockIdx.x << a.lgP) + p;
+  const bool ok = row < a.npencils;
+  V* sm = reinterpret_cast<V*>(smem_raw) + p * LP;
+  auto elem = [&](int m, long long& g) -> bool {
+    g = row * L + t + TT * m;
+    return ok;
+  };
+  V x[E];
+  load_vals<V, E, INV>(a, elem, [&](int m, V v) { x[m] = v; });
+  reg_fft<E, INV, L>(x, t, reinterpret_cast<const V*>(a.tw), sm, [](int e) { return e + (e >> 4); });
+  double acc = 0.0;
+  auto src = [&](int m) { return x[m]; };
+  if (a.pcg_mode) store_vals<V, E, true>(a, acc, elem, src);
+  else store_vals<V, E, false>(a, acc, elem, src);
+  if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
+}
+
+// Column pass (d = 3): P consecutive k1 per block (pencil index fastest across
+// threads: coalesced), TT = L / E threads per pencil; grid = (ceil(N1 / P), Hl).
+template <typename T, int L, int E, bool INV>
+__global__ void __launch_bounds__(256) col_reg_kernel(PassArgs a) {
+  using V = typename cvec<T>::type;
+  constexpr int TT = L / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  count_launch(a.sc);
+  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  const int lgP = a.lgP, tid = threadIdx.x, p = tid & ((1 << lgP) - 1), t = tid >> lgP;
+  const int N1 = a.lay.N1, k1 = (blockIdx.x << lgP) + p;
+  const long long plane = (long long)blockIdx.y * a.lay.N0;     // kl * N0
+  auto elem = [&](int m, long long& g) -> bool {
+    g = (plane + t + TT * m) * N1 + k1;
+    return k1 < N1;
+  };
+  V x[E];
+  load_vals<V, E, false>(a, elem, [&](int m, V v) { x[m] = v; });
+  reg_fft<E, INV, L>(x, t, reinterpret_cast<const V*>(a.tw), reinterpret_cast<V*>(smem_raw),
+                     [&](int e) { return (e << lgP) + p; });
+  V* gb = reinterpret_cast<V*>(a.buf);
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    long long g;
+    if (elem(m, g)) gb[g] = x[m];
+  }
+}
+
+// Middle pass: the real transform of length Nl = 2 H along the halved axis, P
+// consecutive in-plane positions per block (pencil index fastest), TT = H / E
+// threads per pencil.  Shared memory: the loaded half spectrum ((H + 1) x P)
+// and one exchange buffer (H x P).  Same arithmetic as middle_pass_kernel: C2R
+// pre-processing, inverse transform, mask and 1/n, forward transform, R2C
+// post-processing; the inverse transform leaves element t + TT m in the
+// registers from which the forward one starts, so no exchange joins them.
+template <typename T, int H, int E>
+__global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
+  using V = typename cvec<T>::type;
+  constexpr int TT = H / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double scratch[32];
+  count_launch(a.sc);
+  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  const int lgP = a.lgP, tid = threadIdx.x, p = tid & ((1 << lgP) - 1), t = tid >> lgP;
+  const int M = a.lay.M, Nl = a.lay.Nl, xp = (blockIdx.x << lgP) + p;
+  const bool ok = xp < M;
+  V* tile = reinterpret_cast<V*>(smem_raw);          // rows 0..H
+  V* ex = tile + ((H + 1) << lgP);                   // rows 0..H-1
+  auto at = [&](int e) { return (e << lgP) + p; };
+  const V* twh = reinterpret_cast<const V*>(a.tw);
+  const V* twN = reinterpret_cast<const V*>(a.twN);
+  V x[E];
+  if (a.from_real) {
+    // z_j = (y m)[2j] + i (y m)[2j+1] of the signal row of pencil xp
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int j = t + TT * m;
+      T v0 = (T)0, v1 = (T)0;
+      if (ok) {
+        const uint32_t w = a.maskw[(size_t)((2 * j) >> 5) * M + xp];
+        const double y0 = a.yreal[(size_t)xp * Nl + 2 * j];
+        const double y1 = a.yreal[(size_t)xp * Nl + 2 * j + 1];
+        v0 = (T)(((w >> ((2 * j) & 31)) & 1u) ? y0 : 0.0);
+        v1 = (T)(((w >> ((2 * j + 1) & 31)) & 1u) ? y1 : 0.0);
+      }
+      x[m] = cmake<V>(v0, v1);
+    }
+  } else {
+    {
+      auto elem = [&](int m, long long& g) -> bool {
+        g = (long long)(t + TT * m) * M + xp;
+        return ok;
+      };
+      load_vals<V, E, false>(a, elem, [&](int m, V v) { tile[at(t + TT * m)] = v; });
+      if (t == 0) tile[at(H)] = ok ? load_slot<V>(a, (long long)H * M + xp) : cmake<V>((T)0, (T)0);
+    }
+    __syncthreads();
+    // C2R pre-processing: Z_k = (X_k + conj X_{H-k}) + i (X_k - conj X_{H-k}) conj(W^k), W = exp(-2 pi i / Nl)
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + TT * m;
+      V A = tile[at(k)];
+      V Bc = cconj(tile[at(H - k)]);
+      if (k == 0) { A.y = (T)0; Bc.y = (T)0; }     // edge planes: real part only
+      const V sum = cadd(A, Bc);
+      const V d = cmul_i(cmulconj(csub(A, Bc), __ldg(&twN[k])));
+      x[m] = cadd(sum, d);
+    }
+    reg_fft<E, true, H>(x, t, twh, ex, at);
+    // mask and 1/n: Re z_j <-> sample 2j, Im z_j <-> sample 2j+1 of pencil xp
+    const T invn = (T)a.inv_n;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int j = t + TT * m;
+      const uint32_t mw = ok ? __ldg(&a.maskw[(size_t)(j >> 4) * M + xp]) : 0u;
+      x[m].x *= ((mw >> ((2 * j) & 31)) & 1u) ? invn : (T)0;
+      x[m].y *= ((mw >> ((2 * j + 1) & 31)) & 1u) ? invn : (T)0;
+    }
+  }
+  // forward transform; its exchanges use the tile buffer, whose last reads (the
+  // pre-processing) precede the inverse transform's exchange barrier
+  reg_fft<E, false, H>(x, t, twh, tile, at);
+  __syncthreads();                                   // last reads of ex / tile done
+#pragma unroll
+  for (int m = 0; m < E; ++m) ex[at(t + TT * m)] = x[m];
+  __syncthreads();
+  // R2C post-processing: X'_k = (Z_k + conj Z_{H-k})/2 - i W^k (Z_k - conj Z_{H-k})/2, X'_H = Re Z_0 - Im Z_0
+  double acc = 0.0;
+  auto store_all = [&](auto pq) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + TT * m;
+      const V zk = ex[at(k)];
+      const V zc = cconj(ex[at((H - k) & (H - 1))]);
+      const V sum = cscale(cadd(zk, zc), (T)0.5);
+      const V d = cscale(csub(zk, zc), (T)0.5);
+      const V X = csub(sum, cmul_i(cmul(__ldg(&twN[k]), d)));
+      if (ok) {
+        store_slot<V, decltype(pq)::value>(a, (long long)k * M + xp, X, acc);
+        if (k == 0) store_slot<V, decltype(pq)::value>(a, (long long)H * M + xp, cmake<V>(zk.x - zk.y, (T)0), acc);
+      }
+    }
+  };
+  if (a.pcg_mode) store_all(std::true_type{});
+  else store_all(std::false_type{});
+  if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
+}
+
+template <typename T, int L>
+cudaError_t launch_reg_l(int kind, bool inv, const PassArgs& a, int threads, size_t smem, dim3 grid, cudaStream_t st) {
+  constexpr int E = 16;
+  void (*fn)(PassArgs) = nullptr;
+  if (kind == 0) fn = inv ? row_reg_kernel<T, L, E, true> : row_reg_kernel<T, L, E, false>;
+  else if (kind == 1) fn = inv ? col_reg_kernel<T, L, E, true> : col_reg_kernel<T, L, E, false>;
+  else fn = mid_reg_kernel<T, L, E>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  fn<<<grid, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Register engine: E = 16 and L (for the middle pass h = Nl / 2) in {32, ..., 512}.
+template <typename T>
+cudaError_t launch_reg(int kind, bool inv, const PassArgs& a, int threads, size_t smem, dim3 grid, cudaStream_t st) {
+  switch (a.plan.L) {
+    case 32: return launch_reg_l<T, 32>(kind, inv, a, threads, smem, grid, st);
+    case 64: return launch_reg_l<T, 64>(kind, inv, a, threads, smem, grid, st);
+    case 128: return launch_reg_l<T, 128>(kind, inv, a, threads, smem, grid, st);
+    case 256: return launch_reg_l<T, 256>(kind, inv, a, threads, smem, grid, st);
+    case 512: return launch_reg_l<T, 512>(kind, inv, a, threads, smem, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T, int E, int LC>

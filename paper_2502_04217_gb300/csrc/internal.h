@@ -86,6 +86,7 @@ struct PassArgs {
   double* partials;
   unsigned* counter;
   DevScalars* sc;
+  int reg;               // 1: register-engine kernels (fft_reg.cuh), E = 16
 };
 
 // Launchers (fft_passes.cu).  `pass_kind`: 0 row, 1 column, 2 middle.

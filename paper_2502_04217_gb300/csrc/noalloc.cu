@@ -108,15 +108,7 @@ extern "C" ipm_status gapply_noalloc(int ndim, const int64_t* dims, const uint8_
     if (!length_ok(dims[i]))
       return arg_error("gapply_noalloc: every extent must be even, of the form 2^a 3^b (b <= 1), and at most 512");
   if (!mask || !p || !q) return arg_error("gapply_noalloc: mask, p and q must be device pointers");
-  Layout L{};
-  L.d = ndim;
-  L.Nl = (int)dims[ndim - 1];
-  L.N0 = ndim >= 2 ? (int)dims[0] : 1;
-  L.N1 = ndim == 3 ? (int)dims[1] : 1;
-  L.M = L.N0 * L.N1;
-  L.Hl = L.Nl / 2 + 1;
-  L.H = (long long)L.Hl * L.M;
-  L.n = (long long)L.Nl * L.M;
+  const Layout L = layout_init(ndim, ndim >= 2 ? (int)dims[0] : 1, ndim == 3 ? (int)dims[1] : 1, (int)dims[ndim - 1]);
   if (L.H > kNoAllocMaxSlots)
     return arg_error("gapply_noalloc: grid too large for the fixed scratch (at most 262144 half-spectrum "
                      "slots; 512 x 512 and 64 x 64 x 64 fit); use ipm_create / gapply");

@@ -350,3 +350,67 @@ def test_mixed_precision_with_fp64_residual_replacement(refine_every):
     assert r["rel_gap"] <= 1e-9 and r["refinements"] > 0
     assert abs(r["primal"] - r64["primal"]) <= 1e-8 * abs(r64["primal"])
     assert np.abs(v - v64).max() <= 1e-5 * np.abs(v64).max()
+
+
+@pytest.mark.parametrize("tile_p", [0, 2, 16])
+@pytest.mark.parametrize("dims", [(512,), (256, 128), (512, 64), (64, 32, 64), (16, 128, 256), (128, 64, 128),
+                                  (32, 256, 32)])
+def test_register_engine_matches_oracle(dims, tile_p):
+    """The register FFT engine (first and last stage in registers, lengths 32..512):
+    products with G and with K, forced wherever the length allows, against the
+    oracle; passes of other lengths fall back to the shared-memory engine."""
+    n = int(np.prod(dims))
+    for precision in (binding.IPM_FP64, binding.IPM_MIXED):
+        w = _workload(dims, seed=21)
+        h = _handle(w, precision, tile_engine=2, tile_p=tile_p, autotune=0)
+        try:
+            prob = _oracle(w, 1.0)
+            beta = np.random.default_rng(22).standard_normal(n)
+            p = oracle_to_lib(h, beta, dims)
+            q = torch.empty_like(p)
+            binding.gapply(h, p, q)
+            tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * np.linalg.norm(beta)
+            assert np.abs(lib_to_half(h, q) - oracle_to_half(prob.G(beta), dims)).max() < tol
+            # every pass whose length and forced P admit a register tile uses one
+            for name, c in binding.ipm_describe(h).items():
+                L, launchable = c["L"], False
+                if L in (32, 64, 128, 256, 512):
+                    ps = [tile_p] if tile_p else [1, 2, 4, 8, 16, 32]
+                    launchable = any((q * L // 16) % 32 == 0 and q * L // 16 <= 256 for q in ps)
+                assert (c["engine"] == "register") == launchable, (name, c)
+            # K p: the FP64 diagonal epilogue of the last pass
+            rng = np.random.default_rng(23)
+            s1, nu1, s2, nu2 = _interior(n, rng)
+            binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+            S1, S2 = oipm.sigmas(s1, nu1, s2, nu2)
+            pb, pz = rng.standard_normal(n), rng.standard_normal(n)
+            pk = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
+            qk = torch.empty_like(pk)
+            binding.kkt_apply(h, pk, qk)
+            qb, qz = oipm.K_apply(prob.G, S1, S2, pb, pz)
+            H2 = pk.numel() // 2
+            scale = np.linalg.norm(np.concatenate([pb, pz])) * (1 + (S1 + S2).max())
+            tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * scale
+            assert np.abs(lib_to_half(h, qk[:H2]) - oracle_to_half(qb, dims)).max() < tol
+            assert np.abs(lib_to_half(h, qk[H2:]) - oracle_to_half(qz, dims)).max() < 1e-13 * scale
+        finally:
+            binding.ipm_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+@pytest.mark.parametrize("dims", [(64, 32, 64), (256, 64)])
+def test_register_engine_solve_matches_shared_engine(dims, precision):
+    """Whole solves (PCG prologue p = z + beta p and p^T q in the register kernels)
+    with the register engine forced agree with the shared-memory engine."""
+    w = _workload(dims, seed=24)
+    out = {}
+    for engine in (1, 2):
+        h = _handle(w, precision, gap_tol=1e-8, tile_engine=engine, autotune=0)
+        try:
+            out[engine] = binding.ipm_solve(h)
+        finally:
+            binding.ipm_destroy(h)
+    for r in out.values():
+        assert r["status"] == binding.IPM_OK and r["rel_gap"] <= 1e-8
+    tol = 1e-9 if precision == binding.IPM_FP64 else 1e-6
+    assert abs(out[1]["primal"] - out[2]["primal"]) <= tol * abs(out[1]["primal"])
