@@ -104,6 +104,21 @@ typedef struct {
                            registers straight from / to global memory) wherever the length
                            allows it (32, 64, 128, 256 or 512; the middle pass uses Nl/2),
                            else the shared-memory one.  tile_e is ignored by engine 2.       */
+  int sigma_rule;       /* centring parameter for the next direction.  1 (default): adaptive,
+                           sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow) from the last
+                           step alpha (Mehrotra's (mu_aff / mu)^3 heuristic with the previous
+                           step standing in for an affine predictor: one Newton system per
+                           iteration; the first direction uses sigma); 0: sigma, or
+                           sigma_slow after a step alpha < 0.1                               */
+  double sigma_min;     /* lower clamp of the adaptive rule (default 0.03; at 0.01 the PCG
+                           of tiny problems broke down below a 1e-12 gap)                    */
+  int exact_residual;   /* IPM_FP64 only.  0 (default): G beta is carried along with beta
+                           (the last pass of each PCG product also stores (G p)_beta, PCG
+                           accumulates G x = sum alpha G p beside x, the step adds alpha G x),
+                           and an FP64 product recomputes it only to confirm a stop test that
+                           passed on the carried value; 1: an FP64 product recomputes G beta
+                           every IPM iteration (IPM_MIXED always does, its PCG products being
+                           FP32)                                                            */
 } ipm_options;
 
 typedef struct {
@@ -118,8 +133,8 @@ typedef struct {
   double lambda;        /* the lambda actually used                                  */
   double lambda_max;    /* ||M_perp^T b||_inf                                        */
   double seconds;       /* wall time of ipm_solve                                    */
-  int kkt_products;     /* products with M_perp^T M_perp (PCG, one per IPM iteration,
-                           one per FP64 residual replacement)                          */
+  int kkt_products;     /* products with M_perp^T M_perp (PCG; the FP64 products that
+                           recomputed G beta; FP64 residual replacements)               */
   int refinements;      /* FP64 residual replacements inside PCG (refine_every > 0)  */
 } ipm_result;
 

@@ -39,6 +39,12 @@ Our readings (the paper leaves them to MadNLP or prints them with typos)
 * Step: one common step alpha = min(1, tau * alpha_max) for all variables,
   alpha_max the largest step keeping (s, nu) >= 0; tau = 0.995.  sigma = 0.1,
   raised to 0.5 for the next iteration after a step alpha < 0.1.
+* Optional adaptive centring (``sigma_rule="adaptive"``), in the direction of the
+  single-step predictor-corrector the paper suggests (Sec. 5): Mehrotra's
+  centring heuristic sigma = (mu_aff / mu)^3 needs the affine-scaling predictor,
+  a second Newton system per iteration; here the previous step stands in for it,
+  sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow) for the next direction
+  (the first direction uses sigma0), and each iteration solves one system.
 * Stop when the relative duality gap (``Problem.certificate``) is <= gap_tol.
 * PCG: x0 = 0, stop when sqrt(r^T z) <= cg_tol * sqrt(r0^T z0) (relative,
   the default) or sqrt(r^T z) <= cg_tol (absolute, as the paper's 1e-12 rule),
@@ -162,8 +168,15 @@ def starting_point(prob):
     return [beta, z, z.copy(), z.copy(), nu, nu.copy()]
 
 
+def next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min):
+    """Centring parameter for the next direction after a step of length alpha."""
+    if rule == "adaptive":
+        return min(sigma_slow, max(sigma_min, (1.0 - alpha) ** 3))
+    return sigma_slow if alpha < 0.1 else sigma0
+
+
 def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative=True,
-          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None):
+          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.01):
     """Run the IPM; returns a dict with the point, counts and the certificate."""
     w = [np.array(v, dtype=np.float64, copy=True) for v in (w0 or starting_point(prob))]
     sigma = sigma0
@@ -192,7 +205,7 @@ def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative
         alpha = min(1.0, tau * amax)
         for v, d in zip(w, (dbeta, dz, ds1, ds2, dnu1, dnu2)):
             v += alpha * d
-        sigma = sigma_slow if alpha < 0.1 else sigma0
+        sigma = next_sigma(alpha, sigma_rule, sigma0, sigma_slow, sigma_min)
     P, D, gap = prob.certificate(w[0])
     return dict(status=status, point=w, beta=w[0], primal=P, dual=D, gap=gap,
                 ipm_iters=len(cg_counts), cg_counts=cg_counts)

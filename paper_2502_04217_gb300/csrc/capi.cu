@@ -124,6 +124,11 @@ namespace {
     }                                                                                  \
   } while (0)
 
+// FP64 mode updates G beta from the PCG products (G x accumulated alongside x)
+// and recomputes it with an FP64 product only to confirm a passed stop test;
+// mixed precision recomputes it every iteration (its PCG products are FP32).
+int incremental_gb(const sdft_ipm* h) { return (h->opt.precision == IPM_FP64 && !h->opt.exact_residual) ? 1 : 0; }
+
 ipm_status fail_arg(sdft_ipm* h, const char* msg) {
   if (h) h->err = msg; else g_create_error = msg;
   return IPM_ERR_ARG;
@@ -470,6 +475,7 @@ struct GSpec {
   double out_scale = 1.0;
   bool pcg = false;              // MAPIN_PCG / MAPOUT_K inside PCG (p, zv, q of the handle)
   bool refine = false;           // only when the device asks for an FP64 residual replacement
+  bool exact = false;            // only when the device asks for an exact G beta (incremental mode)
   const double* p_in = nullptr;  // kkt_apply: p and q given by the caller
   double* q_out = nullptr;
 };
@@ -497,6 +503,8 @@ ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
     }
     a.check_done = g.pcg ? 1 : 0;
     a.check_refine = g.refine ? 1 : 0;
+    a.check_exact = g.exact ? 1 : 0;
+    if (last) a.gp_out = (g.pcg && !fp32 && incremental_gb(h)) ? h->w.Gp : nullptr;
   };
   ipm_status s;
   if (L.d == 1) {
@@ -602,6 +610,10 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (o.max_ipm < 0 || o.max_cg < 1 || o.cg_chunk < 1) return fail_arg(h, "iteration caps must be positive");
   if (o.refine_every < 0) return fail_arg(h, "refine_every must be >= 0");
   if (o.tile_engine < 0 || o.tile_engine > 2) return fail_arg(h, "tile_engine must be 0, 1 or 2");
+  if (o.sigma_rule < 0 || o.sigma_rule > 1) return fail_arg(h, "sigma_rule must be 0 or 1");
+  if (o.exact_residual < 0 || o.exact_residual > 1) return fail_arg(h, "exact_residual must be 0 or 1");
+  if (o.sigma_rule == 1 && !(o.sigma_min > 0 && o.sigma_min <= o.sigma_slow))
+    return fail_arg(h, "sigma_min must lie in (0, sigma_slow]");
   if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
   if (!(o.tau > 0 && o.tau < 1)) return fail_arg(h, "tau must lie in (0,1)");
   return IPM_OK;
@@ -630,6 +642,9 @@ void ipm_default_options(ipm_options* o) {
   o->tile_p = 0;
   o->refine_every = 0;
   o->tile_engine = 0;
+  o->sigma_rule = 1;
+  o->sigma_min = 0.03;
+  o->exact_residual = 0;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -671,7 +686,8 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   CKC(dalloc(h, &h->d_y, (size_t)L.n * sizeof(double)));
   CKC(dalloc(h, &h->d_maskw, (size_t)((L.Nl + 31) / 32) * L.M * sizeof(uint32_t)));
   double** vec2[] = {&h->w.beta, &h->w.z, &h->w.s1, &h->w.s2, &h->w.nu1, &h->w.nu2, &h->w.c, &h->w.Gb,
-                     &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->w.is1, &h->w.is2, &h->d_tmp};
+                     &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->w.is1, &h->w.is2, &h->d_tmp,
+                     &h->w.Gp, &h->w.Gx};
   for (double** p : vec2) CKC(dalloc(h, p, v2));
   double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q, &h->w.rhs};
   for (double** p : vec4) CKC(dalloc(h, p, v4));
@@ -814,6 +830,7 @@ ipm_status queue_residual_and_test(sdft_ipm* h, LoopCtl ipm_loop) {
   GSpec g;
   g.src = h->w.beta;
   g.dst = h->w.Gb;
+  g.exact = incremental_gb(h) != 0;                    // incremental mode: only when a stop test is to be confirmed
   ipm_status s = run_g(h, false, g);                   // residual always in FP64
   if (s != IPM_OK) return s;
   ProfScope ps(h, 4);
@@ -864,7 +881,8 @@ ipm_status queue_step(sdft_ipm* h) {
     CK(k_step_length(h->lay, h->w, red, h->d_sc, h->opt.tau, h->st));
   }
   ProfScope ps(h, 4);
-  CK(k_step_update(h->lay, h->w, red, h->d_sc, h->opt.sigma, h->opt.sigma_slow, h->st));
+  CK(k_step_update(h->lay, h->w, red, h->d_sc, h->opt.sigma, h->opt.sigma_slow, h->opt.sigma_rule,
+                   h->opt.sigma_min, h->st));
   return IPM_OK;
 }
 
@@ -925,7 +943,7 @@ ipm_status fill_result(sdft_ipm* h, ipm_result* res, double seconds) {
     res->mu = sc.mu;
     res->lambda = sc.lambda;
     res->lambda_max = sc.cmax;
-    res->kkt_products = sc.cg_total + sc.ipm_it + 1 + sc.refinements;
+    res->kkt_products = sc.cg_total + sc.gb_products + sc.refinements;
     res->seconds = seconds;
     res->refinements = sc.refinements;
   }
@@ -947,8 +965,8 @@ ipm_status ipm_solve(sdft_ipm* h, ipm_result* res) {
   ipm_status s;
   {
     ProfScope ps(h, 4);
-    if (h->point_set) CK(k_mu(L, h->w, red, h->d_sc, o.sigma, h->st));
-    else CK(k_init_point(L, h->w, red, h->d_sc, o.sigma, h->st));
+    if (h->point_set) CK(k_mu(L, h->w, red, h->d_sc, o.sigma, incremental_gb(h), h->st));
+    else CK(k_init_point(L, h->w, red, h->d_sc, o.sigma, incremental_gb(h), h->st));
   }
   h->point_set = false;
   const LoopCtl none{0, 0};
@@ -1210,7 +1228,7 @@ ipm_status build_batch_graph(sdft_ipm_batch* b) {
     {
       StreamSwap sw(h, h->cap[0]);
       Reduce red{h->d_partials, h->d_counter};
-      cudaError_t e = k_init_point(h->lay, h->w, red, h->d_sc, h->opt.sigma, h->st);
+      cudaError_t e = k_init_point(h->lay, h->w, red, h->d_sc, h->opt.sigma, incremental_gb(h), h->st);
       if (e != cudaSuccess) s = batch_fail(b, std::string("init: ") + cudaGetErrorString(e), IPM_ERR_CUDA);
       if (s == IPM_OK) s = capture_solve_loop(h);
       if (s != IPM_OK && b->err.empty()) b->err = h->err;

@@ -78,6 +78,14 @@ __device__ __forceinline__ V load_slot(const PassArgs& a, long long g) {
   return map_in<V>(cls, pb.x, pb.y);
 }
 
+// A pass inside a loop returns at once when its product is not wanted: PCG
+// products once PCG has stopped, the FP64 replacement products unless asked
+// for, and the incremental-G-beta residual product unless an exact one is due.
+__device__ __forceinline__ bool pass_skipped(const PassArgs& a) {
+  return (a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now) ||
+         (a.check_exact && !a.sc->exact_now);
+}
+
 // FP64 operands of the K epilogue for one slot: p on both blocks and the two
 // diagonal coefficients of K.
 struct KIn {
@@ -110,6 +118,7 @@ __device__ __forceinline__ void k_store(const PassArgs& a, long long g, V w, con
   double2* q2 = reinterpret_cast<double2*>(a.q);
   __stcs(q2 + g, qb);
   __stcs(q2 + a.lay.H + g, qz);
+  if (a.gp_out) __stcs(reinterpret_cast<double2*>(a.gp_out) + g, make_double2(o0, o1));
   if constexpr (PQ) acc += k.pb.x * qb.x + k.pb.y * qb.y + k.pz.x * qz.x + k.pz.y * qz.y;
 }
 
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) row_pass_kernel(PassAr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
   count_launch(a.sc);
-  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  if (pass_skipped(a)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int PP = a.PP, L = LC > 0 ? LC : a.plan.L, nwork = a.nwork, tid = threadIdx.x;
   const long long row0 = (long long)blockIdx.x << a.lgP;
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) col_pass_kernel(PassAr
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   count_launch(a.sc);
-  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  if (pass_skipped(a)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP, nwork = a.nwork, tid = threadIdx.x;
   const int N1 = a.lay.N1;
@@ -321,7 +330,7 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
   count_launch(a.sc);
-  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  if (pass_skipped(a)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int P = 1 << a.lgP, PP = a.PP;
   const int h = LC > 0 ? LC : a.plan.L, Nl = a.lay.Nl, M = a.lay.M;
@@ -450,7 +459,7 @@ __global__ void __launch_bounds__(256) row_reg_kernel(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
   count_launch(a.sc);
-  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  if (pass_skipped(a)) return;
   const int tid = threadIdx.x, t = tid % TT, p = tid / TT;
   const long long row = ((long long)blockIdx.x << a.lgP) + p;
   const bool ok = row < a.npencils;
@@ -477,7 +486,7 @@ __global__ void __launch_bounds__(256) col_reg_kernel(PassArgs a) {
   constexpr int TT = L / E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   count_launch(a.sc);
-  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  if (pass_skipped(a)) return;
   const int lgP = a.lgP, tid = threadIdx.x, p = tid & ((1 << lgP) - 1), t = tid >> lgP;
   const int N1 = a.lay.N1, k1 = (blockIdx.x << lgP) + p;
   const long long plane = (long long)blockIdx.y * a.lay.N0;     // kl * N0
@@ -511,7 +520,7 @@ __global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
   count_launch(a.sc);
-  if ((a.check_done && a.sc->cg_done) || (a.check_refine && !a.sc->refine_now)) return;
+  if (pass_skipped(a)) return;
   const int lgP = a.lgP, tid = threadIdx.x, p = tid & ((1 << lgP) - 1), t = tid >> lgP;
   const int M = a.lay.M, Nl = a.lay.Nl, xp = (blockIdx.x << lgP) + p;
   const bool ok = xp < M;

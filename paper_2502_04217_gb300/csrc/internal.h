@@ -45,6 +45,10 @@ struct DevScalars {
   int refine_now;    // mixed precision: recompute the PCG residual in FP64 after this update
   int refine_exit;   // ... because PCG had stopped (1) or periodically (0)
   int refinements;   // FP64 residual replacements over the solve
+  int incr;          // 1: G beta is updated from the PCG products and recomputed only to confirm the stop
+  int exact_now;     // (incr) G beta is recomputed by an FP64 product in this IPM iteration
+  int gb_products;   // FP64 products that recomputed G beta over the solve
+  int pad1;
   unsigned long long launches;   // kernels launched by the library (every kernel adds 1)
 };
 
@@ -79,6 +83,8 @@ struct PassArgs {
   int pcg_mode;          // MAPOUT_K inside PCG: form alpha = rho / p^T q
   int check_done;        // return at once when sc->cg_done
   int check_refine;      // return at once unless sc->refine_now
+  int check_exact;       // return at once unless sc->exact_now
+  double* gp_out;        // MAPOUT_K in PCG (incremental G beta): also store (G p)_beta here (2H)
   const uint32_t* maskw; // middle pass: bit-packed mask, word (xl/32)*M + x'
   double inv_n;          // 1/n, applied with the mask
   const double* yreal;   // middle pass "from real": the signal on the grid (row-major)

@@ -83,7 +83,10 @@ __global__ void __launch_bounds__(kThreads) cmax_kernel(const double* __restrict
   }
 }
 
-__device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double sigma0) {
+__device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double sigma0, int incr) {
+  sc->incr = incr;
+  sc->exact_now = 1;
+  sc->gb_products = 0;
   sc->mu = mu;
   sc->sigma = sigma0;
   sc->alpha = 0.0;
@@ -102,7 +105,7 @@ __device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double 
 // Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu; control reset
 __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double* beta, double* z, double* s1, double* s2,
                                                               double* nu1, double* nu2, double* partials, unsigned* counter,
-                                                              DevScalars* sc, double sigma0) {
+                                                              DevScalars* sc, double sigma0, int incr) {
   __shared__ double scratch[32];
   count_launch(sc);
   const double zeta = fmax(1.0, sc->cmax), hl = 0.5 * sc->lambda;
@@ -120,12 +123,12 @@ __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double
     if (!gh) v[0] += hl * zeta + hl * zeta;
   }
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0)
-    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0);
+    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0, incr);
 }
 
 // mu = (nu1^T s1 + nu2^T s2) / 2n at a given point (after ipm_set_point); control reset
 __global__ void __launch_bounds__(kThreads) mu_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
-                                                      DevScalars* sc, double sigma0) {
+                                                      DevScalars* sc, double sigma0, int incr) {
   __shared__ double scratch[32];
   count_launch(sc);
   double v[1] = {0.0};
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) mu_kernel(Layout lay, IpmVectors w, 
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
     if (!is_ghost(lay, i)) v[0] += w.nu1[i] * w.s1[i] + w.nu2[i] * w.s2[i];
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0)
-    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0);
+    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0, incr);
 }
 
 // Duality-gap certificate at beta from G beta and c = M_perp^T b, and the IPM stop test:
@@ -172,9 +175,15 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
     sc->primal = P;
     sc->dual = D;
     sc->gap = gap;
+    // incremental G beta: a stop test passed on the updated G beta is confirmed
+    // by an exact FP64 product first (this iteration takes no step)
+    const bool exact = !sc->incr || sc->exact_now;
+    if (exact) sc->gb_products += 1;
     if (!isfinite(gap) || !isfinite(sc->mu)) { sc->ipm_done = 1; sc->ipm_status = 6; }
-    else if (gap <= gap_tol) { sc->ipm_done = 1; sc->ipm_status = 0; }
+    else if (gap <= gap_tol && exact) { sc->ipm_done = 1; sc->ipm_status = 0; }
+    else if (gap <= gap_tol) sc->exact_now = 1;
     else if (sc->ipm_it >= max_ipm) { sc->ipm_done = 1; sc->ipm_status = 4; }
+    else sc->exact_now = 0;
     set_cond(ipm_loop, sc->ipm_done ? 0u : 1u);
   }
 }
@@ -185,10 +194,11 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
                                                            DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop) {
   __shared__ double scratch[32];
   count_launch(sc);
-  if (sc->ipm_done) {                       // after the stop test: no PCG
+  if (sc->ipm_done || (sc->incr && sc->exact_now)) {   // after the stop test, or before an exact re-test: no PCG
     if (first_thread()) { sc->cg_done = 1; set_cond(cg_loop, 0u); }
     return;
   }
+  const bool incr = sc->incr;
   const long long n2 = 2 * lay.H;
   const double lam = sc->lambda, smu = sc->sigma * sc->mu;
   double v[1] = {0.0};
@@ -225,6 +235,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     w.rhs[i] = rb; w.rhs[n2 + i] = rc;
     w.zv[i] = zb; w.zv[n2 + i] = zz;
     w.p[i] = zb; w.p[n2 + i] = zz;
+    if (incr) w.Gx[i] = 0.0;
     v[0] += rb * zb + rc * zz;
   }
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
@@ -285,10 +296,12 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmV
     return;
   }
   const double alpha = sc->alpha_cg;
+  const bool incr = sc->incr;
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     const double pbv = w.p[i], pzv = w.p[n2 + i];
+    if (incr) w.Gx[i] += alpha * w.Gp[i];      // (G x)_beta alongside x_beta
     w.x[i] += alpha * pbv;
     w.x[n2 + i] += alpha * pzv;
     const double rb = w.r[i] - alpha * w.q[i];
@@ -371,7 +384,7 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
                                                                DevScalars* sc, double tau) {
   __shared__ double scratch[32];
   count_launch(sc);
-  if (sc->ipm_done) return;
+  if (sc->ipm_done || (sc->incr && sc->exact_now)) return;
   const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu;
   // ratio test min over {w / (-dw) : dw < 0} in FP32 (operands converted on the
@@ -396,18 +409,21 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
 
 // Take the step, form the new duality measure mu, count the iteration
 __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
-                                                               DevScalars* sc, double sigma0, double sigma_slow) {
+                                                               DevScalars* sc, double sigma0, double sigma_slow,
+                                                               int sigma_rule, double sigma_min) {
   __shared__ double scratch[32];
   count_launch(sc);
-  if (sc->ipm_done) return;
+  if (sc->ipm_done || (sc->incr && sc->exact_now)) return;
   const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu, alpha = sc->alpha;
+  const bool incr = sc->incr;
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i)) continue;
     const Dir d = direction(w, i, n2, smu);
     w.beta[i] += alpha * w.x[i];
+    if (incr) w.Gb[i] += alpha * w.Gx[i];        // G beta follows beta (G is linear)
     w.z[i] += alpha * w.x[n2 + i];
     const double s1 = w.s1[i] + alpha * d.ds1, s2 = w.s2[i] + alpha * d.ds2;
     const double n1 = w.nu1[i] + alpha * d.dn1, n2_ = w.nu2[i] + alpha * d.dn2;
@@ -416,7 +432,13 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
   }
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
     sc->mu = v[0] / (2.0 * (double)lay.n);
-    sc->sigma = (alpha < 0.1) ? sigma_slow : sigma0;
+    if (sigma_rule == 1) {
+      // adaptive centring: (1 - alpha)^3 stands in for Mehrotra's (mu_aff / mu)^3
+      const double t = 1.0 - alpha;
+      sc->sigma = fmin(sigma_slow, fmax(sigma_min, t * t * t));
+    } else {
+      sc->sigma = (alpha < 0.1) ? sigma_slow : sigma0;
+    }
     sc->ipm_it += 1;
     sc->cg_total += sc->cg_iter;
     if (sc->cg_iter > sc->cg_max) sc->cg_max = sc->cg_iter;
@@ -515,13 +537,14 @@ cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Redu
   cmax_kernel<<<grid_for(n2), kThreads, 0, st>>>(c, n2, lam, relative, red.partials, red.counter, sc);
   return cudaGetLastError();
 }
-cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st) {
+cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr,
+                         cudaStream_t st) {
   init_point_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, red.partials,
-                                                              red.counter, sc, sigma0);
+                                                              red.counter, sc, sigma0, incr);
   return cudaGetLastError();
 }
-cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st) {
-  mu_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0);
+cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr, cudaStream_t st) {
+  mu_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0, incr);
   return cudaGetLastError();
 }
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
@@ -560,8 +583,9 @@ cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalar
   return cudaGetLastError();
 }
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
-                          cudaStream_t st) {
-  step_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0, sigma_slow);
+                          int sigma_rule, double sigma_min, cudaStream_t st) {
+  step_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0, sigma_slow,
+                                                               sigma_rule, sigma_min);
   return cudaGetLastError();
 }
 cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, DevScalars* sc, cudaStream_t st) {

@@ -15,6 +15,8 @@ struct IpmVectors {
   double *is1, *is2;                          // 1/s1, 1/s2 at the current iterate (step kernels)
   double *x, *r, *zv, *p, *q;                 // PCG vectors, 2 blocks each (4H)
   double *rhs;                                // right-hand side of the current Newton system (4H)
+  double *Gp, *Gx;                            // incremental G beta: (G p)_beta of the last PCG product and
+                                              // (G x)_beta = sum alpha (G p)_beta over the PCG solve (2H each)
 };
 
 // grid size used by every elementwise kernel (also sizes the partials buffer)
@@ -45,8 +47,9 @@ struct HandleView {
 cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, DevScalars* sc, cudaStream_t st);
 cudaError_t k_observed_norm(const double* y, const uint8_t* mask, long long n, Reduce red, DevScalars* sc, cudaStream_t st);
 cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Reduce red, DevScalars* sc, cudaStream_t st);
-cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st);
-cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, cudaStream_t st);
+cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr,
+                         cudaStream_t st);
+cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr, cudaStream_t st);
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
                           DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st);
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
@@ -59,7 +62,7 @@ cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars
 cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st);
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st);
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
-                          cudaStream_t st);
+                          int sigma_rule, double sigma_min, cudaStream_t st);
 cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, DevScalars* sc, cudaStream_t st);
 cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, DevScalars* sc, cudaStream_t st);
 cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, DevScalars* sc, cudaStream_t st);

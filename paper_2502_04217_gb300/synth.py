@@ -21,6 +21,12 @@ Workloads (the paper's real X-ray volume is not available; these synthetic
              lattice offsets, noise 0.01, lambda = 0.05 lambda_max.
 * ``3d512``  512^3, 100000 frequencies, background and noise as ``3d``, radius-2
              balls on a period-8 lattice.
+* ``paper``  the paper's own synthetic generator (Sec. 4.1), any N x N x N: the
+             separable signal x_ijk = f(i, 1, N) f(j, 2, N) f(k, 3, N) with
+             f(t, q, N) = cos(2 pi q t / N) + 2 sin(2 pi q t / N), plus iid U(0, 1)
+             noise; about 15 % missing "around the Bragg peaks", read as balls of
+             radius 2 on a period-6 lattice (15.3 % missing); lambda = 0.05
+             lambda_max (the paper does not state its lambda).
 * ``custom`` any even grid, see ``make_problem``.
 
 lambda is returned as a *fraction* of lambda_max = ||M_perp^T b||_inf; each
@@ -60,6 +66,14 @@ def _sparse_signal(rng, dims, k, amp="normal"):
     spec.reshape(-1)[freqs] = amps
     x = np.fft.irfftn(spec, s=dims, axes=tuple(range(len(dims))), norm="ortho")
     return x, freqs, amps
+
+
+def paper_signal(N):
+    """The paper's separable test signal on an N x N x N grid (Sec. 4.1):
+    x_ijk = f(i, 1) f(j, 2) f(k, 3), f(t, q) = cos(2 pi q t / N) + 2 sin(2 pi q t / N)."""
+    t = np.arange(N)
+    f = [np.cos(2 * np.pi * q * t / N) + 2 * np.sin(2 * np.pi * q * t / N) for q in (1, 2, 3)]
+    return f[0][:, None, None] * f[1][None, :, None] * f[2][None, None, :]
 
 
 def lattice_mask(dims, period, radius2, offset=None):
@@ -111,6 +125,12 @@ def make_problem(name, index=0, dims=None, k=None, noise=0.01, missing=0.1, lam_
         offset = rng.integers(0, period, size=3)
         return Workload(dims, lattice_mask(dims, period, radius * radius, offset), y, 0.05, f, a,
                         f"batch[{index}]")
+    if name == "paper":
+        N = int(dims[0]) if dims is not None else 64
+        dims = (N, N, N)
+        rng = np.random.default_rng(SEED_BASE + 6 + (seed if seed is not None else 0))
+        y = paper_signal(N) + rng.uniform(0.0, 1.0, dims)
+        return Workload(dims, lattice_mask(dims, 6, 4), y, 0.05, None, None, f"paper[{N}]")
     if name == "custom":
         dims = tuple(int(d) for d in dims)
         n = int(np.prod(dims))

@@ -414,3 +414,56 @@ def test_register_engine_solve_matches_shared_engine(dims, precision):
         assert r["status"] == binding.IPM_OK and r["rel_gap"] <= 1e-8
     tol = 1e-9 if precision == binding.IPM_FP64 else 1e-6
     assert abs(out[1]["primal"] - out[2]["primal"]) <= tol * abs(out[1]["primal"])
+
+
+@pytest.mark.parametrize("dims", [(32, 24, 16), (64, 48)])
+def test_adaptive_centring_matches_oracle(dims):
+    """sigma_rule = 1 (sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow)): the library
+    and the oracle with the same rule take the same IPM iterations to the same optimum."""
+    w = _workload(dims, seed=25)
+    h = _handle(w, binding.IPM_FP64, gap_tol=1e-8, sigma_rule=1, sigma_min=0.03)
+    try:
+        res = binding.ipm_solve(h)
+    finally:
+        binding.ipm_destroy(h)
+    prob = _oracle(w, res["lambda"])
+    ora = oipm.solve(prob, gap_tol=1e-8, sigma_rule="adaptive", sigma_min=0.03)
+    assert res["status"] == binding.IPM_OK and ora["status"] == "converged"
+    assert res["ipm_iters"] == ora["ipm_iters"]
+    assert abs(res["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
+
+
+def test_fixed_centring_matches_oracle():
+    """sigma_rule = 0 (sigma = 0.1, 0.5 after a step alpha < 0.1): same iterations as the oracle's default."""
+    w = _workload((32, 24, 16), seed=26)
+    h = _handle(w, binding.IPM_FP64, gap_tol=1e-8, sigma_rule=0)
+    try:
+        res = binding.ipm_solve(h)
+    finally:
+        binding.ipm_destroy(h)
+    ora = oipm.solve(_oracle(w, res["lambda"]), gap_tol=1e-8)
+    assert res["ipm_iters"] == ora["ipm_iters"]
+    assert abs(res["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
+
+
+@pytest.mark.parametrize("dims", [(64, 48), (32, 24, 16)])
+def test_carried_g_beta_matches_exact_residual(dims):
+    """FP64 mode carries G beta along with beta (G x accumulated in PCG) and recomputes it
+    only to confirm the stop test: same optimum, same Newton iterations as recomputing it
+    every iteration, and the reported gap is that of an exact product."""
+    w = _workload(dims, seed=27)
+    out = {}
+    for exact in (0, 1):
+        h = _handle(w, binding.IPM_FP64, gap_tol=1e-9, exact_residual=exact)
+        try:
+            out[exact] = binding.ipm_solve(h)
+        finally:
+            binding.ipm_destroy(h)
+    for r in out.values():
+        assert r["status"] == binding.IPM_OK and r["rel_gap"] <= 1e-9
+    assert out[0]["ipm_iters"] == out[1]["ipm_iters"]
+    assert abs(out[0]["primal"] - out[1]["primal"]) <= 1e-10 * abs(out[1]["primal"])
+    # the carried product saves all but the confirming FP64 products
+    assert out[0]["kkt_products"] < out[1]["kkt_products"]
+    ora = oipm.solve(_oracle(w, out[0]["lambda"]), gap_tol=1e-9, sigma_rule="adaptive", sigma_min=0.03)
+    assert abs(out[0]["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])

@@ -149,3 +149,37 @@ def test_config_1d_workload_converges():
             assert abs(res["beta"][nsc + i]) + abs(res["beta"][nsc + nrep + i]) > prob.lam
             strong += 1
     assert strong >= 4
+
+
+@pytest.mark.parametrize("dims", [(16,), (4, 4, 4)])
+def test_adaptive_centring_unmasked_equals_soft_threshold(dims):
+    """The adaptive centring rule changes the path, not the solution."""
+    rng = np.random.default_rng(31)
+    prob = Problem(dims, np.ones(dims, bool), rng.standard_normal(dims), 1.0)
+    prob.lam = 0.3 * prob.lambda_max()
+    res = ipm.solve(prob, gap_tol=1e-12, sigma_rule="adaptive")
+    assert res["status"] == "converged"
+    assert np.abs(res["beta"] - brute.soft_threshold(prob.c, prob.lam)).max() < 1e-8
+
+
+@pytest.mark.parametrize("dims,seed", [((32,), 19), ((8, 8), 20), ((4, 4, 4), 21)])
+def test_adaptive_centring_masked_against_proximal_gradient(dims, seed):
+    prob = _masked(dims, seed, missing=0.2, lam_rel=0.2)
+    Mp = _dense(prob.A, prob.n)[prob.mask.reshape(-1)]
+    ref = brute.proximal_gradient(Mp, prob.b, prob.lam)
+    # at gaps far below 1e-10 the aggressive centring (sigma down to 0.01) drives
+    # PCG into breakdown on such tiny problems; the rule is for practical tolerances
+    res = ipm.solve(prob, gap_tol=1e-10, sigma_rule="adaptive")
+    assert res["status"] == "converged"
+    assert np.abs(res["beta"] - ref).max() < 1e-5
+    assert abs(res["primal"] - prob.objective(ref)) < 2e-9 * max(1, abs(res["primal"]))
+
+
+def test_adaptive_centring_rule():
+    """sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow); the fixed rule switches at alpha = 0.1."""
+    assert ipm.next_sigma(0.0, "adaptive", 0.1, 0.5, 0.01) == 0.5
+    assert ipm.next_sigma(1.0, "adaptive", 0.1, 0.5, 0.01) == 0.01
+    assert abs(ipm.next_sigma(0.5, "adaptive", 0.1, 0.5, 0.01) - 0.125) < 1e-15
+    assert abs(ipm.next_sigma(0.9, "adaptive", 0.1, 0.5, 0.01) - 0.01) < 1e-15      # 0.001 clamped
+    assert ipm.next_sigma(0.05, "fixed", 0.1, 0.5, 0.01) == 0.5
+    assert ipm.next_sigma(0.5, "fixed", 0.1, 0.5, 0.01) == 0.1

@@ -2,7 +2,7 @@
 
 import numpy as np
 
-from paper_2502_04217_gb300.synth import batch_workloads, lattice_mask, make_problem
+from paper_2502_04217_gb300.synth import batch_workloads, lattice_mask, make_problem, paper_signal
 
 
 def test_config_masks_have_the_stated_missing_fractions():
@@ -35,3 +35,18 @@ def test_sparse_spectrum_is_what_was_planted():
     spec = np.fft.rfftn(w.y, norm="ortho").reshape(-1)
     big = np.flatnonzero(np.abs(spec) > 1e-9)
     assert sorted(big.tolist()) == sorted(int(f) for f in w.freqs)
+
+
+def test_paper_generator():
+    """Sec. 4.1: the separable signal has exactly the frequencies (+-1, +-2, +-3) (four
+    slots of the half spectrum), the noise is U(0, 1), and balls of radius 2 on a
+    period-6 lattice remove 33/216 = 15.3 % of the samples ("about 15 %")."""
+    N = 24
+    spec = np.fft.rfftn(paper_signal(N), norm="ortho")
+    big = {tuple(int(v) for v in k) for k in np.argwhere(np.abs(spec) > 1e-9)}
+    assert big == {(1, 2, 3), (1, N - 2, 3), (N - 1, 2, 3), (N - 1, N - 2, 3)}
+    w = make_problem("paper", dims=(96,))
+    assert w.dims == (96, 96, 96)
+    noise = w.y - paper_signal(96)
+    assert noise.min() >= 0.0 and noise.max() < 1.0 and abs(noise.mean() - 0.5) < 0.01
+    assert abs((1 - w.mask.mean()) - 33 / 216) < 1e-12
