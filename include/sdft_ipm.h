@@ -108,7 +108,8 @@ typedef struct {
                            sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow) from the last
                            step alpha (Mehrotra's (mu_aff / mu)^3 heuristic with the previous
                            step standing in for an affine predictor: one Newton system per
-                           iteration; the first direction uses sigma); 0: sigma, or
+                           iteration; the first direction uses sigma; after a PCG solve
+                           stopped at max_cg the fixed rule applies); 0: sigma, or
                            sigma_slow after a step alpha < 0.1                               */
   double sigma_min;     /* lower clamp of the adaptive rule (default 0.03; at 0.01 the PCG
                            of tiny problems broke down below a 1e-12 gap)                    */
@@ -119,6 +120,11 @@ typedef struct {
                            passed on the carried value; 1: an FP64 product recomputes G beta
                            every IPM iteration (IPM_MIXED always does, its PCG products being
                            FP32)                                                            */
+  double precond_rho;   /* identity scale rho of the preconditioner
+                           P = [rho I + Lambda1, Lambda2; Lambda2, Lambda1] (Sec. 3.5).
+                           1 (default): the paper's P; 0: rho = n / m with m the number of
+                           observed samples (the scaled identity of Fountoulakis et al. that
+                           the paper compares with); any other rho > 0 is used as given      */
 } ipm_options;
 
 typedef struct {

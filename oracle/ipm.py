@@ -19,6 +19,12 @@ Paper passages followed, in the order the method applies them
   P^{-1} = [[Lambda1 D^{-1}, -Lambda2 D^{-1}], [-D^{-1} Lambda2, B^{-1}]],
   B^{-1} = D^{-1} (I + Lambda1).
 * Sec. 3.5 / Sec. 5: conjugate gradients on K with preconditioner P.
+* Sec. 3.5 (the comparison with Fountoulakis et al.): their preconditioner
+  multiplies the identity by a scalar rho = n/m set by the fraction of observed
+  data, P_rho = [[rho I + Lambda1, Lambda2], [Lambda2, Lambda1]]; then
+  D_rho = Lambda1 (rho I + Lambda1) - Lambda2^2 = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2
+  and P_rho^{-1} = [[Lambda1, -Lambda2], [-Lambda2, rho I + Lambda1]] D_rho^{-1}
+  (``precond_rho``; rho = 1 is the paper's P).
 
 Our readings (the paper leaves them to MadNLP or prints them with typos)
 ----------------------------------------------------------------------
@@ -45,6 +51,9 @@ Our readings (the paper leaves them to MadNLP or prints them with typos)
   a second Newton system per iteration; here the previous step stands in for it,
   sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow) for the next direction
   (the first direction uses sigma0), and each iteration solves one system.
+  After a PCG solve that stopped at max_cg (an inexact direction) the fixed rule
+  applies instead: with the aggressive centring, mu then ran to 0 while the gap
+  stalled.
 * Stop when the relative duality gap (``Problem.certificate``) is <= gap_tol.
 * PCG: x0 = 0, stop when sqrt(r^T z) <= cg_tol * sqrt(r0^T z0) (relative,
   the default) or sqrt(r^T z) <= cg_tol (absolute, as the paper's 1e-12 rule),
@@ -67,17 +76,18 @@ def K_apply(G, Sig1, Sig2, p_beta, p_z):
     return G(p_beta) + L1 * p_beta + L2 * p_z, L2 * p_beta + L1 * p_z
 
 
-def P_apply(Sig1, Sig2, p_beta, p_z):
-    """P [p_beta; p_z] with P = [I + Lambda1, Lambda2; Lambda2, Lambda1]."""
+def P_apply(Sig1, Sig2, p_beta, p_z, rho=1.0):
+    """P [p_beta; p_z] with P = [rho I + Lambda1, Lambda2; Lambda2, Lambda1] (rho = 1: the paper's P)."""
     L1, L2 = Sig1 + Sig2, Sig1 - Sig2
-    return p_beta + L1 * p_beta + L2 * p_z, L2 * p_beta + L1 * p_z
+    return rho * p_beta + L1 * p_beta + L2 * p_z, L2 * p_beta + L1 * p_z
 
 
-def Pinv_apply(Sig1, Sig2, r_beta, r_z):
-    """P^{-1} [r_beta; r_z] by the closed form Eq. (invprecond1) with Prop. exprbd."""
+def Pinv_apply(Sig1, Sig2, r_beta, r_z, rho=1.0):
+    """P^{-1} [r_beta; r_z] by the closed form Eq. (invprecond1) with Prop. exprbd
+    (D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2; for P_rho, D = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2)."""
     L1, L2 = Sig1 + Sig2, Sig1 - Sig2
-    D = Sig1 + Sig2 + 4.0 * Sig1 * Sig2
-    Binv = (1.0 + L1) / D
+    D = rho * (Sig1 + Sig2) + 4.0 * Sig1 * Sig2
+    Binv = (rho + L1) / D
     return (L1 / D) * r_beta - (L2 / D) * r_z, -(L2 / D) * r_beta + Binv * r_z
 
 
@@ -176,7 +186,8 @@ def next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min):
 
 
 def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative=True,
-          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.01):
+          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.01,
+          precond_rho=1.0):
     """Run the IPM; returns a dict with the point, counts and the certificate."""
     w = [np.array(v, dtype=np.float64, copy=True) for v in (w0 or starting_point(prob))]
     sigma = sigma0
@@ -197,7 +208,7 @@ def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative
         Sig1, Sig2 = sigmas(w[2], w[4], w[3], w[5])
         rhs = condensed_rhs(res, w)
         (dbeta, dz), ncg, _ = pcg(lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b),
-                                  lambda a, b: Pinv_apply(Sig1, Sig2, a, b),
+                                  lambda a, b: Pinv_apply(Sig1, Sig2, a, b, precond_rho),
                                   rhs, cg_tol, max_cg, cg_relative)
         cg_counts.append(ncg)
         ds1, ds2, dnu1, dnu2 = back_substitute(res, w, dbeta, dz)
@@ -205,7 +216,7 @@ def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative
         alpha = min(1.0, tau * amax)
         for v, d in zip(w, (dbeta, dz, ds1, ds2, dnu1, dnu2)):
             v += alpha * d
-        sigma = next_sigma(alpha, sigma_rule, sigma0, sigma_slow, sigma_min)
+        sigma = next_sigma(alpha, sigma_rule if ncg < max_cg else "fixed", sigma0, sigma_slow, sigma_min)
     P, D, gap = prob.certificate(w[0])
     return dict(status=status, point=w, beta=w[0], primal=P, dual=D, gap=gap,
                 ipm_iters=len(cg_counts), cg_counts=cg_counts)

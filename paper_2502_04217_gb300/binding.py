@@ -29,7 +29,8 @@ class ipm_options(ctypes.Structure):
                 ("lambda_relative", ctypes.c_int), ("cg_chunk", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("tile_e", ctypes.c_int), ("tile_p", ctypes.c_int),
                 ("refine_every", ctypes.c_int), ("tile_engine", ctypes.c_int),
-                ("sigma_rule", ctypes.c_int), ("sigma_min", ctypes.c_double), ("exact_residual", ctypes.c_int)]
+                ("sigma_rule", ctypes.c_int), ("sigma_min", ctypes.c_double), ("exact_residual", ctypes.c_int),
+                ("precond_rho", ctypes.c_double)]
 
 
 class ipm_result(ctypes.Structure):

@@ -119,7 +119,12 @@ __device__ __forceinline__ void k_store(const PassArgs& a, long long g, V w, con
   __stcs(q2 + g, qb);
   __stcs(q2 + a.lay.H + g, qz);
   if (a.gp_out) __stcs(reinterpret_cast<double2*>(a.gp_out) + g, make_double2(o0, o1));
-  if constexpr (PQ) acc += k.pb.x * qb.x + k.pb.y * qb.y + k.pz.x * qz.x + k.pz.y * qz.y;
+  if constexpr (PQ) {       // four FMAs into the running sum (the FP64 pipe bounds this pass)
+    acc = fma(k.pb.x, qb.x, acc);
+    acc = fma(k.pb.y, qb.y, acc);
+    acc = fma(k.pz.x, qz.x, acc);
+    acc = fma(k.pz.y, qz.y, acc);
+  }
 }
 
 // Store the complex value of slot g for the last pass (one slot at a time:

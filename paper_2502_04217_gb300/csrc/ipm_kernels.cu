@@ -190,8 +190,14 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
 
 // Barrier diagonals, preconditioner coefficients, condensed right-hand side and
 // PCG start (x = 0, r = rhs, z = P^{-1} r, p = z, rho = r^T z).
+// rho > 0: the identity block of P is scaled by rho; rho <= 0: rho = n / (observed samples)
+__device__ __forceinline__ double precond_scale(double rho, const Layout& lay, const DevScalars* sc) {
+  return rho > 0.0 ? rho : (double)lay.n / fmax(sc->nobs, 1.0);
+}
+
 __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
-                                                           DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop) {
+                                                           DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop,
+                                                           double rho_opt) {
   __shared__ double scratch[32];
   count_launch(sc);
   if (sc->ipm_done || (sc->incr && sc->exact_now)) {   // after the stop test, or before an exact re-test: no PCG
@@ -201,6 +207,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
   const bool incr = sc->incr;
   const long long n2 = 2 * lay.H;
   const double lam = sc->lambda, smu = sc->sigma * sc->mu;
+  const double prho = precond_scale(rho_opt, lay, sc);  // identity scale of P (1: the paper's P)
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
@@ -220,10 +227,10 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
       rc = -r_z - A1 - A2;
       l1 = S1 + S2;
       l2 = S1 - S2;
-      const double iD = rcp1(fma(4.0 * S1, S2, l1));            // D = Sigma1 + Sigma2 + 4 Sigma1 Sigma2
+      const double iD = rcp1(fma(4.0 * S1, S2, prho * l1));     // D = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2
       pa = l1 * iD;
       pb = l2 * iD;
-      pc = (1.0 + l1) * iD;
+      pc = (prho + l1) * iD;
       zb = pa * rb - pb * rc;
       zz = -pb * rb + pc * rc;
     }
@@ -255,19 +262,20 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
 // Preconditioner coefficients only (for precond_apply / kkt_apply on a given Sigma)
 __global__ void __launch_bounds__(kThreads) sigma_coef_kernel(Layout lay, const double* s1, const double* nu1, const double* s2,
                                                               const double* nu2, double* lam1, double* lam2, double* pa,
-                                                              double* pb, double* pc, DevScalars* sc) {
+                                                              double* pb, double* pc, DevScalars* sc, double rho_opt) {
   count_launch(sc);
   const long long n2 = 2 * lay.H;
+  const double prho = precond_scale(rho_opt, lay, sc);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     double l1 = 0, l2 = 0, a = 0, b = 0, c = 0;
     if (!is_ghost(lay, i)) {
       const double S1 = nu1[i] / s1[i], S2 = nu2[i] / s2[i];
       l1 = S1 + S2;
       l2 = S1 - S2;
-      const double iD = 1.0 / (S1 + S2 + 4.0 * S1 * S2);
+      const double iD = 1.0 / (prho * (S1 + S2) + 4.0 * S1 * S2);
       a = l1 * iD;
       b = l2 * iD;
-      c = (1.0 + l1) * iD;
+      c = (prho + l1) * iD;
     }
     lam1[i] = l1; lam2[i] = l2; pa[i] = a; pb[i] = b; pc[i] = c;
   }
@@ -432,8 +440,11 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
   }
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
     sc->mu = v[0] / (2.0 * (double)lay.n);
-    if (sigma_rule == 1) {
-      // adaptive centring: (1 - alpha)^3 stands in for Mehrotra's (mu_aff / mu)^3
+    if (sigma_rule == 1 && sc->cg_status != 1) {
+      // adaptive centring: (1 - alpha)^3 stands in for Mehrotra's (mu_aff / mu)^3;
+      // after a PCG solve stopped at max_cg (an inexact direction) the fixed rule
+      // below keeps the iterate centred (aggressive centring then drove mu to 0
+      // while the gap stalled)
       const double t = 1.0 - alpha;
       sc->sigma = fmin(sigma_slow, fmax(sigma_min, t * t * t));
     } else {
@@ -554,14 +565,15 @@ cudaError_t k_certificate(const Layout& lay, const double* beta, const double* G
   return cudaGetLastError();
 }
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, cudaStream_t st) {
+                      LoopCtl loop, double rho, cudaStream_t st) {
   prepare_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, cg_tol, cg_relative,
-                                                           loop);
+                                                           loop, rho);
   return cudaGetLastError();
 }
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
-                         IpmVectors w, DevScalars* sc, cudaStream_t st) {
-  sigma_coef_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc, sc);
+                         IpmVectors w, DevScalars* sc, double rho, cudaStream_t st) {
+  sigma_coef_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc, sc,
+                                                              rho);
   return cudaGetLastError();
 }
 cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st) {

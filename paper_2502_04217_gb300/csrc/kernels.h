@@ -53,9 +53,9 @@ cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, do
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
                           DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st);
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, cudaStream_t st);
+                      LoopCtl loop, double rho, cudaStream_t st);
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
-                         IpmVectors w, DevScalars* sc, cudaStream_t st);
+                         IpmVectors w, DevScalars* sc, double rho, cudaStream_t st);
 cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st);
 cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, int refine_every,
                          LoopCtl loop, cudaStream_t st);

@@ -78,3 +78,23 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.kkt_apply(None, None, None) == binding.IPM_ERR_ARG
     assert lib.precond_apply(None, None, None) == binding.IPM_ERR_ARG
     lib.ipm_destroy(None)
+
+
+def test_default_options_of_the_solver_variants(lib):
+    o = binding.default_options()
+    assert o.tile_engine == 0 and o.sigma_rule == 1 and o.sigma_min == 0.03
+    assert o.exact_residual == 0 and o.precond_rho == 1.0
+
+
+@pytest.mark.parametrize("field,value", [("tile_engine", 3), ("sigma_rule", 2), ("sigma_min", 0.0),
+                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0),
+                                         ("precond_rho", float("inf"))])
+def test_create_rejects_bad_variant_options(lib, field, value):
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * 1)(8)
+    dummy = (ctypes.c_double * 8)()
+    o = binding.default_options(**{field: value})
+    st = lib.ipm_create(ctypes.byref(h), 1, d, ctypes.cast(dummy, ctypes.c_void_p),
+                        ctypes.cast(dummy, ctypes.c_void_p), 1.0, ctypes.byref(o), None)
+    assert st == binding.IPM_ERR_ARG and field in binding.ipm_last_error(None)
+    assert h.value is None

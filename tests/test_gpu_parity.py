@@ -467,3 +467,64 @@ def test_carried_g_beta_matches_exact_residual(dims):
     assert out[0]["kkt_products"] < out[1]["kkt_products"]
     ora = oipm.solve(_oracle(w, out[0]["lambda"]), gap_tol=1e-9, sigma_rule="adaptive", sigma_min=0.03)
     assert abs(out[0]["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
+
+
+@pytest.mark.parametrize("rho", [0.0, 2.5])
+def test_scaled_identity_preconditioner_matches_oracle(rho):
+    """precond_rho: P_rho^{-1} against the oracle's closed form (rho = 0: n / observed),
+    and a solve with it reaches the same optimum as the paper's P."""
+    dims = (32, 24, 16)
+    w = _workload(dims, seed=28)
+    n = int(np.prod(dims))
+    r = rho if rho > 0 else n / float(w.mask.sum())
+    h = _handle(w, binding.IPM_FP64, gap_tol=1e-9, precond_rho=rho)
+    try:
+        rng = np.random.default_rng(29)
+        s1, nu1, s2, nu2 = _interior(n, rng)
+        binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+        S1, S2 = oipm.sigmas(s1, nu1, s2, nu2)
+        pb, pz = rng.standard_normal(n), rng.standard_normal(n)
+        p = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
+        z = torch.empty_like(p)
+        binding.precond_apply(h, p, z)
+        zb, zz = oipm.Pinv_apply(S1, S2, pb, pz, r)
+        H2 = p.numel() // 2
+        zs = np.abs(np.concatenate([zb, zz])).max()
+        assert np.abs(lib_to_half(h, z[:H2]) - oracle_to_half(zb, dims)).max() < 1e-13 * max(1, zs)
+        assert np.abs(lib_to_half(h, z[H2:]) - oracle_to_half(zz, dims)).max() < 1e-13 * max(1, zs)
+        res = binding.ipm_solve(h)
+    finally:
+        binding.ipm_destroy(h)
+    ora = oipm.solve(_oracle(w, res["lambda"]), gap_tol=1e-9, sigma_rule="adaptive", sigma_min=0.03)
+    assert res["status"] == binding.IPM_OK
+    assert abs(res["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
+
+
+_TILE_PROBE = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+from paper_2502_04217_gb300 import binding
+from paper_2502_04217_gb300.synth import make_problem
+w = make_problem("custom", dims=(64, 32, 48), missing=0.1, seed=30)
+h = binding.ipm_create(w.dims, w.mask, w.y, 0.1, binding.default_options(lambda_relative=1))
+print(json.dumps(binding.ipm_describe(h)))
+binding.ipm_destroy(h)
+"""
+
+
+def test_tile_cache_file_reproduces_tiles(tmp_path):
+    """SDFT_TUNE_CACHE: the first process appends its tuned tiles, a second one reads
+    them back and launches exactly the same tiles without timing anything."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SDFT_TUNE_CACHE=str(tmp_path / "tiles.txt"))
+    run = lambda: subprocess.run([sys.executable, "-c", _TILE_PROBE, root], env=env, capture_output=True, text=True,
+                                 check=True).stdout.strip().splitlines()[-1]
+    first = run()
+    lines = (tmp_path / "tiles.txt").read_text().splitlines()
+    assert len(lines) >= 6 and all(len(ln.split()) == 9 for ln in lines)
+    assert run() == first
+    assert (tmp_path / "tiles.txt").read_text().splitlines() == lines      # nothing re-tuned

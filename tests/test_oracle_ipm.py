@@ -183,3 +183,14 @@ def test_adaptive_centring_rule():
     assert abs(ipm.next_sigma(0.9, "adaptive", 0.1, 0.5, 0.01) - 0.01) < 1e-15      # 0.001 clamped
     assert ipm.next_sigma(0.05, "fixed", 0.1, 0.5, 0.01) == 0.5
     assert ipm.next_sigma(0.5, "fixed", 0.1, 0.5, 0.01) == 0.1
+
+
+def test_scaled_identity_preconditioner_same_solution():
+    """The preconditioner changes the PCG path only: P_rho with rho = n/m reaches the
+    same optimum as the paper's P."""
+    prob = _masked((8, 8), 20, missing=0.2, lam_rel=0.2)
+    m = int(prob.mask.sum())
+    a = ipm.solve(prob, gap_tol=1e-12)
+    b = ipm.solve(prob, gap_tol=1e-12, precond_rho=prob.n / m)
+    assert b["status"] == "converged"
+    assert np.abs(a["beta"] - b["beta"]).max() < 1e-7

@@ -188,3 +188,22 @@ def test_pcg_solves_masked_system():
     x, it, _ = ipm.pcg(lambda a, b: ipm.K_apply(prob.G, S1, S2, a, b),
                        lambda a, b: ipm.Pinv_apply(S1, S2, a, b), tuple(np.split(rhs, 2)), 1e-13, 500)
     assert np.abs(np.concatenate(x) - np.linalg.solve(K, rhs)).max() < 1e-10
+
+
+@pytest.mark.parametrize("rho", [0.5, 1.25, 4.0])
+def test_scaled_identity_preconditioner_closed_form(rho):
+    """P_rho = [rho I + Lambda1, Lambda2; Lambda2, Lambda1] (the scaled identity the paper
+    compares with, Sec. 3.5): closed-form inverse against a dense inverse, and
+    D_rho = Lambda1 (rho + Lambda1) - Lambda2^2 = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2."""
+    rng = np.random.default_rng(40)
+    n = 7
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    L1, L2 = S1 + S2, S1 - S2
+    P = np.block([[np.diag(rho + L1), np.diag(L2)], [np.diag(L2), np.diag(L1)]])
+    Pd = _dense(lambda e: np.concatenate(ipm.P_apply(S1, S2, e[:n], e[n:], rho)), 2 * n)
+    assert np.abs(Pd - P).max() < 1e-14 * np.abs(P).max()
+    Pinv = _dense(lambda e: np.concatenate(ipm.Pinv_apply(S1, S2, e[:n], e[n:], rho)), 2 * n)
+    assert np.abs(Pinv - np.linalg.inv(P)).max() < 1e-12 * np.abs(np.linalg.inv(P)).max()
+    D = L1 * (rho + L1) - L2 ** 2
+    assert np.abs(D - (rho * (S1 + S2) + 4 * S1 * S2)).max() < 1e-12 * D.max()
