@@ -23,8 +23,9 @@
  *  - The library never frees caller memory; caller buffers are copied where
  *    stated, and never retained after the call returns.
  *  - Grids are row-major with the LAST axis contiguous; every extent must be
- *    even (Sec. 3 treats the even case), of the form 2^a 3^b with b <= 1, and
- *    at most 512.
+ *    even (Sec. 3 treats the even case), of the form 2^a 3^b 5^c 7^d with
+ *    b, c, d <= 1 (the FFT's radices: 2, 4, 8, 16 and one stage each of 3, 5, 7),
+ *    and at most 1024 (gapply_noalloc: 2^a 3^b, at most 512).
  *  - "beta layout": vectors indexed like beta are held as 2H doubles, where
  *    H = N_0 ... N_{d-2} (N_{d-1}/2 + 1) is the number of half-spectrum slots.
  *    Slot s carries two doubles; coordinates that are not LASSO variables
@@ -125,6 +126,11 @@ typedef struct {
                            1 (default): the paper's P; 0: rho = n / m with m the number of
                            observed samples (the scaled identity of Fountoulakis et al. that
                            the paper compares with); any other rho > 0 is used as given      */
+  int pdl;              /* 1 (default): the kernels of a solve (and of gapply / kkt_apply) are
+                           launched with programmatic dependent launch: each may start while
+                           its predecessor drains and waits on the device until that
+                           predecessor has completed (same results, shorter gaps between the
+                           many small kernels of a solve); 0: plain stream order            */
 } ipm_options;
 
 typedef struct {

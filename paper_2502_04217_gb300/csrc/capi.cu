@@ -19,7 +19,19 @@
 
 using namespace sdft;
 
+namespace sdft {
+thread_local bool g_pdl = false;
+}
+
 namespace {
+
+// Sets programmatic dependent launch for the kernels this thread queues while
+// the guard lives (solve loops and operator calls of a handle with opt.pdl).
+struct PdlScope {
+  bool saved;
+  explicit PdlScope(bool on) : saved(g_pdl) { g_pdl = on; }
+  ~PdlScope() { g_pdl = saved; }
+};
 
 thread_local std::string g_create_error;
 
@@ -47,27 +59,33 @@ struct ProfEntry {
   cudaEvent_t a, b;
 };
 
+// Supported transform lengths: 2^a 3^b 5^c 7^d with b, c, d <= 1.
 bool factor_ok(int L) {
   int m = L;
   while (m % 2 == 0) m /= 2;
-  if (m % 3 == 0) m /= 3;
+  for (int q : {3, 5, 7})
+    if (m % q == 0) m /= q;
   return m == 1;
 }
 
 // Radices for length L: with element budget E per thread, 16s (E = 16), then 8s
-// (E divisible by 8), then 4s (E divisible by 4), then 2s, and a single 3 last
-// when L has a factor 3.
+// (E divisible by 8), then 4s (E divisible by 4), then 2s, and last a single 3,
+// 5 and 7 for the odd factors of L (in that order: every stage before the 5 and
+// the 7 then has a power-of-two Ns).
 FftPlan make_plan(int L, int E) {
   FftPlan p{};
   p.L = L;
   int m = L;
-  bool three = (m % 3 == 0);
-  if (three) m /= 3;
+  bool odd[3] = {false, false, false};
+  const int q[3] = {3, 5, 7};
+  for (int i = 0; i < 3; ++i)
+    if (m % q[i] == 0) { odd[i] = true; m /= q[i]; }
   while (E % 16 == 0 && m % 16 == 0) { p.radix[p.nst++] = 16; m /= 16; }
   while (E % 8 == 0 && m % 8 == 0) { p.radix[p.nst++] = 8; m /= 8; }
   while (E % 4 == 0 && m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
-  if (three) p.radix[p.nst++] = 3;
+  for (int i = 0; i < 3; ++i)
+    if (odd[i]) p.radix[p.nst++] = q[i];
   return p;
 }
 
@@ -663,6 +681,7 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (o.sigma_rule < 0 || o.sigma_rule > 1) return fail_arg(h, "sigma_rule must be 0 or 1");
   if (o.exact_residual < 0 || o.exact_residual > 1) return fail_arg(h, "exact_residual must be 0 or 1");
   if (!(o.precond_rho >= 0.0) || !std::isfinite(o.precond_rho)) return fail_arg(h, "precond_rho must be >= 0 and finite");
+  if (o.pdl < 0 || o.pdl > 1) return fail_arg(h, "pdl must be 0 or 1");
   if (o.sigma_rule == 1 && !(o.sigma_min > 0 && o.sigma_min <= o.sigma_slow))
     return fail_arg(h, "sigma_min must lie in (0, sigma_slow]");
   if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
@@ -697,6 +716,7 @@ void ipm_default_options(ipm_options* o) {
   o->sigma_min = 0.03;
   o->exact_residual = 0;
   o->precond_rho = 1.0;
+  o->pdl = 1;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -706,8 +726,8 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   *out = nullptr;
   if (ndim < 1 || ndim > 3 || !dims) return fail_arg(nullptr, "ndim must be 1, 2 or 3");
   for (int i = 0; i < ndim; ++i) {
-    if (dims[i] < 2 || dims[i] % 2 || dims[i] > 512 || !factor_ok((int)dims[i]))
-      return fail_arg(nullptr, "every extent must be even, of the form 2^a 3^b (b <= 1), and at most 512");
+    if (dims[i] < 2 || dims[i] % 2 || dims[i] > 1024 || !factor_ok((int)dims[i]))
+      return fail_arg(nullptr, "every extent must be even, of the form 2^a 3^b 5^c 7^d (b, c, d <= 1), and at most 1024");
   }
   ipm_options o;
   ipm_default_options(&o);
@@ -1015,6 +1035,7 @@ ipm_status ipm_solve(sdft_ipm* h, ipm_result* res) {
   const ipm_options& o = h->opt;
   Reduce red{h->d_partials, h->d_counter};
   ipm_status s;
+  PdlScope pdl(o.pdl != 0);
   {
     ProfScope ps(h, 4);
     if (h->point_set) CK(k_mu(L, h->w, red, h->d_sc, o.sigma, incremental_gb(h), h->st));
@@ -1052,6 +1073,7 @@ ipm_status gapply(sdft_ipm* h, const double* p, double* q) {
   GSpec g;
   g.src = p;
   g.dst = q;
+  PdlScope pdl(h->opt.pdl != 0);
   ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, g);
   if (s != IPM_OK) return s;
   CK(cudaStreamSynchronize(h->st));
@@ -1068,6 +1090,7 @@ ipm_status kkt_apply(sdft_ipm* h, const double* p, double* q) {
   g.mapout = MAPOUT_K;
   g.p_in = p;
   g.q_out = q;
+  PdlScope pdl(h->opt.pdl != 0);
   ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, g);
   if (s != IPM_OK) return s;
   CK(cudaStreamSynchronize(h->st));
@@ -1278,6 +1301,7 @@ ipm_status build_batch_graph(sdft_ipm_batch* b) {
   for (int i = 0; i < count && s == IPM_OK; ++i) {
     sdft_ipm* h = b->members[i];
     CKB(cudaStreamWaitEvent(h->cap[0], b->ev[count], 0));
+    PdlScope pdl(h->opt.pdl != 0);
     {
       StreamSwap sw(h, h->cap[0]);
       Reduce red{h->d_partials, h->d_counter};

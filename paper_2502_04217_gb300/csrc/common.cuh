@@ -8,6 +8,15 @@
 
 namespace sdft {
 
+// Programmatic dependent launch (sm_90+).  Kernels of the solve loop start with
+// pdl_wait(): when launched with programmatic stream serialization it blocks
+// until the preceding grid has completed and its memory is visible (without
+// that attribute it returns at once), so a kernel may be launched while its
+// predecessor drains.  pdl_launch() after a block's main work lets the next
+// kernel of the stream begin launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // ---------------------------------------------------------------------------
 // Complex helpers (double2 / float2 as interleaved re, im)
 // ---------------------------------------------------------------------------

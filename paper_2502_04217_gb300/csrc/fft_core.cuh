@@ -7,7 +7,8 @@
 // warp, which walk p fastest, touch consecutive words.
 //
 // Each thread owns E complex values per stage (E/R butterflies of radix R;
-// R in {2, 3, 4, 8, 16}, the radix-16 butterfly done as 4 x 4 in registers).
+// R in {2, 3, 4, 8, 16}, the radix-16 butterfly done as 4 x 4 in registers;
+// radices 5 and 7, which need not divide E, take ceil(E/R) guarded butterflies).
 // A stage reads all its inputs into registers, synchronises, then writes its
 // outputs into the same buffer (Stockham autosort, decimation in time):
 //     for butterfly j of a stage of radix R after Ns = R_1 ... R_{s-1}:
@@ -119,11 +120,60 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16(V* a) {
   }
 }
 
+// Odd prime R (5, 7): pairing x_n with x_{R-n}, a_n = x_n + x_{R-n}, b_n = x_n - x_{R-n},
+// every output pair k, R-k shares A_k = x_0 + sum_n a_n cos(2 pi n k / R) and
+// B_k = sum_n b_n sin(2 pi n k / R): forward X_k = A_k - i B_k, X_{R-k} = A_k + i B_k
+// (inverse: the signs of i B_k swap), X_0 = x_0 + sum_n a_n.
+// cos(2 pi m / R) and sin(2 pi m / R) for 0 <= m <= (R - 1) / 2, R in {5, 7}
+__host__ __device__ constexpr double odd_cos(int R, int m) {
+  return R == 5 ? (m == 0 ? 1.0 : m == 1 ? 0.30901699437494742410 : -0.80901699437494742410)
+                : (m == 0 ? 1.0 : m == 1 ? 0.62348980185873353053 : m == 2 ? -0.22252093395631440429
+                                                                           : -0.90096886790241912624);
+}
+__host__ __device__ constexpr double odd_sin(int R, int m) {
+  return R == 5 ? (m == 0 ? 0.0 : m == 1 ? 0.95105651629515357212 : 0.58778525229247312917)
+                : (m == 0 ? 0.0 : m == 1 ? 0.78183148246802980871 : m == 2 ? 0.97492791218182360702
+                                                                           : 0.43388373911755812048);
+}
+
+template <int R, bool INV, typename V> __device__ __forceinline__ void dft_odd(V* a) {
+  using T = decltype(V::x);
+  constexpr int Q = (R - 1) / 2;
+  V sum[Q + 1], dif[Q + 1];
+  V x0 = a[0];
+  V X0 = x0;
+#pragma unroll
+  for (int n = 1; n <= Q; ++n) {
+    sum[n] = cadd(a[n], a[R - n]);
+    dif[n] = csub(a[n], a[R - n]);
+    X0 = cadd(X0, sum[n]);
+  }
+#pragma unroll
+  for (int k = 1; k <= Q; ++k) {
+    V A = x0, B = cmake<V>((T)0, (T)0);
+#pragma unroll
+    for (int n = 1; n <= Q; ++n) {
+      // cos / sin of 2 pi n k / R from the table of the first Q + 1 multiples
+      const int m = (n * k) % R;
+      const int mm = m <= Q ? m : R - m;
+      const T c = (T)odd_cos(R, mm);
+      const T sn = m <= Q ? (T)odd_sin(R, mm) : -(T)odd_sin(R, mm);
+      A = cmake<V>(A.x + c * sum[n].x, A.y + c * sum[n].y);
+      B = cmake<V>(B.x + sn * dif[n].x, B.y + sn * dif[n].y);
+    }
+    const V iB = cmul_i(B);
+    a[k] = INV ? cadd(A, iB) : csub(A, iB);
+    a[R - k] = INV ? csub(A, iB) : cadd(A, iB);
+  }
+  a[0] = X0;
+}
+
 template <int R, bool INV, typename V> __device__ __forceinline__ void dft_r(V* a) {
   if constexpr (R == 2) dft2<INV>(a);
   else if constexpr (R == 3) dft3<INV>(a);
   else if constexpr (R == 4) dft4<INV>(a);
   else if constexpr (R == 8) dft8<INV>(a);
+  else if constexpr (R == 5 || R == 7) dft_odd<R, INV>(a);
   else dft16<INV>(a);
 }
 
@@ -169,13 +219,69 @@ __device__ __forceinline__ void fft_stage(V* buf, int L, int lgNs, int lgP, int 
   __syncthreads();
 }
 
+// One stage of an odd radix R in {5, 7} that need not divide E: the P L / R
+// butterflies w = tid + b nwork (b < ceil(E / R)) are spread over the working
+// threads with a guard, and Ns (the product of the earlier radices) may be any
+// integer.  Same formulas as fft_stage.
+template <int E, int R, bool INV, typename V>
+__device__ __forceinline__ void fft_stage_odd(V* buf, int L, int Ns, int lgP, int PP, const V* __restrict__ tw,
+                                              int tid, int nwork) {
+  constexpr int B = (E + R - 1) / R;
+  const int LR = L / R;
+  const int twstride = L / (Ns * R);
+  const int nbfly = (LR << lgP);
+  V a[B][R];
+  const bool active = tid < nwork;
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int w = tid + b * nwork;
+      if (w < nbfly) {
+        const int p = w & ((1 << lgP) - 1), j = w >> lgP, k = j % Ns;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          V v = buf[(j + r * LR) * PP + p];
+          if (r > 0 && Ns > 1) {
+            V t = __ldg(&tw[k * r * twstride]);
+            v = INV ? cmulconj(v, t) : cmul(v, t);
+          }
+          a[b][r] = v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int w = tid + b * nwork;
+      if (w < nbfly) {
+        const int p = w & ((1 << lgP) - 1), j = w >> lgP, k = j % Ns;
+        dft_r<R, INV>(a[b]);
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(base + r * Ns) * PP + p] = a[b][r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // Full transform of the P pencils held in buf (length plan.L each), in place.
-template <int E, bool INV, typename V>
+// ODD: the plan may hold radix-5 / radix-7 stages (a separate instantiation, so
+// that the registers of those stages do not weigh on the other kernels).
+template <int E, bool INV, bool ODD, typename V>
 __device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, int PP, const V* __restrict__ tw,
                                          int tid, int nwork) {
-  int lgNs = 0;
+  int lgNs = 0, Ns = 1;
   for (int s = 0; s < plan.nst; ++s) {
     const int R = plan.radix[s];
+    if constexpr (ODD) {
+      // radices 5 and 7 come last (after the powers of two and a 3)
+      if (R == 5) fft_stage_odd<E, 5, INV>(buf, plan.L, Ns, lgP, PP, tw, tid, nwork);
+      if (R == 7) fft_stage_odd<E, 7, INV>(buf, plan.L, Ns, lgP, PP, tw, tid, nwork);
+    }
+    Ns *= R;
     if constexpr (E % 16 == 0) {
       if (R == 16) fft_stage<E, 16, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
     }
@@ -189,7 +295,7 @@ __device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, i
     if constexpr (E % 3 == 0) {
       if (R == 3) fft_stage<E, 3, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
     }
-    lgNs += (R == 16) ? 4 : (R == 8) ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));   // radix 3 is last
+    lgNs += (R == 16) ? 4 : (R == 8) ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));   // odd radices come last
   }
 }
 
@@ -261,12 +367,12 @@ __device__ __forceinline__ void fft_stages_c(V* buf, int lgP, int PP, const V* _
 }
 
 // Full transform with the length fixed at compile time (LC > 0) or taken from
-// the plan (LC = 0).
+// the plan (LC = 0; LC = -1 for plans with a radix-5 or radix-7 stage).
 template <int E, bool INV, int LC, typename V>
 __device__ __forceinline__ void fft_tile_l(V* buf, const FftPlan& plan, int lgP, int PP, const V* __restrict__ tw,
                                            int tid, int nwork) {
   if constexpr (LC > 0) fft_stages_c<E, INV, LC, 0, 0>(buf, lgP, PP, tw, tid, nwork);
-  else fft_tile<E, INV>(buf, plan, lgP, PP, tw, tid, nwork);
+  else fft_tile<E, INV, (LC < 0)>(buf, plan, lgP, PP, tw, tid, nwork);
 }
 
 }  // namespace sdft

@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) row_pass_kernel(PassAr
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
+  pdl_wait();
   count_launch(a.sc);
   if (pass_skipped(a)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
@@ -289,6 +290,7 @@ template <typename T, int E, bool INV, int LC>
 __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) col_pass_kernel(PassArgs a) {
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   count_launch(a.sc);
   if (pass_skipped(a)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
@@ -334,6 +336,7 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
+  pdl_wait();
   count_launch(a.sc);
   if (pass_skipped(a)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
@@ -463,6 +466,7 @@ __global__ void __launch_bounds__(256) row_reg_kernel(PassArgs a) {
   constexpr int TT = L / E, LP = L + L / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
+  pdl_wait();
   count_launch(a.sc);
   if (pass_skipped(a)) return;
   const int tid = threadIdx.x, t = tid % TT, p = tid / TT;
@@ -490,6 +494,7 @@ __global__ void __launch_bounds__(256) col_reg_kernel(PassArgs a) {
   using V = typename cvec<T>::type;
   constexpr int TT = L / E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   count_launch(a.sc);
   if (pass_skipped(a)) return;
   const int lgP = a.lgP, tid = threadIdx.x, p = tid & ((1 << lgP) - 1), t = tid >> lgP;
@@ -524,6 +529,7 @@ __global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
   constexpr int TT = H / E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
+  pdl_wait();
   count_launch(a.sc);
   if (pass_skipped(a)) return;
   const int lgP = a.lgP, tid = threadIdx.x, p = tid & ((1 << lgP) - 1), t = tid >> lgP;
@@ -622,8 +628,7 @@ cudaError_t launch_reg_l(int kind, bool inv, const PassArgs& a, int threads, siz
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fn<<<grid, threads, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(fn, grid, dim3(threads), smem, st, a);
 }
 
 // Register engine: E = 16 and L (for the middle pass h = Nl / 2) in {32, ..., 512}.
@@ -649,14 +654,15 @@ cudaError_t launch_typed(int kind, bool inv, const PassArgs& a, int threads, siz
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fn<<<grid, threads, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(fn, grid, dim3(threads), smem, st, a);
 }
 
 // Power-of-two lengths 128, 256 and 512 run kernels with the length (and so
 // the whole stage schedule) fixed at compile time.
 template <typename T, int E>
 cudaError_t launch_l(int kind, bool inv, const PassArgs& a, int threads, size_t smem, dim3 grid, cudaStream_t st) {
+  for (int s = 0; s < a.plan.nst; ++s)
+    if (a.plan.radix[s] == 5 || a.plan.radix[s] == 7) return launch_typed<T, E, -1>(kind, inv, a, threads, smem, grid, st);
   if constexpr (E == 4 || E == 8 || E == 16) {
     switch (a.plan.L) {
       case 128: return launch_typed<T, E, 128>(kind, inv, a, threads, smem, grid, st);

@@ -95,6 +95,26 @@ struct PassArgs {
   int reg;               // 1: register-engine kernels (fft_reg.cuh), E = 16
 };
 
+// Launch with programmatic stream serialization while g_pdl is set (by the
+// solve and operator entry points of the calling thread); every kernel launched
+// through here starts with pdl_wait().
+extern thread_local bool g_pdl;
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fn, static_cast<KArgs>(args)...);
+}
+
 // Launchers (fft_passes.cu).  `pass_kind`: 0 row, 1 column, 2 middle.
 cudaError_t launch_pass(int pass_kind, bool inv, bool fp32, int E, const PassArgs& a, int threads,
                         size_t smem, dim3 grid, cudaStream_t st);

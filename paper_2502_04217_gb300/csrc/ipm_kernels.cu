@@ -40,6 +40,7 @@ __device__ __forceinline__ void set_cond(const LoopCtl& c, unsigned v) {
 
 __global__ void __launch_bounds__(kThreads) pack_mask_kernel(const uint8_t* __restrict__ mask, uint32_t* __restrict__ words,
                                                              int Nl, int M, DevScalars* sc) {
+  pdl_wait();
   count_launch(sc);
   // one thread per output word: 32 consecutive samples of one row x'
   const long long nw = (long long)((Nl + 31) / 32) * M;
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(kThreads) pack_mask_kernel(const uint8_t* __re
 __global__ void __launch_bounds__(kThreads) observed_norm_kernel(const double* __restrict__ y, const uint8_t* __restrict__ mask,
                                                                  long long n, double* partials, unsigned* counter,
                                                                  DevScalars* sc) {
+  pdl_wait();
   __shared__ double scratch[64];
   count_launch(sc);
   double v[2] = {0.0, 0.0};
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(kThreads) observed_norm_kernel(const double* _
 // ||c||_inf for lambda_max; sets lambda (relative or absolute)
 __global__ void __launch_bounds__(kThreads) cmax_kernel(const double* __restrict__ c, long long n2, double lam_in, int relative,
                                                         double* partials, unsigned* counter, DevScalars* sc) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   double v[1] = {0.0};
@@ -106,6 +109,7 @@ __device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double 
 __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double* beta, double* z, double* s1, double* s2,
                                                               double* nu1, double* nu2, double* partials, unsigned* counter,
                                                               DevScalars* sc, double sigma0, int incr) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   const double zeta = fmax(1.0, sc->cmax), hl = 0.5 * sc->lambda;
@@ -129,6 +133,7 @@ __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double
 // mu = (nu1^T s1 + nu2^T s2) / 2n at a given point (after ipm_set_point); control reset
 __global__ void __launch_bounds__(kThreads) mu_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                       DevScalars* sc, double sigma0, int incr) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   double v[1] = {0.0};
@@ -150,6 +155,7 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
                                                                const double* __restrict__ Gb, const double* __restrict__ c,
                                                                double* partials, unsigned* counter, DevScalars* sc,
                                                                double gap_tol, int max_ipm, LoopCtl ipm_loop) {
+  pdl_wait();
   __shared__ double scratch[4 * 32];
   count_launch(sc);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -198,6 +204,7 @@ __device__ __forceinline__ double precond_scale(double rho, const Layout& lay, c
 __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                            DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop,
                                                            double rho_opt) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   if (sc->ipm_done || (sc->incr && sc->exact_now)) {   // after the stop test, or before an exact re-test: no PCG
@@ -263,6 +270,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
 __global__ void __launch_bounds__(kThreads) sigma_coef_kernel(Layout lay, const double* s1, const double* nu1, const double* s2,
                                                               const double* nu2, double* lam1, double* lam2, double* pa,
                                                               double* pb, double* pc, DevScalars* sc, double rho_opt) {
+  pdl_wait();
   count_launch(sc);
   const long long n2 = 2 * lay.H;
   const double prho = precond_scale(rho_opt, lay, sc);
@@ -285,6 +293,7 @@ __global__ void __launch_bounds__(kThreads) sigma_coef_kernel(Layout lay, const 
 __global__ void __launch_bounds__(kThreads) precond_kernel(long long n2, const double* __restrict__ pa, const double* __restrict__ pb,
                                                            const double* __restrict__ pc, const double* __restrict__ r,
                                                            double* __restrict__ z, DevScalars* sc) {
+  pdl_wait();
   count_launch(sc);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     const double rb = r[i], rz = r[n2 + i], a = pa[i], b = pb[i], c = pc[i];
@@ -297,6 +306,7 @@ __global__ void __launch_bounds__(kThreads) precond_kernel(long long n2, const d
 // beta_cg = rho'/rho, stop test; the PCG loop condition is !cg_done.
 __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
                                                               DevScalars* sc, int max_cg, int refine_every, LoopCtl cg_loop) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   if (sc->cg_done) {
@@ -348,6 +358,7 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmV
 // a converged FP32 phase, PCG stops only if the FP64 residual passes the test.
 __global__ void __launch_bounds__(kThreads) refine_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
                                                           DevScalars* sc, LoopCtl cg_loop) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   if (!sc->refine_now) return;
@@ -390,6 +401,7 @@ __device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long 
 // Largest step keeping (s, nu) >= 0; alpha = min(1, tau * alpha_max)
 __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                                DevScalars* sc, double tau) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   if (sc->ipm_done || (sc->incr && sc->exact_now)) return;
@@ -419,6 +431,7 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
 __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                                DevScalars* sc, double sigma0, double sigma_slow,
                                                                int sigma_rule, double sigma_min) {
+  pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
   if (sc->ipm_done || (sc->incr && sc->exact_now)) return;
@@ -462,6 +475,7 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
 // unpack: v = B^H beta restricted to the half spectrum, twins filled with conj(rep).
 __global__ void __launch_bounds__(kThreads) unpack_kernel(Layout lay, const double* __restrict__ beta, double* __restrict__ vh,
                                                           DevScalars* sc) {
+  pdl_wait();
   count_launch(sc);
   const long long H = lay.H;
   const double rh = 0.70710678118654752440;
@@ -494,6 +508,7 @@ __global__ void __launch_bounds__(kThreads) unpack_kernel(Layout lay, const doub
 // pack: beta = B v from the canonical half spectrum (twin slots of vh ignored)
 __global__ void __launch_bounds__(kThreads) pack_kernel(Layout lay, const double* __restrict__ vh, double* __restrict__ beta,
                                                         DevScalars* sc) {
+  pdl_wait();
   count_launch(sc);
   const long long H = lay.H;
   const double r2 = 1.41421356237309504880;
@@ -512,6 +527,7 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(Layout lay, const double
 
 // ghost coordinates of a beta-layout vector forced to 0
 __global__ void __launch_bounds__(kThreads) clear_ghosts_kernel(Layout lay, double* v, int blocks, DevScalars* sc) {
+  pdl_wait();
   count_launch(sc);
   const long long n2 = 2 * lay.H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
@@ -537,80 +553,58 @@ int grid_for(long long n) {
 
 cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, DevScalars* sc, cudaStream_t st) {
   const long long nw = (long long)((Nl + 31) / 32) * M;
-  pack_mask_kernel<<<grid_for(nw), kThreads, 0, st>>>(mask, words, Nl, M, sc);
-  return cudaGetLastError();
+  return launch_k(pack_mask_kernel, dim3(grid_for(nw)), dim3(kThreads), 0, st, mask, words, Nl, M, sc);
 }
 cudaError_t k_observed_norm(const double* y, const uint8_t* mask, long long n, Reduce red, DevScalars* sc, cudaStream_t st) {
-  observed_norm_kernel<<<grid_for(n), kThreads, 0, st>>>(y, mask, n, red.partials, red.counter, sc);
-  return cudaGetLastError();
+  return launch_k(observed_norm_kernel, dim3(grid_for(n)), dim3(kThreads), 0, st, y, mask, n, red.partials, red.counter, sc);
 }
 cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Reduce red, DevScalars* sc, cudaStream_t st) {
-  cmax_kernel<<<grid_for(n2), kThreads, 0, st>>>(c, n2, lam, relative, red.partials, red.counter, sc);
-  return cudaGetLastError();
+  return launch_k(cmax_kernel, dim3(grid_for(n2)), dim3(kThreads), 0, st, c, n2, lam, relative, red.partials, red.counter, sc);
 }
 cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr,
                          cudaStream_t st) {
-  init_point_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, red.partials,
-                                                              red.counter, sc, sigma0, incr);
-  return cudaGetLastError();
+  return launch_k(init_point_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, red.partials, red.counter, sc, sigma0, incr);
 }
 cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr, cudaStream_t st) {
-  mu_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0, incr);
-  return cudaGetLastError();
+  return launch_k(mu_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, sigma0, incr);
 }
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
                           DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st) {
-  certificate_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, beta, Gb, c, red.partials, red.counter, sc,
-                                                               gap_tol, max_ipm, loop);
-  return cudaGetLastError();
+  return launch_k(certificate_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, beta, Gb, c, red.partials, red.counter, sc, gap_tol, max_ipm, loop);
 }
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
                       LoopCtl loop, double rho, cudaStream_t st) {
-  prepare_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, cg_tol, cg_relative,
-                                                           loop, rho);
-  return cudaGetLastError();
+  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho);
 }
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
                          IpmVectors w, DevScalars* sc, double rho, cudaStream_t st) {
-  sigma_coef_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc, sc,
-                                                              rho);
-  return cudaGetLastError();
+  return launch_k(sigma_coef_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc, sc, rho);
 }
 cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st) {
-  precond_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w.pa, w.pb, w.pc, r, z, sc);
-  return cudaGetLastError();
+  return launch_k(precond_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w.pa, w.pb, w.pc, r, z, sc);
 }
 cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, int refine_every,
                          LoopCtl loop, cudaStream_t st) {
-  pcg_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, max_cg,
-                                                              refine_every, loop);
-  return cudaGetLastError();
+  return launch_k(pcg_update_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials, red.counter, sc, max_cg, refine_every, loop);
 }
 cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st) {
-  refine_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(2 * lay.H, w, red.partials, red.counter, sc, loop);
-  return cudaGetLastError();
+  return launch_k(refine_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials, red.counter, sc, loop);
 }
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st) {
-  step_length_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, tau);
-  return cudaGetLastError();
+  return launch_k(step_length_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, tau);
 }
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           int sigma_rule, double sigma_min, cudaStream_t st) {
-  step_update_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, w, red.partials, red.counter, sc, sigma0, sigma_slow,
-                                                               sigma_rule, sigma_min);
-  return cudaGetLastError();
+  return launch_k(step_update_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, sigma0, sigma_slow, sigma_rule, sigma_min);
 }
 cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, DevScalars* sc, cudaStream_t st) {
-  unpack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, beta, vh, sc);
-  return cudaGetLastError();
+  return launch_k(unpack_kernel, dim3(grid_for(lay.H)), dim3(kThreads), 0, st, lay, beta, vh, sc);
 }
 cudaError_t k_pack(const Layout& lay, const double* vh, double* beta, DevScalars* sc, cudaStream_t st) {
-  pack_kernel<<<grid_for(lay.H), kThreads, 0, st>>>(lay, vh, beta, sc);
-  return cudaGetLastError();
+  return launch_k(pack_kernel, dim3(grid_for(lay.H)), dim3(kThreads), 0, st, lay, vh, beta, sc);
 }
 cudaError_t k_clear_ghosts(const Layout& lay, double* v, int blocks, DevScalars* sc, cudaStream_t st) {
-  clear_ghosts_kernel<<<grid_for(2 * lay.H), kThreads, 0, st>>>(lay, v, blocks, sc);
-  return cudaGetLastError();
+  return launch_k(clear_ghosts_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, v, blocks, sc);
 }
 
 }  // namespace sdft

@@ -50,8 +50,8 @@ def test_default_options(lib):
     assert o.gap_tol == 1e-6 and o.cg_relative == 1 and o.tau == 0.995 and o.sigma == 0.1
 
 
-@pytest.mark.parametrize("dims,why", [((7,), "odd"), ((10,), "factor 5"), ((4, 4, 4, 4), "ndim"),
-                                      ((1024,), "too long"), ((0,), "empty")])
+@pytest.mark.parametrize("dims,why", [((7,), "odd"), ((22,), "factor 11"), ((50,), "factor 5 twice"),
+                                      ((4, 4, 4, 4), "ndim"), ((2048,), "too long"), ((0,), "empty")])
 def test_create_rejects_bad_grids_without_gpu_work(lib, dims, why):
     h = ctypes.c_void_p()
     d = (ctypes.c_int64 * len(dims))(*dims)
@@ -83,11 +83,11 @@ def test_null_handle_calls_fail_cleanly(lib):
 def test_default_options_of_the_solver_variants(lib):
     o = binding.default_options()
     assert o.tile_engine == 0 and o.sigma_rule == 1 and o.sigma_min == 0.03
-    assert o.exact_residual == 0 and o.precond_rho == 1.0
+    assert o.exact_residual == 0 and o.precond_rho == 1.0 and o.pdl == 1
 
 
 @pytest.mark.parametrize("field,value", [("tile_engine", 3), ("sigma_rule", 2), ("sigma_min", 0.0),
-                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0),
+                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0), ("pdl", 2),
                                          ("precond_rho", float("inf"))])
 def test_create_rejects_bad_variant_options(lib, field, value):
     h = ctypes.c_void_p()

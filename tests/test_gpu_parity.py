@@ -528,3 +528,71 @@ def test_tile_cache_file_reproduces_tiles(tmp_path):
     assert len(lines) >= 6 and all(len(ln.split()) == 9 for ln in lines)
     assert run() == first
     assert (tmp_path / "tiles.txt").read_text().splitlines() == lines      # nothing re-tuned
+
+
+@pytest.mark.parametrize("dims", [(70,), (40, 28), (20, 14, 10), (30, 56), (560, 16), (16, 560), (14, 40, 30)])
+def test_radix_5_and_7_lengths_match_oracle(dims):
+    """Extents with factors 5 and 7 (radix-5 and radix-7 stages, e.g. the paper's 560):
+    products with G and K in both precisions against the oracle."""
+    n = int(np.prod(dims))
+    for precision in (binding.IPM_FP64, binding.IPM_MIXED):
+        w = _workload(dims, seed=31)
+        h = _handle(w, precision)
+        try:
+            prob = _oracle(w, 1.0)
+            rng = np.random.default_rng(32)
+            beta = rng.standard_normal(n)
+            p = oracle_to_lib(h, beta, dims)
+            q = torch.empty_like(p)
+            binding.gapply(h, p, q)
+            tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * np.linalg.norm(beta)
+            assert np.abs(lib_to_half(h, q) - oracle_to_half(prob.G(beta), dims)).max() < tol
+            s1, nu1, s2, nu2 = _interior(n, rng)
+            binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+            S1, S2 = oipm.sigmas(s1, nu1, s2, nu2)
+            pb, pz = rng.standard_normal(n), rng.standard_normal(n)
+            pk = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
+            qk = torch.empty_like(pk)
+            binding.kkt_apply(h, pk, qk)
+            qb, qz = oipm.K_apply(prob.G, S1, S2, pb, pz)
+            H2 = pk.numel() // 2
+            scale = np.linalg.norm(np.concatenate([pb, pz])) * (1 + (S1 + S2).max())
+            tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * scale
+            assert np.abs(lib_to_half(h, qk[:H2]) - oracle_to_half(qb, dims)).max() < tol
+        finally:
+            binding.ipm_destroy(h)
+
+
+def test_radix_5_and_7_solve_matches_oracle():
+    w = _workload((20, 14, 10), seed=33)
+    h = _handle(w, binding.IPM_FP64, gap_tol=1e-9)
+    try:
+        res = binding.ipm_solve(h)
+    finally:
+        binding.ipm_destroy(h)
+    ora = oipm.solve(_oracle(w, res["lambda"]), gap_tol=1e-9, sigma_rule="adaptive", sigma_min=0.03)
+    assert res["status"] == binding.IPM_OK
+    assert abs(res["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
+
+
+@pytest.mark.parametrize("precision,dims", [(binding.IPM_FP64, (64, 48)), (binding.IPM_MIXED, (32, 24, 16))])
+def test_programmatic_dependent_launch_is_bit_identical(precision, dims):
+    """pdl = 1 only overlaps kernel launches (each kernel waits on the device for its
+    predecessor): the solve, graph or host-driven, is bit-identical to pdl = 0."""
+    w = _workload(dims, seed=34)
+    out = {}
+    for pdl in (0, 1):
+        for graph in (0, 1):
+            h = _handle(w, precision, gap_tol=1e-8, pdl=pdl, use_graph=graph, autotune=0)
+            try:
+                r = binding.ipm_solve(h)
+                H, n = binding.ipm_sizes(h)
+                v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+                binding.ipm_get_spectrum(h, v)
+                out[(pdl, graph)] = (r["primal"], r["ipm_iters"], r["cg_iters_total"], v.cpu().numpy())
+            finally:
+                binding.ipm_destroy(h)
+    ref = out[(0, 1)]
+    for key, val in out.items():
+        assert val[:3] == ref[:3], key
+        assert np.array_equal(val[3], ref[3]), key
