@@ -131,6 +131,11 @@ typedef struct {
                            its predecessor drains and waits on the device until that
                            predecessor has completed (same results, shorter gaps between the
                            many small kernels of a solve); 0: plain stream order            */
+  int krylov;           /* Krylov method for the Newton systems (Sec. 3.5 names CG, CR and CAr
+                           for these SPD systems).  0 (default): preconditioned conjugate
+                           gradients; 1: preconditioned conjugate residuals (one product K z
+                           per iteration, two update kernels; G beta is then recomputed every
+                           iteration, and refine_every must be 0)                          */
 } ipm_options;
 
 typedef struct {

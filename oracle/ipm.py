@@ -57,7 +57,8 @@ Our readings (the paper leaves them to MadNLP or prints them with typos)
 * Stop when the relative duality gap (``Problem.certificate``) is <= gap_tol.
 * PCG: x0 = 0, stop when sqrt(r^T z) <= cg_tol * sqrt(r0^T z0) (relative,
   the default) or sqrt(r^T z) <= cg_tol (absolute, as the paper's 1e-12 rule),
-  or after max_cg iterations.
+  or after max_cg iterations.  ``krylov="cr"`` uses preconditioned conjugate
+  residuals instead (Sec. 3.5 lists CR beside CG), with the same stop rule.
 """
 
 import numpy as np
@@ -117,6 +118,38 @@ def pcg(apply_K, apply_Pinv, rhs, tol, max_iter, relative=True):
         rho_new = dot(r, zv)
         p = (zv[0] + (rho_new / rho) * p[0], zv[1] + (rho_new / rho) * p[1])
         rho = rho_new
+        it += 1
+    return x, it, np.sqrt(max(rho, 0.0))
+
+
+def pcr(apply_K, apply_Pinv, rhs, tol, max_iter, relative=True):
+    """Preconditioned conjugate residuals (the CR the paper lists beside CG for these
+    SPD systems, Sec. 3.5): one product K z per iteration, the residual minimised in
+    the P^{-1} norm; same stop rule as ``pcg``.  Returns (x, iterations, sqrt(r^T z))."""
+    def dot(a, b):
+        return a[0] @ b[0] + a[1] @ b[1]
+
+    x = (np.zeros_like(rhs[0]), np.zeros_like(rhs[1]))
+    r = (rhs[0].copy(), rhs[1].copy())
+    z = apply_Pinv(*r)
+    rho = dot(r, z)
+    stop = tol * np.sqrt(max(rho, 0.0)) if relative else tol
+    p = q = None
+    zw_old = 0.0
+    it = 0
+    while it < max_iter and np.sqrt(max(rho, 0.0)) > stop:
+        w = apply_K(*z)                                     # K z
+        zw = dot(z, w)
+        beta = zw / zw_old if p is not None else 0.0
+        p = z if p is None else (z[0] + beta * p[0], z[1] + beta * p[1])
+        q = w if q is None else (w[0] + beta * q[0], w[1] + beta * q[1])   # q = K p
+        u = apply_Pinv(*q)
+        alpha = zw / dot(q, u)
+        x = (x[0] + alpha * p[0], x[1] + alpha * p[1])
+        r = (r[0] - alpha * q[0], r[1] - alpha * q[1])
+        z = (z[0] - alpha * u[0], z[1] - alpha * u[1])
+        rho = dot(r, z)
+        zw_old = zw
         it += 1
     return x, it, np.sqrt(max(rho, 0.0))
 
@@ -187,7 +220,7 @@ def next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min):
 
 def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative=True,
           sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.01,
-          precond_rho=1.0):
+          precond_rho=1.0, krylov="cg"):
     """Run the IPM; returns a dict with the point, counts and the certificate."""
     w = [np.array(v, dtype=np.float64, copy=True) for v in (w0 or starting_point(prob))]
     sigma = sigma0
@@ -207,7 +240,7 @@ def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative
         res, mu = residuals(prob, Gbeta, w, sigma)
         Sig1, Sig2 = sigmas(w[2], w[4], w[3], w[5])
         rhs = condensed_rhs(res, w)
-        (dbeta, dz), ncg, _ = pcg(lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b),
+        (dbeta, dz), ncg, _ = (pcr if krylov == "cr" else pcg)(lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b),
                                   lambda a, b: Pinv_apply(Sig1, Sig2, a, b, precond_rho),
                                   rhs, cg_tol, max_cg, cg_relative)
         cg_counts.append(ncg)

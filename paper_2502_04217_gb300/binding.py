@@ -30,7 +30,8 @@ class ipm_options(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("tile_e", ctypes.c_int), ("tile_p", ctypes.c_int),
                 ("refine_every", ctypes.c_int), ("tile_engine", ctypes.c_int),
                 ("sigma_rule", ctypes.c_int), ("sigma_min", ctypes.c_double), ("exact_residual", ctypes.c_int),
-                ("precond_rho", ctypes.c_double), ("pdl", ctypes.c_int)]
+                ("precond_rho", ctypes.c_double), ("pdl", ctypes.c_int),
+                ("krylov", ctypes.c_int)]
 
 
 class ipm_result(ctypes.Structure):

@@ -147,7 +147,9 @@ namespace {
 // FP64 mode updates G beta from the PCG products (G x accumulated alongside x)
 // and recomputes it with an FP64 product only to confirm a passed stop test;
 // mixed precision recomputes it every iteration (its PCG products are FP32).
-int incremental_gb(const sdft_ipm* h) { return (h->opt.precision == IPM_FP64 && !h->opt.exact_residual) ? 1 : 0; }
+int incremental_gb(const sdft_ipm* h) {
+  return (h->opt.precision == IPM_FP64 && !h->opt.exact_residual && h->opt.krylov == 0) ? 1 : 0;
+}
 
 ipm_status fail_arg(sdft_ipm* h, const char* msg) {
   if (h) h->err = msg; else g_create_error = msg;
@@ -543,6 +545,7 @@ struct GSpec {
   bool pcg = false;              // MAPIN_PCG / MAPOUT_K inside PCG (p, zv, q of the handle)
   bool refine = false;           // only when the device asks for an FP64 residual replacement
   bool exact = false;            // only when the device asks for an exact G beta (incremental mode)
+  bool cr = false;               // conjugate residuals: w = K z (z of the handle) with z^T w
   const double* p_in = nullptr;  // kkt_apply: p and q given by the caller
   double* q_out = nullptr;
 };
@@ -568,7 +571,17 @@ ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
       a.lam2 = h->w.lam2;
       a.pcg_mode = g.pcg ? 1 : 0;
     }
-    a.check_done = g.pcg ? 1 : 0;
+    if (g.cr) {
+      if (first) { a.mapin = MAPIN_BETA; a.src = h->w.zv; }
+      if (last) {
+        a.mapout = MAPOUT_K;
+        a.p = h->w.zv;
+        a.q = h->w.wcr;
+        a.pcg_mode = 1;
+        a.cr_mode = 1;
+      }
+    }
+    a.check_done = (g.pcg || g.cr) ? 1 : 0;
     a.check_refine = g.refine ? 1 : 0;
     a.check_exact = g.exact ? 1 : 0;
     if (last) a.gp_out = (g.pcg && !fp32 && incremental_gb(h)) ? h->w.Gp : nullptr;
@@ -682,6 +695,8 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (o.exact_residual < 0 || o.exact_residual > 1) return fail_arg(h, "exact_residual must be 0 or 1");
   if (!(o.precond_rho >= 0.0) || !std::isfinite(o.precond_rho)) return fail_arg(h, "precond_rho must be >= 0 and finite");
   if (o.pdl < 0 || o.pdl > 1) return fail_arg(h, "pdl must be 0 or 1");
+  if (o.krylov < 0 || o.krylov > 1) return fail_arg(h, "krylov must be 0 (CG) or 1 (CR)");
+  if (o.krylov == 1 && o.refine_every > 0) return fail_arg(h, "krylov = 1 (CR) does not combine with refine_every");
   if (o.sigma_rule == 1 && !(o.sigma_min > 0 && o.sigma_min <= o.sigma_slow))
     return fail_arg(h, "sigma_min must lie in (0, sigma_slow]");
   if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
@@ -717,6 +732,7 @@ void ipm_default_options(ipm_options* o) {
   o->exact_residual = 0;
   o->precond_rho = 1.0;
   o->pdl = 1;
+  o->krylov = 0;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -761,7 +777,7 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
                      &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->w.is1, &h->w.is2, &h->d_tmp,
                      &h->w.Gp, &h->w.Gx};
   for (double** p : vec2) CKC(dalloc(h, p, v2));
-  double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q, &h->w.rhs};
+  double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q, &h->w.rhs, &h->w.wcr, &h->w.ucr};
   for (double** p : vec4) CKC(dalloc(h, p, v4));
   CKC(dalloc(h, &h->d_U, (size_t)L.H * 2 * sizeof(double)));
   CKC(cudaMemsetAsync(h->d_U, 0, (size_t)L.H * 2 * sizeof(double), h->st));
@@ -918,6 +934,20 @@ ipm_status queue_prepare(sdft_ipm* h, LoopCtl cg_loop) {
 }
 
 ipm_status queue_pcg_iteration(sdft_ipm* h, LoopCtl cg_loop) {
+  if (h->opt.krylov == 1) {
+    // conjugate residuals: w = K z, then the two update kernels
+    GSpec k;
+    k.mapin = MAPIN_BETA;
+    k.mapout = MAPOUT_K;
+    k.cr = true;
+    ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, k);
+    if (s != IPM_OK) return s;
+    Reduce red{h->d_partials, h->d_counter};
+    ProfScope ps(h, 3);
+    CK(k_cr_update_a(h->lay, h->w, red, h->d_sc, cg_loop, h->st));
+    CK(k_cr_update_b(h->lay, h->w, red, h->d_sc, h->opt.max_cg, cg_loop, h->st));
+    return IPM_OK;
+  }
   GSpec k;
   k.mapin = MAPIN_PCG;
   k.mapout = MAPOUT_K;

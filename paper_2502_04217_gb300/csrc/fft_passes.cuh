@@ -235,7 +235,7 @@ __device__ __forceinline__ void finish_pq(const PassArgs& a, double acc, double*
       sc->cg_status = 2;
       sc->cg_done = 1;
       sc->alpha_cg = 0.0;
-    } else {
+    } else if (!a.cr_mode) {
       sc->alpha_cg = sc->rho / pq;
     }
   }

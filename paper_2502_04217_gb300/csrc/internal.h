@@ -19,6 +19,7 @@ struct DevScalars {
   double pq;         // p^T K p of the last product
   double alpha_cg;   // rho / p^T K p
   double beta_cg;    // rho_new / rho (0 before the first product)
+  double zw_old;     // conjugate residuals: z^T K z of the previous iteration (0 at a PCG start)
   int cg_done;       // 1 once PCG has stopped (kernels then return at once)
   int cg_iter;       // PCG iterations of the current solve
   int cg_status;     // 0 ok, 1 hit max_cg, 2 non-finite value
@@ -81,6 +82,7 @@ struct PassArgs {
   const double* lam2;
   double* q;             // MAPOUT_K: K p (4H)
   int pcg_mode;          // MAPOUT_K inside PCG: form alpha = rho / p^T q
+  int cr_mode;           // with pcg_mode: conjugate residuals, only store the product's p^T q (= z^T K z)
   int check_done;        // return at once when sc->cg_done
   int check_refine;      // return at once unless sc->refine_now
   int check_exact;       // return at once unless sc->exact_now

@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     const double rho = v[0];
     sc->rho = rho;
     sc->beta_cg = 0.0;
+    sc->zw_old = 0.0;
     sc->cg_iter = 0;
     sc->cg_status = 0;
     sc->cg_stop = cg_relative ? cg_tol * sqrt(fmax(rho, 0.0)) : cg_tol;
@@ -349,6 +350,83 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmV
       sc->refine_now = 1;
       sc->refine_exit = conv ? 1 : 0;
     }
+    set_cond(cg_loop, sc->cg_done ? 0u : 1u);
+  }
+}
+
+// Conjugate residuals (Sec. 3.5 lists CR beside CG), after w = K z and
+// sc->pq = z^T w: beta = z^T w / (z^T w)_previous (0 at a PCG start),
+// p = z + beta p, q = w + beta q (= K p), u = P^{-1} q, alpha = z^T w / q^T u.
+__global__ void __launch_bounds__(kThreads) cr_update_a_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
+                                                               DevScalars* sc, LoopCtl cg_loop) {
+  pdl_wait();
+  __shared__ double scratch[32];
+  count_launch(sc);
+  if (sc->cg_done) {
+    if (first_thread()) set_cond(cg_loop, 0u);
+    return;
+  }
+  const double zw = sc->pq, zw0 = sc->zw_old;
+  const bool first = !(zw0 > 0.0);              // a PCG start: p = z, q = w (old p, q not read)
+  const double beta = first ? 0.0 : zw / zw0;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    double pb = w.zv[i], pz = w.zv[n2 + i], qb = w.wcr[i], qz = w.wcr[n2 + i];
+    if (!first) {
+      pb += beta * w.p[i];
+      pz += beta * w.p[n2 + i];
+      qb += beta * w.q[i];
+      qz += beta * w.q[n2 + i];
+    }
+    w.p[i] = pb; w.p[n2 + i] = pz;
+    w.q[i] = qb; w.q[n2 + i] = qz;
+    const double a = w.pa[i], b = w.pb[i], c = w.pc[i];
+    const double ub = a * qb - b * qz, uz = -b * qb + c * qz;
+    w.ucr[i] = ub; w.ucr[n2 + i] = uz;
+    v[0] += qb * ub + qz * uz;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double qu = v[0];
+    sc->zw_old = zw;
+    if (!(qu > 0.0) || !isfinite(qu)) { sc->cg_status = 2; sc->cg_done = 1; sc->alpha_cg = 0.0; }
+    else sc->alpha_cg = zw / qu;
+    set_cond(cg_loop, sc->cg_done ? 0u : 1u);
+  }
+}
+
+// Conjugate residuals, second half: x += alpha p, r -= alpha q, z -= alpha u,
+// rho = r^T z and the stop test of PCG.
+__global__ void __launch_bounds__(kThreads) cr_update_b_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
+                                                               DevScalars* sc, int max_cg, LoopCtl cg_loop) {
+  pdl_wait();
+  __shared__ double scratch[32];
+  count_launch(sc);
+  if (sc->cg_done) {
+    if (first_thread()) set_cond(cg_loop, 0u);
+    return;
+  }
+  const double alpha = sc->alpha_cg;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    w.x[i] += alpha * w.p[i];
+    w.x[n2 + i] += alpha * w.p[n2 + i];
+    const double rb = w.r[i] - alpha * w.q[i], rz = w.r[n2 + i] - alpha * w.q[n2 + i];
+    const double zb = w.zv[i] - alpha * w.ucr[i], zz = w.zv[n2 + i] - alpha * w.ucr[n2 + i];
+    w.r[i] = rb; w.r[n2 + i] = rz;
+    w.zv[i] = zb; w.zv[n2 + i] = zz;
+    v[0] += rb * zb + rz * zz;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double rho_new = v[0];
+    sc->rho = rho_new;
+    sc->cg_iter += 1;
+    const bool conv = sqrt(fmax(rho_new, 0.0)) <= sc->cg_stop;
+    if (!isfinite(rho_new)) { sc->cg_status = 2; sc->cg_done = 1; }
+    else if (conv) sc->cg_done = 1;
+    else if (sc->cg_iter >= max_cg) { sc->cg_status = 1; sc->cg_done = 1; }
+    sc->refine_now = 0;
     set_cond(cg_loop, sc->cg_done ? 0u : 1u);
   }
 }
@@ -589,6 +667,15 @@ cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars
 }
 cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st) {
   return launch_k(refine_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials, red.counter, sc, loop);
+}
+cudaError_t k_cr_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st) {
+  return launch_k(cr_update_a_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+                  red.counter, sc, loop);
+}
+cudaError_t k_cr_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
+                          cudaStream_t st) {
+  return launch_k(cr_update_b_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+                  red.counter, sc, max_cg, loop);
 }
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st) {
   return launch_k(step_length_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, tau);

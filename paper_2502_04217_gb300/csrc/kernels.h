@@ -15,6 +15,7 @@ struct IpmVectors {
   double *is1, *is2;                          // 1/s1, 1/s2 at the current iterate (step kernels)
   double *x, *r, *zv, *p, *q;                 // PCG vectors, 2 blocks each (4H)
   double *rhs;                                // right-hand side of the current Newton system (4H)
+  double *wcr, *ucr;                          // conjugate residuals: w = K z and u = P^{-1} q (4H each)
   double *Gp, *Gx;                            // incremental G beta: (G p)_beta of the last PCG product and
                                               // (G x)_beta = sum alpha (G p)_beta over the PCG solve (2H each)
 };
@@ -60,6 +61,9 @@ cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* 
 cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, int refine_every,
                          LoopCtl loop, cudaStream_t st);
 cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st);
+cudaError_t k_cr_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st);
+cudaError_t k_cr_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
+                          cudaStream_t st);
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st);
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           int sigma_rule, double sigma_min, cudaStream_t st);

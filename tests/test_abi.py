@@ -83,11 +83,11 @@ def test_null_handle_calls_fail_cleanly(lib):
 def test_default_options_of_the_solver_variants(lib):
     o = binding.default_options()
     assert o.tile_engine == 0 and o.sigma_rule == 1 and o.sigma_min == 0.03
-    assert o.exact_residual == 0 and o.precond_rho == 1.0 and o.pdl == 1
+    assert o.exact_residual == 0 and o.precond_rho == 1.0 and o.pdl == 1 and o.krylov == 0
 
 
 @pytest.mark.parametrize("field,value", [("tile_engine", 3), ("sigma_rule", 2), ("sigma_min", 0.0),
-                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0), ("pdl", 2),
+                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0), ("pdl", 2), ("krylov", 2),
                                          ("precond_rho", float("inf"))])
 def test_create_rejects_bad_variant_options(lib, field, value):
     h = ctypes.c_void_p()

@@ -596,3 +596,23 @@ def test_programmatic_dependent_launch_is_bit_identical(precision, dims):
     for key, val in out.items():
         assert val[:3] == ref[:3], key
         assert np.array_equal(val[3], ref[3]), key
+
+
+@pytest.mark.parametrize("precision,dims", [(binding.IPM_FP64, (32, 24, 16)), (binding.IPM_FP64, (64, 48)),
+                                            (binding.IPM_MIXED, (32, 24, 16))])
+def test_conjugate_residuals_match_oracle(precision, dims):
+    """krylov = 1 (preconditioned conjugate residuals): the same optimum as the oracle's
+    CR solve, and in FP64 the same IPM and Krylov iteration counts."""
+    w = _workload(dims, seed=35)
+    h = _handle(w, precision, gap_tol=1e-8, krylov=1)
+    try:
+        res = binding.ipm_solve(h)
+    finally:
+        binding.ipm_destroy(h)
+    ora = oipm.solve(_oracle(w, res["lambda"]), gap_tol=1e-8, sigma_rule="adaptive", sigma_min=0.03, krylov="cr")
+    assert res["status"] == binding.IPM_OK and ora["status"] == "converged"
+    tol = 1e-8 if precision == binding.IPM_FP64 else 1e-6
+    assert abs(res["primal"] - ora["primal"]) <= tol * abs(ora["primal"])
+    if precision == binding.IPM_FP64:
+        assert res["ipm_iters"] == ora["ipm_iters"]
+        assert res["cg_iters_total"] == sum(ora["cg_counts"])

@@ -207,3 +207,21 @@ def test_scaled_identity_preconditioner_closed_form(rho):
     assert np.abs(Pinv - np.linalg.inv(P)).max() < 1e-12 * np.abs(np.linalg.inv(P)).max()
     D = L1 * (rho + L1) - L2 ** 2
     assert np.abs(D - (rho * (S1 + S2) + 4 * S1 * S2)).max() < 1e-12 * D.max()
+
+
+@pytest.mark.parametrize("dims", [(8,), (4, 6)])
+def test_preconditioned_conjugate_residuals_solve_the_newton_system(dims):
+    """CR (Sec. 3.5 lists it beside CG): the condensed system K x = rhs solved by PCR equals
+    the dense solve, and PCR reaches it in no more iterations than the system's size."""
+    prob = _problem(dims)
+    n = prob.n
+    rng = np.random.default_rng(41)
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    K = _dense(lambda e: np.concatenate(ipm.K_apply(prob.G, S1, S2, e[:n], e[n:])), 2 * n)
+    rhs = rng.standard_normal(2 * n)
+    (xb, xz), it, res = ipm.pcr(lambda a, b: ipm.K_apply(prob.G, S1, S2, a, b),
+                                lambda a, b: ipm.Pinv_apply(S1, S2, a, b), tuple(np.split(rhs, 2)), 1e-13, 500)
+    ref = np.linalg.solve(K, rhs)
+    assert np.abs(np.concatenate([xb, xz]) - ref).max() < 1e-9 * np.abs(ref).max()
+    assert it <= 2 * n + 2
