@@ -26,7 +26,7 @@ from .mapping import beta_to_v, v_to_beta
 
 
 class Problem:
-    """One masked, noisy real signal on an even d-dimensional grid.
+    """One masked, noisy real signal on a d-dimensional grid (any extents >= 2).
 
     mask[j] = True where sample j is observed (the complement of the paper's
     missing set M); y holds the signal, its values at missing samples are

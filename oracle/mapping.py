@@ -5,26 +5,33 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Paper passages followed
 -----------------------
 * Sec. 3, definition of the subspace F: a real signal has a conjugate-symmetric
-  DFT, v_k = conj(v_{-k}); for even n the entries v_0 and v_{n/2} are real.
+  DFT, v_k = conj(v_{-k}); for even n the entries v_0 and v_{n/2} are real, for
+  odd n only v_0 is (the paper's second definition of F, for odd n).
 * Sec. 3, Eq. (beta): beta = [v_0, v_{n/2}, sqrt2 Re v_{1:n/2-1},
   sqrt2 Im v_{1:n/2-1}] and its inverse Eq. (v).
 * Sec. 3, Eq. (map): with these maps IDFT(v) = A beta with A real orthogonal.
 
-The paper gives the 1D map only and states that 2D/3D analogues exist.  Our
-reading for d-dimensional even grids N = (N_1, ..., N_d):
+The paper gives the 1D map for even n only and states that 2D/3D analogues
+exist.  Our reading for d-dimensional grids N = (N_1, ..., N_d), each N_i even
+or odd:
 
 * a frequency k (multi-index, k_i in [0, N_i)) is *self-conjugate* when
-  2k = 0 mod N, i.e. every k_i is 0 or N_i/2 (2^d such points); it
-  contributes the single real coordinate v_k;
+  2k = 0 mod N, i.e. every k_i is 0 or (N_i even) N_i/2; there are
+  S = prod_i (2 if N_i is even else 1) such points, each contributing the
+  single real coordinate v_k;
 * every other frequency pairs with -k.  The pair's *representative* is k when
-  1 <= k_d <= N_d/2 - 1, and, on the two planes k_d in {0, N_d/2}, the member
-  whose leading indices (k_1..k_{d-1}) are lexicographically smaller than
-  those of -k.  A representative contributes sqrt2 Re v_k and sqrt2 Im v_k;
+  1 <= k_d and 2 k_d < N_d, and, on the edge planes 2 k_d = 0 mod N_d
+  (k_d = 0, and k_d = N_d/2 for even N_d), the member whose leading indices
+  (k_1..k_{d-1}) are lexicographically smaller than those of -k.  A
+  representative contributes sqrt2 Re v_k and sqrt2 Im v_k;
 * beta is ordered as [self-conjugate values, sqrt2 Re of representatives,
   sqrt2 Im of representatives], each group in row-major order of k.
 
-For d = 1 this is exactly Eq. (beta).  The count is 2^d + (n - 2^d) = n and B
-stays unitary, so A = C^H B^H stays real orthogonal (checked by the tests).
+For d = 1 and even n this is exactly Eq. (beta); for odd n it is
+[v_0, sqrt2 Re v_{1:(n-1)/2}, sqrt2 Im v_{1:(n-1)/2}], the same construction on
+the odd-n subspace (whose printed index range runs to (n+1)/2; the pairs are
+k = 1 .. (n-1)/2).  The count is S + (n - S) = n and B stays unitary, so
+A = C^H B^H stays real orthogonal (checked by the tests).
 """
 
 import functools
@@ -40,14 +47,14 @@ def frequency_classes(dims):
     pair representatives, and of the twin -k of each representative."""
     dims = tuple(int(d) for d in dims)
     for d in dims:
-        if d < 2 or d % 2:
-            raise ValueError("every grid dimension must be even and >= 2")
+        if d < 2:
+            raise ValueError("every grid dimension must be >= 2")
     k = np.indices(dims).reshape(len(dims), -1)          # k[i] = k_i for every flat index
     neg = (-k) % np.asarray(dims)[:, None]                # the multi-index of -k
     self_conj = np.all(neg == k, axis=0)
     kd, Nd = k[-1], dims[-1]
-    interior = (kd >= 1) & (kd <= Nd // 2 - 1)
-    edge = (kd == 0) | (kd == Nd // 2)
+    interior = (kd >= 1) & (2 * kd < Nd)
+    edge = (2 * kd) % Nd == 0
     # lexicographic "k[:-1] < neg[:-1]": decided by the first leading index that differs
     lead_less = np.zeros(k.shape[1], dtype=bool)
     undecided = np.ones(k.shape[1], dtype=bool)
@@ -58,7 +65,8 @@ def frequency_classes(dims):
     sc = np.flatnonzero(self_conj)
     rep = np.flatnonzero(is_rep)
     twin = np.ravel_multi_index(tuple(neg[:, rep]), dims).astype(np.int64)
-    assert sc.size == 2 ** len(dims) and sc.size + 2 * rep.size == int(np.prod(dims))
+    n_sc = int(np.prod([2 if N % 2 == 0 else 1 for N in dims]))
+    assert sc.size == n_sc and sc.size + 2 * rep.size == int(np.prod(dims))
     return sc.astype(np.int64), rep.astype(np.int64), twin
 
 

@@ -27,7 +27,7 @@ Workloads (the paper's real X-ray volume is not available; these synthetic
              noise; about 15 % missing "around the Bragg peaks", read as balls of
              radius 2 on a period-6 lattice (15.3 % missing); lambda = 0.05
              lambda_max (the paper does not state its lambda).
-* ``custom`` any even grid, see ``make_problem``.
+* ``custom`` any grid (even or odd extents), see ``make_problem``.
 
 lambda is returned as a *fraction* of lambda_max = ||M_perp^T b||_inf; each
 solver computes lambda_max itself.
@@ -57,7 +57,7 @@ def _sparse_signal(rng, dims, k, amp="normal"):
     # interior of the last (halved) axis: every such frequency is its own representative
     interior = np.arange(int(np.prod(half)))
     last = interior % half[-1]
-    interior = interior[(last >= 1) & (last <= dims[-1] // 2 - 1)]
+    interior = interior[(last >= 1) & (2 * last < dims[-1])]
     freqs = np.sort(rng.choice(interior, size=k, replace=False))
     if amp == "laplace":
         amps = rng.laplace(0.0, 1.0, k) + 1j * rng.laplace(0.0, 1.0, k)

@@ -46,7 +46,7 @@ def test_golden_unmasked_n2():
     assert abs(res["primal"] - vals["OBJECTIVE"][0]) < 1e-11
 
 
-@pytest.mark.parametrize("dims", [(16,), (8, 6), (4, 4, 4), (256,)])
+@pytest.mark.parametrize("dims", [(16,), (8, 6), (4, 4, 4), (256,), (15,), (5, 6), (3, 4, 5)])
 def test_unmasked_equals_soft_threshold(dims):
     rng = np.random.default_rng(12)
     prob = Problem(dims, np.ones(dims, bool), rng.standard_normal(dims), 1.0)
@@ -66,7 +66,7 @@ def test_lambda_above_lambda_max_gives_zero(dims):
 
 
 @pytest.mark.parametrize("dims,seed", [((8,), 14), ((8,), 16), ((10,), 16), ((2, 4), 14), ((4, 2), 15),
-                                       ((2, 2, 2), 15)])
+                                       ((2, 2, 2), 15), ((7,), 14), ((3, 3), 15), ((2, 3), 16)])
 def test_masked_tiny_against_enumeration(dims, seed):
     prob = _masked(dims, seed, missing=0.25, lam_rel=0.3)
     Mp = _dense(prob.A, prob.n)[prob.mask.reshape(-1)]
@@ -81,7 +81,8 @@ def test_masked_tiny_against_enumeration(dims, seed):
     assert abs(res["primal"] - prob.objective(sols[0])) < 1e-10 * max(1, abs(res["primal"]))
 
 
-@pytest.mark.parametrize("dims,seed", [((32,), 19), ((8, 8), 20), ((4, 4, 4), 21), ((6, 10), 22)])
+@pytest.mark.parametrize("dims,seed", [((32,), 19), ((8, 8), 20), ((4, 4, 4), 21), ((6, 10), 22),
+                                       ((27,), 19), ((5, 7), 20), ((3, 5, 4), 21)])
 def test_masked_small_against_proximal_gradient(dims, seed):
     prob = _masked(dims, seed, missing=0.2, lam_rel=0.2)
     Mp = _dense(prob.A, prob.n)[prob.mask.reshape(-1)]

@@ -12,7 +12,7 @@ import pytest
 from oracle import ipm
 from oracle.lasso import Problem
 
-SMALL = [(8,), (12,), (4, 6), (4, 4, 4), (2, 4, 6)]
+SMALL = [(8,), (12,), (4, 6), (4, 4, 4), (2, 4, 6), (9,), (3, 5), (3, 4, 5)]
 
 
 def _problem(dims, seed=0, missing=0.3, lam=0.1):

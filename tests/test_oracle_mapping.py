@@ -16,7 +16,9 @@ from oracle import mapping
 from oracle.lasso import Problem
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-DIMS = [(2,), (4,), (8,), (10,), (4, 6), (6, 4), (2, 8), (4, 4, 4), (2, 4, 6), (6, 2, 4)]
+DIMS = [(2,), (4,), (8,), (10,), (4, 6), (6, 4), (2, 8), (4, 4, 4), (2, 4, 6), (6, 2, 4),
+        # odd extents (the odd-n subspace of Sec. 3), alone and mixed with even ones
+        (3,), (5,), (9,), (15,), (3, 5), (5, 4), (4, 5), (3, 3, 3), (3, 4, 5), (2, 3, 2)]
 
 
 def _read_golden(name):
@@ -86,7 +88,7 @@ def test_A_real_orthogonal(dims):
     assert np.abs(odft.idft(mapping.beta_to_v(beta, dims)).imag).max() < 1e-13
 
 
-@pytest.mark.parametrize("dims", [(4,), (6,), (4, 2), (2, 4), (2, 2, 4)])
+@pytest.mark.parametrize("dims", [(4,), (6,), (4, 2), (2, 4), (2, 2, 4), (5,), (3, 4), (4, 3), (3, 3, 2)])
 def test_A_beta_equals_textbook_sum(dims):
     rng = np.random.default_rng(3)
     beta = rng.standard_normal(int(np.prod(dims)))
@@ -113,6 +115,61 @@ def test_A_1d_matches_closed_form_of_eq_map(n):
     assert np.abs(A - ref).max() < 1e-13
 
 
+@pytest.mark.parametrize("n", [3, 5, 9, 15, 21])
+def test_A_1d_odd_closed_form(n):
+    """Eq. (map) redone for odd n: no Nyquist term, h = (n-1)/2 pairs, so
+    x_k = n^{-1/2} (beta_0 + sum_{j=1}^{h} sqrt2 cos(2 pi jk/n) beta_j
+                    - sum_{j=1}^{h} sqrt2 sin(2 pi jk/n) beta_{j+h})."""
+    A = _dense_A((n,))
+    h = (n - 1) // 2
+    ref = np.zeros((n, n))
+    for k in range(n):
+        ref[k, 0] = 1.0
+        for j in range(1, h + 1):
+            ref[k, j] = np.sqrt(2) * np.cos(2 * np.pi * j * k / n)
+            ref[k, j + h] = -np.sqrt(2) * np.sin(2 * np.pi * j * k / n)
+    ref /= np.sqrt(n)
+    assert np.abs(A - ref).max() < 1e-13
+
+
+def test_A_n3_by_hand():
+    """n = 3 worked by hand: beta = [v_0, sqrt2 Re v_1, sqrt2 Im v_1],
+    cos(2 pi/3) = -1/2, sin(2 pi/3) = sqrt3/2, so sqrt3 A is
+    [[1, sqrt2, 0], [1, -1/sqrt2, -sqrt6/2], [1, -1/sqrt2, sqrt6/2]]."""
+    r2, r6 = np.sqrt(2.0), np.sqrt(6.0)
+    ref = np.array([[1.0, r2, 0.0], [1.0, -1 / r2, -r6 / 2], [1.0, -1 / r2, r6 / 2]]) / np.sqrt(3.0)
+    assert np.abs(_dense_A((3,)) - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("n", [3, 7, 9, 25])
+def test_odd_subspace_of_real_signals(n):
+    """Sec. 3, the odd-n subspace: the DFT of a real signal has v_0 real and
+    v_k = conj(v_{n-k}) for k = 1 .. (n-1)/2, and no other real entry; the map
+    beta = B v then round-trips through x exactly."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n)
+    v = np.fft.fft(x, norm="ortho")
+    assert abs(v[0].imag) < 1e-14
+    for k in range(1, (n - 1) // 2 + 1):
+        assert abs(v[k] - np.conj(v[n - k])) < 1e-13
+    beta = mapping.v_to_beta(v, (n,))
+    prob = Problem((n,), np.ones(n, bool), np.zeros(n), 1.0)
+    assert np.abs(prob.A(beta) - x).max() < 1e-13
+    assert np.abs(prob.At(x) - beta).max() < 1e-13
+
+
+def test_representatives_of_odd_1d_order():
+    sc, rep, twin = mapping.frequency_classes((7,))
+    assert list(sc) == [0] and list(rep) == [1, 2, 3] and list(twin) == [6, 5, 4]
+
+
+def test_self_conjugate_count_mixed_parity():
+    # one self-conjugate index per odd axis, two per even axis
+    for dims, count in [((3, 5), 1), ((4, 5), 2), ((5, 4), 2), ((4, 3, 6), 4), ((3, 3, 3), 1)]:
+        sc, rep, _ = mapping.frequency_classes(dims)
+        assert sc.size == count and sc.size + 2 * rep.size == int(np.prod(dims))
+
+
 def test_golden_n4():
     g = _read_golden("mapping_n4.txt")
     A_ref = np.array([row[1:] for row in g["A"]]) / 2.0
@@ -123,7 +180,7 @@ def test_golden_n4():
     assert np.abs(mapping.beta_to_v(np.array(g["BETA"][0]), (4,)) - v).max() < 1e-14
 
 
-@pytest.mark.parametrize("dims", [(8,), (12,), (6, 10), (4, 6, 8), (16, 16)])
+@pytest.mark.parametrize("dims", [(8,), (12,), (6, 10), (4, 6, 8), (16, 16), (9,), (15,), (5, 7), (3, 5, 7)])
 def test_dft_matches_numpy_fft(dims):
     rng = np.random.default_rng(4)
     x = rng.standard_normal(dims) + 1j * rng.standard_normal(dims)
@@ -138,11 +195,11 @@ def test_representatives_of_paper_1d_order():
     assert list(sc) == [0, 4] and list(rep) == [1, 2, 3] and list(twin) == [7, 6, 5]
 
 
-def test_representatives_cover_half_spectrum_2d():
+@pytest.mark.parametrize("dims", [(6, 8), (6, 7), (5, 9), (3, 4, 7)])
+def test_representatives_cover_half_spectrum_2d(dims):
     # every representative lies in the half spectrum k_d <= N_d/2 used by a real FFT
-    dims = (6, 8)
     sc, rep, twin = mapping.frequency_classes(dims)
     k = np.array(np.unravel_index(rep, dims))
     assert np.all(k[-1] <= dims[-1] // 2)
     allk = np.concatenate([sc, rep, twin])
-    assert sorted(allk.tolist()) == list(range(48))
+    assert sorted(allk.tolist()) == list(range(int(np.prod(dims))))
