@@ -23,18 +23,23 @@
  *  - The library never frees caller memory; caller buffers are copied where
  *    stated, and never retained after the call returns.
  *  - Grids are row-major with the LAST axis contiguous; every extent must be
- *    even (Sec. 3 treats the even case), of the form 2^a 3^b 5^c 7^d with
- *    b, c, d <= 1 (the FFT's radices: 2, 4, 8, 16 and one stage each of 3, 5, 7),
- *    and at most 1024 (gapply_noalloc: 2^a 3^b, at most 512).
+ *    of the form 2^a 3^b 5^c 7^d (the FFT's radices: 2, 4, 8, 16, 3, 5, 7),
+ *    at least 2 and at most 1024.  Extents may be even or odd: Sec. 3 defines
+ *    the conjugate-symmetric subspace F for both (for odd n only v_0 is real)
+ *    and treats the even case in detail; the odd case uses the same map with
+ *    no Nyquist entry.  Odd extents without a factor 3 must be at most 512
+ *    (625 and 875 have no launchable FFT tile: IPM_ERR_ARG).  gapply_noalloc
+ *    takes even extents 2^a 3^b up to 512.
  *  - "beta layout": vectors indexed like beta are held as 2H doubles, where
- *    H = N_0 ... N_{d-2} (N_{d-1}/2 + 1) is the number of half-spectrum slots.
- *    Slot s carries two doubles; coordinates that are not LASSO variables
- *    (imaginary parts of self-conjugate frequencies, conjugate twins on the
- *    planes k_{d-1} in {0, N_{d-1}/2}) are "ghosts" and are always 0.  The
- *    order of slots is internal; use ipm_pack_beta / ipm_unpack_beta to move
- *    between the beta layout and the canonical half spectrum.
+ *    H = N_0 ... N_{d-2} (floor(N_{d-1}/2) + 1) is the number of half-spectrum
+ *    slots.  Slot s carries two doubles; coordinates that are not LASSO
+ *    variables (imaginary parts of self-conjugate frequencies, conjugate twins
+ *    on the edge planes k_{d-1} = 0 and, for even N_{d-1}, k_{d-1} = N_{d-1}/2)
+ *    are "ghosts" and are always 0.  The order of slots is internal; use
+ *    ipm_pack_beta / ipm_unpack_beta to move between the beta layout and the
+ *    canonical half spectrum.
  *  - "canonical half spectrum": the orthonormal DFT v of Sec. 3 restricted to
- *    k_{d-1} in [0, N_{d-1}/2], row-major with the halved axis last, as
+ *    k_{d-1} in [0, floor(N_{d-1}/2)], row-major with the halved axis last, as
  *    interleaved (re, im) doubles: 2H doubles (the layout of numpy's rfftn).
  *  - Two-block vectors of the condensed system (p, q, r, z in kkt_apply and
  *    precond_apply) are [beta block | z block], 4H doubles.

@@ -59,33 +59,32 @@ struct ProfEntry {
   cudaEvent_t a, b;
 };
 
-// Supported transform lengths: 2^a 3^b 5^c 7^d with b, c, d <= 1.
+// Supported transform lengths: 2^a 3^b 5^c 7^d (even or odd).
 bool factor_ok(int L) {
   int m = L;
-  while (m % 2 == 0) m /= 2;
-  for (int q : {3, 5, 7})
-    if (m % q == 0) m /= q;
+  for (int q : {2, 3, 5, 7})
+    while (m % q == 0) m /= q;
   return m == 1;
 }
 
 // Radices for length L: with element budget E per thread, 16s (E = 16), then 8s
-// (E divisible by 8), then 4s (E divisible by 4), then 2s, and last a single 3,
-// 5 and 7 for the odd factors of L (in that order: every stage before the 5 and
-// the 7 then has a power-of-two Ns).
+// (E divisible by 8), then 4s (E divisible by 4), then 2s, and last the odd
+// factors of L: every 3, then every 5, then every 7.  Every power-of-two stage
+// then has a power-of-two Ns; the odd stages take any Ns.
 FftPlan make_plan(int L, int E) {
   FftPlan p{};
   p.L = L;
   int m = L;
-  bool odd[3] = {false, false, false};
+  int cnt[3] = {0, 0, 0};
   const int q[3] = {3, 5, 7};
   for (int i = 0; i < 3; ++i)
-    if (m % q[i] == 0) { odd[i] = true; m /= q[i]; }
+    while (m % q[i] == 0) { ++cnt[i]; m /= q[i]; }
   while (E % 16 == 0 && m % 16 == 0) { p.radix[p.nst++] = 16; m /= 16; }
   while (E % 8 == 0 && m % 8 == 0) { p.radix[p.nst++] = 8; m /= 8; }
   while (E % 4 == 0 && m % 4 == 0) { p.radix[p.nst++] = 4; m /= 4; }
   while (m % 2 == 0) { p.radix[p.nst++] = 2; m /= 2; }
   for (int i = 0; i < 3; ++i)
-    if (odd[i]) p.radix[p.nst++] = q[i];
+    for (int c = 0; c < cnt[i]; ++c) p.radix[p.nst++] = q[i];
   return p;
 }
 
@@ -270,15 +269,37 @@ bool make_cfg_reg(PassCfg& c, int kind, int L, long long npen, bool fp32, int P)
 }
 
 // Default choice without timing: E = 8 (12 with a factor 3), P as large as keeps
-// two tiles per SM, at least 2 (FP64) or 4 (FP32).
-void plan_tile(PassCfg& c, int L, int rows, long long npen, bool fp32) {
+// two tiles per SM, at least 2 (FP64) or 4 (FP32); failing that, the first
+// launchable (E, P).  Returns false when no shape fits the pass.
+bool plan_tile(PassCfg& c, int L, int rows, long long npen, bool fp32) {
   const int E = (L % 3 == 0) ? 12 : 8;
   int P = fp32 ? 16 : 8;
   const int Pmin = fp32 ? 4 : 2;
   while (P > Pmin && (npen + P - 1) / P < 2 * 152) P /= 2;
-  while ((P * L) % E != 0) P *= 2;
+  while ((P * L) % E != 0 && P <= 32) P *= 2;
   while (P > 1 && !make_cfg(c, L, rows, npen, fp32, E, P)) P /= 2;
-  make_cfg(c, L, rows, npen, fp32, E, P);
+  if (make_cfg(c, L, rows, npen, fp32, E, P)) return true;
+  const int Es[3] = {(L % 3 == 0) ? 12 : 16, (L % 3 == 0) ? 6 : 8, (L % 3 == 0) ? 6 : 4};
+  for (int e : Es)
+    for (int q = 1; q <= 32; q *= 2)
+      if (make_cfg(c, L, rows, npen, fp32, e, q)) return true;
+  return false;
+}
+
+// The FFT passes of a layout (length, shared-memory rows) all have a
+// launchable tile in FP64 (whose tiles are the larger).  Odd lengths without a
+// factor 3 need P = E pencils, so their P L / E threads exceed the block limit
+// above 512 (625 and 875).
+bool passes_launchable(const Layout& L) {
+  PassCfg c;
+  const bool odd = (L.Nl & 1) != 0;
+  if (!plan_tile(c, odd ? L.Nl : L.Nl / 2, odd ? L.Nl + 1 : L.Hl, 1, false)) return false;
+  if (L.d >= 2) {
+    const int Lr = (L.d == 3) ? L.N1 : L.N0;
+    if (!plan_tile(c, Lr, Lr, 1, false)) return false;
+  }
+  if (L.d == 3 && !plan_tile(c, L.N0, L.N0, 1, false)) return false;
+  return true;
 }
 
 dim3 pass_grid(const Layout& L, int kind, long long npen, int lgP) {
@@ -350,7 +371,7 @@ void tune_cache_append(const TuneKey& k, const TuneVal& v) {
 ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long long npen, bool fp32,
                      bool last = false, bool beta_form = false) {
   c.kind = kind;
-  plan_tile(c, L, rows, npen, fp32);
+  if (!plan_tile(c, L, rows, npen, fp32)) return fail_arg(h, "no launchable FFT tile for a pass of this grid");
   c.grid = pass_grid(h->lay, kind, npen, c.lgP);
   if (h->opt.tile_engine == 2) {
     // forced register engine: the given P (else the smallest launchable one
@@ -472,14 +493,21 @@ ipm_status plan_passes(sdft_ipm* h, PassSet& ps, bool fp32) {
   const Layout& L = h->lay;
   const void *t64, *t32;
   ipm_status s;
-  // middle pass: h = Nl/2 complex FFT, Hl rows, M pencils
+  // middle pass.  Even Nl: complex FFT of length Nl/2, Hl rows, M pencils.
+  // Odd Nl: complex FFT of length Nl carrying two pencils, Nl + 1 rows (the
+  // half spectra of both staged first), ceil(M/2) pencil pairs.
   {
     PassCfg& c = ps.mid;
-    if ((s = make_tables(h, L.Nl / 2, &t64, &t32)) != IPM_OK) return s;
+    const bool odd = (L.Nl & 1) != 0;
+    if ((s = make_tables(h, odd ? L.Nl : L.Nl / 2, &t64, &t32)) != IPM_OK) return s;
     c.tw = fp32 ? t32 : t64;
     if ((s = make_tables(h, L.Nl, &t64, &t32)) != IPM_OK) return s;
     c.twN = fp32 ? t32 : t64;
-    if ((s = tune_tile(h, c, 2, L.Nl / 2, L.Hl, L.M, fp32)) != IPM_OK) return s;
+    if (odd) {
+      if ((s = tune_tile(h, c, 2, L.Nl, L.Nl + 1, (L.M + 1) / 2, fp32)) != IPM_OK) return s;
+    } else {
+      if ((s = tune_tile(h, c, 2, L.Nl / 2, L.Hl, L.M, fp32)) != IPM_OK) return s;
+    }
   }
   if (L.d >= 2) {
     // row pass along the contiguous in-plane axis: rows of length Lr
@@ -742,8 +770,8 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   *out = nullptr;
   if (ndim < 1 || ndim > 3 || !dims) return fail_arg(nullptr, "ndim must be 1, 2 or 3");
   for (int i = 0; i < ndim; ++i) {
-    if (dims[i] < 2 || dims[i] % 2 || dims[i] > 1024 || !factor_ok((int)dims[i]))
-      return fail_arg(nullptr, "every extent must be even, of the form 2^a 3^b 5^c 7^d (b, c, d <= 1), and at most 1024");
+    if (dims[i] < 2 || dims[i] > 1024 || !factor_ok((int)dims[i]))
+      return fail_arg(nullptr, "every extent must be of the form 2^a 3^b 5^c 7^d, at least 2 and at most 1024");
   }
   ipm_options o;
   ipm_default_options(&o);
@@ -756,6 +784,11 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   for (int i = 0; i < ndim; ++i) h->dims[i] = (int)dims[i];
   h->lay = layout_init(ndim, ndim >= 2 ? (int)dims[0] : 1, ndim == 3 ? (int)dims[1] : 1, (int)dims[ndim - 1]);
   Layout& L = h->lay;
+  if (!passes_launchable(L)) {
+    g_create_error = "an extent has no launchable FFT tile (odd extents without a factor 3 must be at most 512)";
+    delete h;
+    return IPM_ERR_ARG;
+  }
   auto cleanup_fail = [&](ipm_status s) {
     g_create_error = h->err;
     ipm_destroy(h);

@@ -78,18 +78,21 @@ template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) 
 
 // ---------------------------------------------------------------------------
 // Layout of the half spectrum.  A grid N_0 x ... x N_{d-1} (row-major, last
-// axis contiguous) has H = Hl * M complex half-spectrum slots, Hl = N_l/2 + 1
-// along the halved last axis l and M = N_0 ... N_{d-2} in-plane frequencies.
-// Slot s = kl * M + k' (the halved axis is OUTERMOST), k' = k0 for d = 2 and
-// k' = k0 * N1 + k1 for d = 3.  The beta vector has 2H doubles: beta[2s] and
-// beta[2s+1] are the two real coordinates carried by slot s.
+// axis contiguous; every extent even or odd) has H = Hl * M complex
+// half-spectrum slots, Hl = floor(N_l/2) + 1 along the halved last axis l and
+// M = N_0 ... N_{d-2} in-plane frequencies.  Slot s = kl * M + k' (the halved
+// axis is OUTERMOST), k' = k0 for d = 2 and k' = k0 * N1 + k1 for d = 3.  The
+// beta vector has 2H doubles: beta[2s] and beta[2s+1] are the two real
+// coordinates carried by slot s.
 //
-// Slot classes (the representative rule of the real parametrisation):
-//   INTERIOR  1 <= kl <= N_l/2 - 1: the slot is its pair's representative,
+// Slot classes (the representative rule of the real parametrisation; the edge
+// planes are those with 2 kl = 0 mod N_l: kl = 0, and kl = N_l/2 for even N_l):
+//   INTERIOR  1 <= kl, 2 kl < N_l: the slot is its pair's representative,
 //             beta = (sqrt2 Re v, sqrt2 Im v);
-//   EDGE_REP  kl in {0, N_l/2}, k' lexicographically before -k': as INTERIOR;
-//   EDGE_SC   kl in {0, N_l/2}, k' = -k' (self-conjugate): beta = (v, ghost);
-//   EDGE_TWIN kl in {0, N_l/2}, the other member of a pair: (ghost, ghost).
+//   EDGE_REP  edge plane, k' lexicographically before -k': as INTERIOR;
+//   EDGE_SC   edge plane, k' = -k' (self-conjugate): beta = (v, ghost);
+//   EDGE_TWIN edge plane, the other member of a pair: (ghost, ghost).
+// On an odd in-plane axis only index 0 is its own negative.
 // Ghost coordinates are kept at exactly 0 in every vector.
 // ---------------------------------------------------------------------------
 enum SlotClass { INTERIOR = 0, EDGE_REP = 1, EDGE_SC = 2, EDGE_TWIN = 3 };
@@ -128,7 +131,7 @@ struct Layout {
   int d;          // 1, 2 or 3
   int N0, N1;     // in-plane lengths (d=3: N0 x N1; d=2: N0, N1 = 1; d=1: 1, 1)
   int Nl;         // last (halved) axis length
-  int Hl;         // Nl / 2 + 1
+  int Hl;         // floor(Nl / 2) + 1
   int M;          // in-plane count
   long long H;    // number of complex slots = Hl * M
   long long n;    // number of grid points = Nl * M
@@ -155,7 +158,7 @@ __host__ __device__ __forceinline__ int slot_class(const Layout& L, long long s)
   // H < 2^31 for every supported grid, so 32-bit division suffices
   const unsigned su = (unsigned)s;
   const int kl = (int)fast_div(su, L.divM);
-  if (kl >= 1 && kl <= L.Nl / 2 - 1) return INTERIOR;
+  if (kl >= 1 && 2 * kl < L.Nl) return INTERIOR;
   const int kp = (int)(su - (unsigned)kl * (unsigned)L.M);
   if (L.d == 1) return EDGE_SC;
   int k0, k1;

@@ -219,7 +219,7 @@ __device__ __forceinline__ void fft_stage(V* buf, int L, int lgNs, int lgP, int 
   __syncthreads();
 }
 
-// One stage of an odd radix R in {5, 7} that need not divide E: the P L / R
+// One stage of an odd radix R in {3, 5, 7} that need not divide E: the P L / R
 // butterflies w = tid + b nwork (b < ceil(E / R)) are spread over the working
 // threads with a guard, and Ns (the product of the earlier radices) may be any
 // integer.  Same formulas as fft_stage.
@@ -268,8 +268,9 @@ __device__ __forceinline__ void fft_stage_odd(V* buf, int L, int Ns, int lgP, in
 }
 
 // Full transform of the P pencils held in buf (length plan.L each), in place.
-// ODD: the plan may hold radix-5 / radix-7 stages (a separate instantiation, so
-// that the registers of those stages do not weigh on the other kernels).
+// ODD: the plan may hold radix-5 / radix-7 stages or several radix-3 stages,
+// all run by the guarded general-Ns stage (a separate instantiation, so that
+// the registers of those stages do not weigh on the other kernels).
 template <int E, bool INV, bool ODD, typename V>
 __device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, int PP, const V* __restrict__ tw,
                                          int tid, int nwork) {
@@ -277,9 +278,14 @@ __device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, i
   for (int s = 0; s < plan.nst; ++s) {
     const int R = plan.radix[s];
     if constexpr (ODD) {
-      // radices 5 and 7 come last (after the powers of two and a 3)
-      if (R == 5) fft_stage_odd<E, 5, INV>(buf, plan.L, Ns, lgP, PP, tw, tid, nwork);
-      if (R == 7) fft_stage_odd<E, 7, INV>(buf, plan.L, Ns, lgP, PP, tw, tid, nwork);
+      // the odd radices come last (after the powers of two)
+      if (R == 3 || R == 5 || R == 7) {
+        if (R == 3) fft_stage_odd<E, 3, INV>(buf, plan.L, Ns, lgP, PP, tw, tid, nwork);
+        if (R == 5) fft_stage_odd<E, 5, INV>(buf, plan.L, Ns, lgP, PP, tw, tid, nwork);
+        if (R == 7) fft_stage_odd<E, 7, INV>(buf, plan.L, Ns, lgP, PP, tw, tid, nwork);
+        Ns *= R;
+        continue;
+      }
     }
     Ns *= R;
     if constexpr (E % 16 == 0) {
@@ -292,7 +298,7 @@ __device__ __forceinline__ void fft_tile(V* buf, const FftPlan& plan, int lgP, i
       if (R == 4) fft_stage<E, 4, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
     }
     if (R == 2) fft_stage<E, 2, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
-    if constexpr (E % 3 == 0) {
+    if constexpr (!ODD && E % 3 == 0) {
       if (R == 3) fft_stage<E, 3, INV>(buf, plan.L, lgNs, lgP, PP, tw, tid, nwork);
     }
     lgNs += (R == 16) ? 4 : (R == 8) ? 3 : (R == 4 ? 2 : (R == 2 ? 1 : 0));   // odd radices come last

@@ -453,6 +453,118 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_pass_kernel(Pas
 }
 
 // ---------------------------------------------------------------------------
+// Middle pass for an odd halved-axis length Nl = 2 h + 1 (Sec. 3, the subspace
+// F for odd n: v_0 real and the pairs k = 1 .. h; no Nyquist plane, so the
+// edge plane is kl = 0 alone).  The real transforms of two pencils a and b run
+// as ONE complex transform of length Nl: with the full Hermitian columns
+// Y[Nl - k] = conj Y[k] of both, the inverse transform of Y_a + i Y_b is
+// y_a + i y_b with y_a, y_b real; after the mask the forward transform W of
+// m_a y_a / n + i m_b y_b / n separates as
+//   Y'_a[k] = (W_k + conj W_{-k}) / 2,   Y'_b[k] = (W_k - conj W_{-k}) / (2 i).
+// A tile holds P pencil pairs: pencils x0 + q (a) and x0 + P + q (b).  The
+// half spectra (h + 1 slots each) are staged first, one load per slot (the
+// PCG-form load also writes p back), then expanded to the Nl rows of the tile.
+// With from_real the input is the real signal y * m itself and only the
+// forward transform runs.
+// ---------------------------------------------------------------------------
+template <typename T, int E>
+__global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) middle_odd_kernel(PassArgs a) {
+  using V = typename cvec<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double scratch[32];
+  pdl_wait();
+  count_launch(a.sc);
+  if (pass_skipped(a)) return;
+  V* buf = reinterpret_cast<V*>(smem_raw);       // FFT rows 0..Nl-1, P pairs each (stride PP)
+  const int lgP = a.lgP, P = 1 << lgP, PP = a.PP;
+  const int Nl = a.lay.Nl, h = Nl >> 1, M = a.lay.M;
+  const int x0 = blockIdx.x * 2 * P;
+  const int tid = threadIdx.x, nwork = a.nwork, nthr = blockDim.x;
+  const V* tw = reinterpret_cast<const V*>(a.tw);
+  const V zero = cmake<V>((T)0, (T)0);
+  auto mask_bit = [&](int x, int n) -> bool {
+    return x < M && ((__ldg(&a.maskw[(size_t)(n >> 5) * M + x]) >> (n & 31)) & 1u);
+  };
+
+  if (a.from_real) {
+    for (int idx = tid; idx < P * Nl; idx += nthr) {
+      const int q = idx & (P - 1), n = idx >> lgP;
+      const int xa = x0 + q, xb = xa + P;
+      const T va = mask_bit(xa, n) ? (T)a.yreal[(size_t)xa * Nl + n] : (T)0;
+      const T vb = mask_bit(xb, n) ? (T)a.yreal[(size_t)xb * Nl + n] : (T)0;
+      buf[n * PP + q] = cmake<V>(va, vb);
+    }
+    __syncthreads();
+  } else {
+    // stage the half spectra: X[kl * 2P + pp] = slot kl * M + x0 + pp
+    V* X = buf;
+    for (int idx = tid; idx < (h + 1) * 2 * P; idx += nthr) {
+      const int pp = idx & (2 * P - 1), kl = idx >> (lgP + 1);
+      const int x = x0 + pp;
+      X[idx] = (x < M) ? load_slot<V>(a, (long long)kl * M + x) : zero;
+    }
+    __syncthreads();
+    // Z[k] = Y_a[k] + i Y_b[k]; on the edge plane kl = 0 only the real part is kept
+    V zr[E];
+    if (tid < nwork) {
+#pragma unroll
+      for (int b = 0; b < E; ++b) {
+        const int w = tid + b * nwork;
+        const int q = w & (P - 1), k = w >> lgP;
+        const bool cj = k > h;
+        const int kk = cj ? Nl - k : k;
+        V ya = X[kk * 2 * P + q], yb = X[kk * 2 * P + P + q];
+        if (kk == 0) { ya.y = (T)0; yb.y = (T)0; }
+        if (cj) { ya = cconj(ya); yb = cconj(yb); }
+        zr[b] = cmake<V>(ya.x - yb.y, ya.y + yb.x);
+      }
+    }
+    __syncthreads();
+    if (tid < nwork) {
+#pragma unroll
+      for (int b = 0; b < E; ++b) {
+        const int w = tid + b * nwork;
+        buf[(w >> lgP) * PP + (w & (P - 1))] = zr[b];
+      }
+    }
+    __syncthreads();
+    fft_tile<E, true, true>(buf, a.plan, lgP, PP, tw, tid, nwork);
+    // mask and 1/n: Re <-> sample n of pencil a, Im <-> sample n of pencil b
+    const T invn = (T)a.inv_n;
+    if (tid < nwork) {
+#pragma unroll
+      for (int b = 0; b < E; ++b) {
+        const int w = tid + b * nwork;
+        const int q = w & (P - 1), n = w >> lgP;
+        V z = buf[n * PP + q];
+        z.x *= mask_bit(x0 + q, n) ? invn : (T)0;
+        z.y *= mask_bit(x0 + P + q, n) ? invn : (T)0;
+        buf[n * PP + q] = z;
+      }
+    }
+    __syncthreads();
+  }
+  fft_tile<E, false, true>(buf, a.plan, lgP, PP, tw, tid, nwork);
+  double acc = 0.0;
+  auto store_all = [&](auto pq) {
+    for (int idx = tid; idx < (h + 1) * P; idx += nthr) {
+      const int q = idx & (P - 1), k = idx >> lgP;
+      const V wk = buf[k * PP + q];
+      const V wc = cconj(buf[(k == 0 ? 0 : Nl - k) * PP + q]);
+      const V ya = cscale(cadd(wk, wc), (T)0.5);
+      const V d = csub(wk, wc);
+      const V yb = cmake<V>(d.y * (T)0.5, -d.x * (T)0.5);
+      const int xa = x0 + q, xb = xa + P;
+      if (xa < M) store_slot<V, decltype(pq)::value>(a, (long long)k * M + xa, ya, acc);
+      if (xb < M) store_slot<V, decltype(pq)::value>(a, (long long)k * M + xb, yb, acc);
+    }
+  };
+  if (a.pcg_mode) store_all(std::true_type{});
+  else store_all(std::false_type{});
+  if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
+}
+
+// ---------------------------------------------------------------------------
 // Register-engine passes (fft_reg.cuh): lengths fixed at compile time, E = 16
 // values per thread, the first stage loading from and the last stage storing to
 // global memory; shared memory only for the exchanges between stages.
@@ -661,8 +773,21 @@ cudaError_t launch_typed(int kind, bool inv, const PassArgs& a, int threads, siz
 // the whole stage schedule) fixed at compile time.
 template <typename T, int E>
 cudaError_t launch_l(int kind, bool inv, const PassArgs& a, int threads, size_t smem, dim3 grid, cudaStream_t st) {
-  for (int s = 0; s < a.plan.nst; ++s)
+  if (kind == 2 && (a.lay.Nl & 1)) {
+    void (*fn)(PassArgs) = middle_odd_kernel<T, E>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_k(fn, grid, dim3(threads), smem, st, a);
+  }
+  // 5s, 7s or more than one 3: the general-Ns odd stages
+  int threes = 0;
+  for (int s = 0; s < a.plan.nst; ++s) {
     if (a.plan.radix[s] == 5 || a.plan.radix[s] == 7) return launch_typed<T, E, -1>(kind, inv, a, threads, smem, grid, st);
+    if (a.plan.radix[s] == 3) ++threes;
+  }
+  if (threes > 1) return launch_typed<T, E, -1>(kind, inv, a, threads, smem, grid, st);
   if constexpr (E == 4 || E == 8 || E == 16) {
     switch (a.plan.L) {
       case 128: return launch_typed<T, E, 128>(kind, inv, a, threads, smem, grid, st);

@@ -50,8 +50,12 @@ def test_default_options(lib):
     assert o.gap_tol == 1e-6 and o.cg_relative == 1 and o.tau == 0.995 and o.sigma == 0.1
 
 
-@pytest.mark.parametrize("dims,why", [((7,), "odd"), ((22,), "factor 11"), ((50,), "factor 5 twice"),
-                                      ((4, 4, 4, 4), "ndim"), ((2048,), "too long"), ((0,), "empty")])
+@pytest.mark.parametrize("dims,why", [((22,), "factor 11"), ((13,), "prime 13"), ((8, 33), "factor 11"),
+                                      ((4, 4, 4, 4), "ndim"), ((2048,), "too long"), ((1025,), "too long, odd"),
+                                      ((0,), "empty"), ((1,), "one"), ((8, 1), "one"),
+                                      ((625,), "odd, no factor 3, no launchable tile"),
+                                      ((875, 4), "odd, no factor 3, no launchable tile"),
+                                      ((4, 6, 625), "odd, no factor 3, no launchable tile")])
 def test_create_rejects_bad_grids_without_gpu_work(lib, dims, why):
     h = ctypes.c_void_p()
     d = (ctypes.c_int64 * len(dims))(*dims)

@@ -61,6 +61,30 @@ def test_batch_equals_standalone_solves(precision):
         assert np.array_equal(vb, v)
 
 
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+def test_batch_with_odd_members_equals_standalone_solves(precision):
+    """Odd and mixed-parity grids (Sec. 3, F for odd n) beside even ones in one batch."""
+    ws = [make_problem("custom", dims=d, missing=0.12, seed=60 + i)
+          for i, d in enumerate([(15, 21), (9, 7, 5), (45,), (16, 12, 8), (27, 10, 9)])]
+    opt = binding.default_options(precision=precision, lambda_relative=1, gap_tol=1e-9)
+    b = binding.ipm_create_batch([(w.dims, w.mask, w.y, 0.1) for w in ws], opt)
+    try:
+        res_b = binding.ipm_solve_batch(b)
+        spec_b = [_spectrum(binding.ipm_batch_member(b, i)) for i in range(len(ws))]
+    finally:
+        binding.ipm_destroy_batch(b)
+    for w, rb, vb in zip(ws, res_b, spec_b):
+        h = binding.ipm_create(w.dims, w.mask, w.y, 0.1, opt)
+        try:
+            r = binding.ipm_solve(h)
+            v = _spectrum(h)
+        finally:
+            binding.ipm_destroy(h)
+        assert rb["rel_gap"] <= 1e-9
+        assert rb["primal"] == r["primal"] and rb["cg_iters_total"] == r["cg_iters_total"]
+        assert np.array_equal(vb, v)
+
+
 def test_batch_members_match_oracle():
     ws = _problems()[:4]
     opt = binding.default_options(lambda_relative=1, gap_tol=1e-10)
@@ -81,7 +105,7 @@ def test_batch_members_match_oracle():
 def test_batch_rejects_a_bad_member_and_keeps_nothing():
     w = make_problem("custom", dims=(8, 8), seed=50)
     with pytest.raises(binding.IpmError) as e:
-        binding.ipm_create_batch([(w.dims, w.mask, w.y, 0.1), ((7, 8), w.mask, w.y, 0.1)])
+        binding.ipm_create_batch([(w.dims, w.mask, w.y, 0.1), ((11, 8), w.mask, w.y, 0.1)])
     assert e.value.status == binding.IPM_ERR_ARG
     assert "problem 1" in binding.ipm_last_error(None)
 

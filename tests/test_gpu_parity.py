@@ -575,6 +575,102 @@ def test_radix_5_and_7_solve_matches_oracle():
     assert abs(res["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
 
 
+ODD_SIZES = [(9,), (15,), (105,), (243,), (343,), (729,),
+             (15, 21), (21, 15), (16, 9), (9, 16), (27, 25), (7, 5),
+             (5, 7, 9), (9, 12, 15), (12, 10, 9), (7, 5, 3), (3, 3, 3), (49, 6, 35)]
+# even extents with repeated odd factors (several radix-3/5/7 stages)
+REPEATED_ODD_FACTOR_SIZES = [(36,), (18, 36), (72, 18, 12), (54, 50), (98,), (50, 98), (36, 20, 18)]
+
+
+def _check_g_and_k(dims, precision, seed, **opt):
+    n = int(np.prod(dims))
+    w = _workload(dims, seed=seed)
+    h = _handle(w, precision, **opt)
+    try:
+        prob = _oracle(w, 1.0)
+        rng = np.random.default_rng(seed + 1)
+        beta = rng.standard_normal(n)
+        # the layout holds exactly n LASSO coordinates, ghosts at 0
+        lib = oracle_to_lib(h, beta, dims)
+        assert np.abs(lib_to_half(h, lib) - oracle_to_half(beta, dims)).max() < 1e-14
+        assert np.count_nonzero(~ghost_mask(h, dims)) == n
+        q = torch.empty_like(lib)
+        binding.gapply(h, lib, q)
+        tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * np.linalg.norm(beta)
+        assert np.abs(lib_to_half(h, q) - oracle_to_half(prob.G(beta), dims)).max() < tol
+        assert np.all(q.cpu().numpy()[ghost_mask(h, dims)] == 0.0)
+        s1, nu1, s2, nu2 = _interior(n, rng)
+        binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+        S1, S2 = oipm.sigmas(s1, nu1, s2, nu2)
+        pb, pz = rng.standard_normal(n), rng.standard_normal(n)
+        pk = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
+        qk = torch.empty_like(pk)
+        binding.kkt_apply(h, pk, qk)
+        qb, qz = oipm.K_apply(prob.G, S1, S2, pb, pz)
+        H2 = pk.numel() // 2
+        scale = np.linalg.norm(np.concatenate([pb, pz])) * (1 + (S1 + S2).max())
+        tol = (1e-12 if precision == binding.IPM_FP64 else 5e-5) * scale
+        assert np.abs(lib_to_half(h, qk[:H2]) - oracle_to_half(qb, dims)).max() < tol
+        assert np.abs(lib_to_half(h, qk[H2:]) - oracle_to_half(qz, dims)).max() < 1e-13 * scale
+    finally:
+        binding.ipm_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+@pytest.mark.parametrize("dims", ODD_SIZES)
+def test_odd_extents_match_oracle(dims, precision):
+    """Odd extents (Sec. 3, the subspace F for odd n): the beta layout, G and K
+    against the oracle, on odd and mixed-parity grids (odd halved axis: the
+    two-pencil middle pass; odd in-plane axes: the general-Ns odd stages)."""
+    _check_g_and_k(dims, precision, seed=41)
+
+
+@pytest.mark.parametrize("dims", REPEATED_ODD_FACTOR_SIZES)
+def test_repeated_odd_factors_match_oracle(dims):
+    for precision in (binding.IPM_FP64, binding.IPM_MIXED):
+        _check_g_and_k(dims, precision, seed=43)
+
+
+@pytest.mark.parametrize("dims", [(15, 21), (9, 16), (7, 5, 3)])
+@pytest.mark.parametrize("tile_e,tile_p", [(4, 4), (8, 8), (16, 16), (12, 2), (6, 4)])
+def test_odd_extents_every_tile_shape(dims, tile_e, tile_p):
+    """Forced tile shapes on odd grids (a shape that does not fit a pass keeps
+    that pass's default)."""
+    _check_g_and_k(dims, binding.IPM_FP64, seed=45, tile_e=tile_e, tile_p=tile_p, autotune=0)
+
+
+@pytest.mark.parametrize("name,dims", [("custom", (243,)), ("custom", (15, 21)), ("custom", (9, 7, 5))])
+def test_odd_extents_solve_matches_oracle(name, dims):
+    w = _workload(dims, seed=47)
+    h = _handle(w, binding.IPM_FP64, gap_tol=1e-10)
+    try:
+        res = binding.ipm_solve(h)
+        H, n = binding.ipm_sizes(h)
+        v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+        binding.ipm_get_spectrum(h, v)
+        v = v.cpu().numpy()
+    finally:
+        binding.ipm_destroy(h)
+    prob = _oracle(w, res["lambda"])
+    assert res["status"] == binding.IPM_OK and res["rel_gap"] <= 1e-10
+    # lambda = 0.1 lambda_max: M_perp^T b through the odd middle pass's real-input path
+    assert abs(res["lambda"] - 0.1 * prob.lambda_max()) <= 1e-12 * prob.lambda_max()
+    ora = oipm.solve(prob, gap_tol=1e-10, sigma_rule="adaptive", sigma_min=0.03)
+    assert abs(res["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
+    vref = oracle_to_half(ora["beta"], w.dims)
+    assert np.abs(v - vref).max() <= 1e-6 * np.abs(vref).max()
+
+
+def test_odd_extents_mixed_solve_reaches_gap():
+    w = _workload((45, 27, 35), seed=49)
+    h = _handle(w, binding.IPM_MIXED, gap_tol=1e-6)
+    try:
+        res = binding.ipm_solve(h)
+    finally:
+        binding.ipm_destroy(h)
+    assert res["status"] == binding.IPM_OK and res["rel_gap"] <= 1e-6
+
+
 @pytest.mark.parametrize("precision,dims", [(binding.IPM_FP64, (64, 48)), (binding.IPM_MIXED, (32, 24, 16))])
 def test_programmatic_dependent_launch_is_bit_identical(precision, dims):
     """pdl = 1 only overlaps kernel launches (each kernel waits on the device for its
