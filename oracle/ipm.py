@@ -58,7 +58,8 @@ Our readings (the paper leaves them to MadNLP or prints them with typos)
 * PCG: x0 = 0, stop when sqrt(r^T z) <= cg_tol * sqrt(r0^T z0) (relative,
   the default) or sqrt(r^T z) <= cg_tol (absolute, as the paper's 1e-12 rule),
   or after max_cg iterations.  ``krylov="cr"`` uses preconditioned conjugate
-  residuals instead (Sec. 3.5 lists CR beside CG), with the same stop rule.
+  residuals and ``krylov="car"`` the conjugate A-residual method instead (Sec. 3.5
+  lists CR and CAr beside CG), with the same stop rule.
 """
 
 import numpy as np
@@ -154,6 +155,73 @@ def pcr(apply_K, apply_Pinv, rhs, tol, max_iter, relative=True):
     return x, it, np.sqrt(max(rho, 0.0))
 
 
+def pcar(apply_K, apply_Pinv, rhs, tol, max_iter, relative=True):
+    """Preconditioned conjugate A-residuals (CAr, named in Sec. 3.5 beside CG and CR for
+    these SPD systems; Montoison, Orban and Saunders 2023).  With M = P^{-1} = L L^T and
+    the split system L^T K L, CG minimises the K-norm of the error, CR the norm of
+    the residual, and CAr the norm of (L^T K L) times the residual, i.e.
+    w^T M w with w = K M r, over the same Krylov space.  It is CG in the inner product
+    of the cube of the split operator.  Written on the unsplit vectors:
+        z = M r, w = K z, y = M w       (w, y kept by recurrence after the start)
+        v = K y                          (the one product per iteration)
+        rho = y^T v, beta = rho / rho_prev,
+        p = z + beta p, Q = w + beta Q (= K p), U = v + beta U (= K M K p),
+        alpha = rho / (U^T M U),
+        x += alpha p, r -= alpha Q, w -= alpha U, y -= alpha M U, z = M r.
+    Starting costs one more product (w = K z).  Same stop rule as ``pcg``.
+    In floating point the recurred w and y drift from K M r once rho has fallen
+    by the unit round-off against the rho of the cycle's start (rho weighs the
+    residual by the cube of the operator), and r^T z then stalls above the stop
+    threshold: the method restarts there (w = K z, y = M w from the current
+    residual, beta = 0; one more product), as it does when rho or U^T M U is not
+    positive.  Returns (x, iterations, sqrt(r^T z))."""
+    def dot(a, b):
+        return a[0] @ b[0] + a[1] @ b[1]
+
+    def axpy(a, x, y):
+        return (y[0] + a * x[0], y[1] + a * x[1])
+
+    x = (np.zeros_like(rhs[0]), np.zeros_like(rhs[1]))
+    r = (rhs[0].copy(), rhs[1].copy())
+    z = apply_Pinv(*r)
+    rho_rz = dot(r, z)
+    stop = tol * np.sqrt(max(rho_rz, 0.0)) if relative else tol
+    eps = np.finfo(np.float64).eps
+    w = y = p = Q = U = None
+    rho_prev = rho_start = 0.0
+    it = 0
+    while it < max_iter and np.sqrt(max(rho_rz, 0.0)) > stop:
+        if w is None:                                   # (re)start: w and y from r
+            w = apply_K(*z)
+            y = apply_Pinv(*w)
+            p = None
+        v = apply_K(*y)
+        rho = dot(y, v)
+        if p is None:
+            rho_start = rho
+            p, Q, U = z, w, v
+        else:
+            if not (rho > eps * rho_start):
+                w = None                                # recurrences exhausted: restart
+                continue
+            beta = rho / rho_prev
+            p, Q, U = axpy(beta, p, z), axpy(beta, Q, w), axpy(beta, U, v)
+        MU = apply_Pinv(*U)
+        um = dot(U, MU)
+        if not (rho > 0.0 and um > 0.0):
+            break                                       # breakdown right after a (re)start
+        alpha = rho / um
+        x = axpy(alpha, p, x)
+        r = axpy(-alpha, Q, r)
+        w = axpy(-alpha, U, w)
+        y = axpy(-alpha, MU, y)
+        z = apply_Pinv(*r)
+        rho_rz = dot(r, z)
+        rho_prev = rho
+        it += 1
+    return x, it, np.sqrt(max(rho_rz, 0.0))
+
+
 # ---- Newton system ------------------------------------------------------------------
 
 def residuals(prob, Gbeta, w, sigma):
@@ -240,7 +308,8 @@ def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative
         res, mu = residuals(prob, Gbeta, w, sigma)
         Sig1, Sig2 = sigmas(w[2], w[4], w[3], w[5])
         rhs = condensed_rhs(res, w)
-        (dbeta, dz), ncg, _ = (pcr if krylov == "cr" else pcg)(lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b),
+        solver = {"cg": pcg, "cr": pcr, "car": pcar}[krylov]
+        (dbeta, dz), ncg, _ = solver(lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b),
                                   lambda a, b: Pinv_apply(Sig1, Sig2, a, b, precond_rho),
                                   rhs, cg_tol, max_cg, cg_relative)
         cg_counts.append(ncg)

@@ -203,3 +203,11 @@ def test_conjugate_residual_ipm_same_solution():
     b = ipm.solve(prob, gap_tol=1e-12, krylov="cr")
     assert b["status"] == "converged"
     assert np.abs(a["beta"] - b["beta"]).max() < 1e-7
+
+
+def test_conjugate_a_residual_ipm_same_solution():
+    prob = _masked((8, 8), 20, missing=0.2, lam_rel=0.2)
+    a = ipm.solve(prob, gap_tol=1e-12)
+    b = ipm.solve(prob, gap_tol=1e-12, krylov="car")
+    assert b["status"] == "converged"
+    assert np.abs(a["beta"] - b["beta"]).max() < 1e-7

@@ -225,3 +225,59 @@ def test_preconditioned_conjugate_residuals_solve_the_newton_system(dims):
     ref = np.linalg.solve(K, rhs)
     assert np.abs(np.concatenate([xb, xz]) - ref).max() < 1e-9 * np.abs(ref).max()
     assert it <= 2 * n + 2
+
+
+@pytest.mark.parametrize("dims", [(8,), (4, 6), (9,)])
+def test_conjugate_a_residuals_solve_the_newton_system(dims):
+    """CAr (Sec. 3.5 names it beside CG and CR): the condensed system solved by PCAR
+    equals the dense solve."""
+    prob = _problem(dims)
+    n = prob.n
+    rng = np.random.default_rng(43)
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    K = _dense(lambda e: np.concatenate(ipm.K_apply(prob.G, S1, S2, e[:n], e[n:])), 2 * n)
+    rhs = rng.standard_normal(2 * n)
+    (xb, xz), it, res = ipm.pcar(lambda a, b: ipm.K_apply(prob.G, S1, S2, a, b),
+                                 lambda a, b: ipm.Pinv_apply(S1, S2, a, b), tuple(np.split(rhs, 2)), 1e-13, 500)
+    ref = np.linalg.solve(K, rhs)
+    assert np.abs(np.concatenate([xb, xz]) - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_krylov_iterates_minimise_their_norms(k):
+    """After k iterations from x0 = 0 each method's iterate is the minimiser, over the
+    Krylov space span{M r0, (MK) M r0, ..., (MK)^{k-1} M r0} (M = P^{-1}), of its own
+    norm, found here by dense least squares on an orthonormal basis:
+    CG the K-norm of the error, CR r^T M r, CAr (K M r)^T M (K M r)."""
+    prob = _problem((4, 6))
+    n = prob.n
+    rng = np.random.default_rng(47)
+    s1, nu1, s2, nu2 = _interior_point(n, rng)
+    S1, S2 = ipm.sigmas(s1, nu1, s2, nu2)
+    K = _dense(lambda e: np.concatenate(ipm.K_apply(prob.G, S1, S2, e[:n], e[n:])), 2 * n)
+    M = _dense(lambda e: np.concatenate(ipm.Pinv_apply(S1, S2, e[:n], e[n:])), 2 * n)
+    M = (M + M.T) / 2
+    Lc = np.linalg.cholesky(M)                     # M = Lc Lc^T
+    b = rng.standard_normal(2 * n)
+    V = [M @ b]
+    for _ in range(k - 1):
+        V.append(M @ (K @ V[-1]))
+    Qb, _ = np.linalg.qr(np.stack(V, axis=1))
+    xs = np.linalg.solve(K, b)
+    Kh = np.linalg.cholesky(K)                     # K = Kh Kh^T
+    # each norm is || W (b - K Qb c) || for a fixed W; minimise over c
+    W = {"cg": Kh.T @ np.linalg.inv(K),            # ||e||_K = ||Kh^T K^{-1} r||
+         "cr": Lc.T,                               # r^T M r
+         "car": Lc.T @ K @ M}                      # (K M r)^T M (K M r)
+    split = lambda v: tuple(np.split(v, 2))
+    Kop = lambda a, c: ipm.K_apply(prob.G, S1, S2, a, c)
+    Mop = lambda a, c: ipm.Pinv_apply(S1, S2, a, c)
+    for name, fn in (("cg", ipm.pcg), ("cr", ipm.pcr), ("car", ipm.pcar)):
+        A = W[name] @ K @ Qb
+        c, *_ = np.linalg.lstsq(A, W[name] @ b, rcond=None)
+        x_ref = Qb @ c
+        (xb, xz), it, _ = fn(Kop, Mop, split(b), 0.0, k)
+        assert it == k
+        x = np.concatenate([xb, xz])
+        assert np.abs(x - x_ref).max() < 1e-8 * np.abs(xs).max(), name
