@@ -139,8 +139,15 @@ typedef struct {
   int krylov;           /* Krylov method for the Newton systems (Sec. 3.5 names CG, CR and CAr
                            for these SPD systems).  0 (default): preconditioned conjugate
                            gradients; 1: preconditioned conjugate residuals (one product K z
-                           per iteration, two update kernels; G beta is then recomputed every
-                           iteration, and refine_every must be 0)                          */
+                           per iteration, two update kernels); 2: conjugate A-residuals (CAr:
+                           the iterate minimising (K P^{-1} r)^T P^{-1} (K P^{-1} r) over the
+                           Krylov space; one product K y per iteration with y = P^{-1} K z
+                           kept by recurrence, one more product at each PCG start and at each
+                           restart, which happens when y^T K y has fallen by the unit round-off
+                           of the products' precision since the last start; restart products
+                           count in kkt_products).  With 1 or 2, G beta is recomputed every
+                           iteration and refine_every must be 0.  Changing the method with
+                           ipm_set_options allocates its vectors (4 x 4H doubles at most). */
 } ipm_options;
 
 typedef struct {

@@ -248,12 +248,12 @@ bool make_cfg(PassCfg& c, int L, int rows, long long npen, bool fp32, int E, int
 // Tile of the register engine: E = 16 values per thread, L / 16 threads per
 // pencil, P pencils per block (a power of two; the block a multiple of 32 threads,
 // at most 256, the kernels' launch bound).  Shared memory: row passes P padded rows (L + L/16 values), column
-// passes L x P, middle passes (2 h + 1) x P (half spectrum and exchange buffer).
+// passes L x P, middle passes (h + 1) x P (the half spectrum, reused for the exchanges).
 bool make_cfg_reg(PassCfg& c, int kind, int L, long long npen, bool fp32, int P) {
   if (L != 32 && L != 64 && L != 128 && L != 256 && L != 512) return false;
   const int esz = fp32 ? 8 : 16, threads = P * (L / 16);
   if (threads % 32 != 0 || threads > 256) return false;
-  const size_t rows = kind == 0 ? (size_t)(L + L / 16) : kind == 1 ? (size_t)L : (size_t)(2 * L + 1);
+  const size_t rows = kind == 0 ? (size_t)(L + L / 16) : kind == 1 ? (size_t)L : (size_t)(L + 1);
   const size_t smem = rows * P * esz;
   if (smem > 200 * 1024) return false;
   c.E = 16;
@@ -574,6 +574,8 @@ struct GSpec {
   bool refine = false;           // only when the device asks for an FP64 residual replacement
   bool exact = false;            // only when the device asks for an exact G beta (incremental mode)
   bool cr = false;               // conjugate residuals: w = K z (z of the handle) with z^T w
+  double* cr_in = nullptr;       // (cr) input and output of that product: z and w unless set
+  double* cr_out = nullptr;
   const double* p_in = nullptr;  // kkt_apply: p and q given by the caller
   double* q_out = nullptr;
 };
@@ -600,11 +602,12 @@ ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
       a.pcg_mode = g.pcg ? 1 : 0;
     }
     if (g.cr) {
-      if (first) { a.mapin = MAPIN_BETA; a.src = h->w.zv; }
+      double* in = g.cr_in ? g.cr_in : h->w.zv;
+      if (first) { a.mapin = MAPIN_BETA; a.src = in; }
       if (last) {
         a.mapout = MAPOUT_K;
-        a.p = h->w.zv;
-        a.q = h->w.wcr;
+        a.p = in;
+        a.q = g.cr_out ? g.cr_out : h->w.wcr;
         a.pcg_mode = 1;
         a.cr_mode = 1;
       }
@@ -723,8 +726,8 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (o.exact_residual < 0 || o.exact_residual > 1) return fail_arg(h, "exact_residual must be 0 or 1");
   if (!(o.precond_rho >= 0.0) || !std::isfinite(o.precond_rho)) return fail_arg(h, "precond_rho must be >= 0 and finite");
   if (o.pdl < 0 || o.pdl > 1) return fail_arg(h, "pdl must be 0 or 1");
-  if (o.krylov < 0 || o.krylov > 1) return fail_arg(h, "krylov must be 0 (CG) or 1 (CR)");
-  if (o.krylov == 1 && o.refine_every > 0) return fail_arg(h, "krylov = 1 (CR) does not combine with refine_every");
+  if (o.krylov < 0 || o.krylov > 2) return fail_arg(h, "krylov must be 0 (CG), 1 (CR) or 2 (CAr)");
+  if (o.krylov >= 1 && o.refine_every > 0) return fail_arg(h, "krylov = 1 (CR) or 2 (CAr) does not combine with refine_every");
   if (o.sigma_rule == 1 && !(o.sigma_min > 0 && o.sigma_min <= o.sigma_slow))
     return fail_arg(h, "sigma_min must lie in (0, sigma_slow]");
   if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
@@ -810,8 +813,11 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
                      &h->w.lam1, &h->w.lam2, &h->w.pa, &h->w.pb, &h->w.pc, &h->w.is1, &h->w.is2, &h->d_tmp,
                      &h->w.Gp, &h->w.Gx};
   for (double** p : vec2) CKC(dalloc(h, p, v2));
-  double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q, &h->w.rhs, &h->w.wcr, &h->w.ucr};
+  double** vec4[] = {&h->w.x, &h->w.r, &h->w.zv, &h->w.p, &h->w.q, &h->w.rhs};
   for (double** p : vec4) CKC(dalloc(h, p, v4));
+  // vectors of the other Krylov methods only when they are chosen
+  if (o.krylov >= 1) for (double** p : {&h->w.wcr, &h->w.ucr}) CKC(dalloc(h, p, v4));
+  if (o.krylov == 2) for (double** p : {&h->w.vcar, &h->w.Ucar}) CKC(dalloc(h, p, v4));
   CKC(dalloc(h, &h->d_U, (size_t)L.H * 2 * sizeof(double)));
   CKC(cudaMemsetAsync(h->d_U, 0, (size_t)L.H * 2 * sizeof(double), h->st));
   CKC(dalloc(h, &h->d_sc, sizeof(DevScalars)));
@@ -865,6 +871,12 @@ ipm_status ipm_set_options(sdft_ipm* h, const ipm_options* opt) {
   ipm_status s = check_options(h, *opt);
   if (s != IPM_OK) return s;
   const bool rel_changed = opt->lambda_relative != h->opt.lambda_relative;
+  // vectors of a Krylov method chosen only now
+  const size_t v4 = 4 * (size_t)h->lay.H * sizeof(double);
+  if (opt->krylov >= 1 && !h->w.wcr)
+    for (double** p : {&h->w.wcr, &h->w.ucr}) CK(dalloc(h, p, v4));
+  if (opt->krylov == 2 && !h->w.vcar)
+    for (double** p : {&h->w.vcar, &h->w.Ucar}) CK(dalloc(h, p, v4));
   h->opt = *opt;
   h->graph_valid = false;            // kernel arguments of the graph depend on the options
   if (rel_changed) {
@@ -962,11 +974,38 @@ ipm_status queue_residual_and_test(sdft_ipm* h, LoopCtl ipm_loop) {
 ipm_status queue_prepare(sdft_ipm* h, LoopCtl cg_loop) {
   Reduce red{h->d_partials, h->d_counter};
   ProfScope ps(h, 4);
-  CK(k_prepare(h->lay, h->w, red, h->d_sc, h->opt.cg_tol, h->opt.cg_relative, cg_loop, h->opt.precond_rho, h->st));
+  CK(k_prepare(h->lay, h->w, red, h->d_sc, h->opt.cg_tol, h->opt.cg_relative, cg_loop, h->opt.precond_rho,
+               h->opt.krylov == 2 ? 1 : 0, h->st));
   return IPM_OK;
 }
 
 ipm_status queue_pcg_iteration(sdft_ipm* h, LoopCtl cg_loop) {
+  const bool mixed = h->opt.precision == IPM_MIXED;
+  if (h->opt.krylov == 2) {
+    // conjugate A-residuals: at a (re)start w = K z and y = P^{-1} w (the passes
+    // and the kernel return at once otherwise), then v = K y and the two updates
+    GSpec st;
+    st.cr = true;
+    st.refine = true;
+    ipm_status s = run_g(h, mixed, st);
+    if (s != IPM_OK) return s;
+    {
+      ProfScope ps(h, 3);
+      CK(k_car_start(h->lay, h->w, h->d_sc, h->st));
+    }
+    GSpec k;
+    k.cr = true;
+    k.cr_in = h->w.ucr;
+    k.cr_out = h->w.vcar;
+    if ((s = run_g(h, mixed, k)) != IPM_OK) return s;
+    Reduce red{h->d_partials, h->d_counter};
+    ProfScope ps(h, 3);
+    // the restart threshold: the unit round-off of the products' precision
+    const double eps = mixed ? 1.1920928955078125e-07 : 2.220446049250313e-16;
+    CK(k_car_update_a(h->lay, h->w, red, h->d_sc, eps, cg_loop, h->st));
+    CK(k_car_update_b(h->lay, h->w, red, h->d_sc, h->opt.max_cg, cg_loop, h->st));
+    return IPM_OK;
+  }
   if (h->opt.krylov == 1) {
     // conjugate residuals: w = K z, then the two update kernels
     GSpec k;

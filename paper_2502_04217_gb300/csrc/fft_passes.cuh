@@ -630,13 +630,16 @@ __global__ void __launch_bounds__(256) col_reg_kernel(PassArgs a) {
 
 // Middle pass: the real transform of length Nl = 2 H along the halved axis, P
 // consecutive in-plane positions per block (pencil index fastest), TT = H / E
-// threads per pencil.  Shared memory: the loaded half spectrum ((H + 1) x P)
-// and one exchange buffer (H x P).  Same arithmetic as middle_pass_kernel: C2R
+// threads per pencil.  Shared memory: one (H + 1) x P tile, holding the loaded
+// half spectrum, then every exchange of both transforms, then the spectrum for
+// the post-processing.  Same arithmetic as middle_pass_kernel: C2R
 // pre-processing, inverse transform, mask and 1/n, forward transform, R2C
 // post-processing; the inverse transform leaves element t + TT m in the
-// registers from which the forward one starts, so no exchange joins them.
+// registers from which the forward one starts, so no exchange joins them.  The
+// FP32 kernel is held to 64 registers (no spills), so that 8 blocks of 128
+// threads share an SM.
 template <typename T, int H, int E>
-__global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) mid_reg_kernel(PassArgs a) {
   using V = typename cvec<T>::type;
   constexpr int TT = H / E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -648,7 +651,6 @@ __global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
   const int M = a.lay.M, Nl = a.lay.Nl, xp = (blockIdx.x << lgP) + p;
   const bool ok = xp < M;
   V* tile = reinterpret_cast<V*>(smem_raw);          // rows 0..H
-  V* ex = tile + ((H + 1) << lgP);                   // rows 0..H-1
   auto at = [&](int e) { return (e << lgP) + p; };
   const V* twh = reinterpret_cast<const V*>(a.tw);
   const V* twN = reinterpret_cast<const V*>(a.twN);
@@ -689,7 +691,8 @@ __global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
       const V d = cmul_i(cmulconj(csub(A, Bc), __ldg(&twN[k])));
       x[m] = cadd(sum, d);
     }
-    reg_fft<E, true, H>(x, t, twh, ex, at);
+    __syncthreads();                                 // pre-processing reads done: the tile is free
+    reg_fft<E, true, H>(x, t, twh, tile, at);
     // mask and 1/n: Re z_j <-> sample 2j, Im z_j <-> sample 2j+1 of pencil xp
     const T invn = (T)a.inv_n;
 #pragma unroll
@@ -700,12 +703,13 @@ __global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
       x[m].y *= ((mw >> ((2 * j + 1) & 31)) & 1u) ? invn : (T)0;
     }
   }
-  // forward transform; its exchanges use the tile buffer, whose last reads (the
-  // pre-processing) precede the inverse transform's exchange barrier
+  // forward transform; its exchanges reuse the tile once every thread has read
+  // its last exchange of the inverse transform
+  if (!a.from_real) __syncthreads();
   reg_fft<E, false, H>(x, t, twh, tile, at);
-  __syncthreads();                                   // last reads of ex / tile done
+  __syncthreads();                                   // last exchange reads done
 #pragma unroll
-  for (int m = 0; m < E; ++m) ex[at(t + TT * m)] = x[m];
+  for (int m = 0; m < E; ++m) tile[at(t + TT * m)] = x[m];
   __syncthreads();
   // R2C post-processing: X'_k = (Z_k + conj Z_{H-k})/2 - i W^k (Z_k - conj Z_{H-k})/2, X'_H = Re Z_0 - Im Z_0
   double acc = 0.0;
@@ -713,8 +717,8 @@ __global__ void __launch_bounds__(256) mid_reg_kernel(PassArgs a) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + TT * m;
-      const V zk = ex[at(k)];
-      const V zc = cconj(ex[at((H - k) & (H - 1))]);
+      const V zk = tile[at(k)];
+      const V zc = cconj(tile[at((H - k) & (H - 1))]);
       const V sum = cscale(cadd(zk, zc), (T)0.5);
       const V d = cscale(csub(zk, zc), (T)0.5);
       const V X = csub(sum, cmul_i(cmul(__ldg(&twN[k]), d)));

@@ -19,7 +19,9 @@ struct DevScalars {
   double pq;         // p^T K p of the last product
   double alpha_cg;   // rho / p^T K p
   double beta_cg;    // rho_new / rho (0 before the first product)
-  double zw_old;     // conjugate residuals: z^T K z of the previous iteration (0 at a PCG start)
+  double zw_old;     // conjugate residuals: z^T K z of the previous iteration (0 at a PCG start);
+                     // conjugate A-residuals: y^T K y of the previous iteration (0 at a (re)start)
+  double rho_car0;   // conjugate A-residuals: y^T K y at the start of the current cycle
   int cg_done;       // 1 once PCG has stopped (kernels then return at once)
   int cg_iter;       // PCG iterations of the current solve
   int cg_status;     // 0 ok, 1 hit max_cg, 2 non-finite value
@@ -43,7 +45,8 @@ struct DevScalars {
   int cg_total;      // PCG iterations over the solve
   int cg_max;        // largest PCG count of one IPM iteration
   int cg_cap_hit;    // some PCG solve stopped at max_cg
-  int refine_now;    // mixed precision: recompute the PCG residual in FP64 after this update
+  int refine_now;    // mixed precision: recompute the PCG residual in FP64 after this update;
+                     // conjugate A-residuals: (re)start product w = K z requested
   int refine_exit;   // ... because PCG had stopped (1) or periodically (0)
   int refinements;   // FP64 residual replacements over the solve
   int incr;          // 1: G beta is updated from the PCG products and recomputed only to confirm the stop

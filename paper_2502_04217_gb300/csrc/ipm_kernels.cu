@@ -203,7 +203,7 @@ __device__ __forceinline__ double precond_scale(double rho, const Layout& lay, c
 
 __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                            DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop,
-                                                           double rho_opt) {
+                                                           double rho_opt, int car) {
   pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     sc->cg_status = 0;
     sc->cg_stop = cg_relative ? cg_tol * sqrt(fmax(rho, 0.0)) : cg_tol;
     sc->cg_done = (sqrt(fmax(rho, 0.0)) <= sc->cg_stop) ? 1 : 0;
-    sc->refine_now = 0;
+    sc->refine_now = car ? 1 : 0;       // conjugate A-residuals start with w = K z
+    sc->rho_car0 = 0.0;
     if (!isfinite(rho)) { sc->cg_status = 2; sc->cg_done = 1; }
     set_cond(cg_loop, sc->cg_done ? 0u : 1u);
   }
@@ -427,6 +428,122 @@ __global__ void __launch_bounds__(kThreads) cr_update_b_kernel(long long n2, Ipm
     else if (conv) sc->cg_done = 1;
     else if (sc->cg_iter >= max_cg) { sc->cg_status = 1; sc->cg_done = 1; }
     sc->refine_now = 0;
+    set_cond(cg_loop, sc->cg_done ? 0u : 1u);
+  }
+}
+
+// Conjugate A-residuals (CAr; Sec. 3.5 names it beside CG and CR): CG in the
+// inner product of the cube of the split operator L^T K L (M = P^{-1} = L L^T),
+// i.e. the Krylov iterate minimising (K M r)^T M (K M r).  Vectors: z = M r,
+// w = K z, y = M w (both kept by recurrence), v = K y (the product of every
+// iteration), p, q = K p, U = K M K p.  A (re)start computes w = K z by one more
+// product (its passes run only while refine_now is set) and y here.
+__global__ void __launch_bounds__(kThreads) car_start_kernel(long long n2, IpmVectors w, DevScalars* sc) {
+  pdl_wait();
+  count_launch(sc);
+  if (sc->cg_done || !sc->refine_now) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->refinements += 1;     // the extra product
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double wb = w.wcr[i], wz = w.wcr[n2 + i];
+    const double a = w.pa[i], b = w.pb[i], c = w.pc[i];
+    w.ucr[i] = a * wb - b * wz;
+    w.ucr[n2 + i] = -b * wb + c * wz;
+  }
+}
+
+// After v = K y and sc->pq = y^T v = rho.  At a cycle start (zw_old = 0): beta = 0
+// and rho_car0 = rho.  Otherwise, when rho has fallen to restart_eps * rho_car0 or
+// below (the recurred w and y have drifted from K M r), no update is made and the
+// next iteration restarts from the current residual; else beta = rho / zw_old.
+// p = z + beta p, q = w + beta q, U = v + beta U, alpha = rho / U^T M U.
+__global__ void __launch_bounds__(kThreads) car_update_a_kernel(long long n2, IpmVectors w, double* partials,
+                                                                unsigned* counter, DevScalars* sc, double restart_eps,
+                                                                LoopCtl cg_loop) {
+  pdl_wait();
+  __shared__ double scratch[32];
+  count_launch(sc);
+  if (sc->cg_done) {
+    if (first_thread()) set_cond(cg_loop, 0u);
+    return;
+  }
+  const double rho = sc->pq, rho0 = sc->zw_old;
+  const bool first = !(rho0 > 0.0);
+  const bool restart = !first && !(rho > restart_eps * sc->rho_car0);
+  const double beta = (first || restart) ? 0.0 : rho / rho0;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  if (!restart) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+      double pb = w.zv[i], pz = w.zv[n2 + i], qb = w.wcr[i], qz = w.wcr[n2 + i];
+      double ub = w.vcar[i], uz = w.vcar[n2 + i];
+      if (!first) {
+        pb += beta * w.p[i];
+        pz += beta * w.p[n2 + i];
+        qb += beta * w.q[i];
+        qz += beta * w.q[n2 + i];
+        ub += beta * w.Ucar[i];
+        uz += beta * w.Ucar[n2 + i];
+      }
+      w.p[i] = pb; w.p[n2 + i] = pz;
+      w.q[i] = qb; w.q[n2 + i] = qz;
+      w.Ucar[i] = ub; w.Ucar[n2 + i] = uz;
+      const double a = w.pa[i], b = w.pb[i], c = w.pc[i];
+      v[0] += ub * (a * ub - b * uz) + uz * (-b * ub + c * uz);
+    }
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    if (restart) {
+      sc->refine_now = 1;
+      sc->zw_old = 0.0;
+      sc->alpha_cg = 0.0;
+      sc->refinements += 1;            // this iteration's product is not used
+    } else {
+      const double um = v[0];
+      sc->refine_now = 0;
+      sc->zw_old = rho;
+      if (first) sc->rho_car0 = rho;
+      if (!(rho > 0.0) || !(um > 0.0) || !isfinite(um)) { sc->cg_status = 2; sc->cg_done = 1; sc->alpha_cg = 0.0; }
+      else sc->alpha_cg = rho / um;
+    }
+    set_cond(cg_loop, sc->cg_done ? 0u : 1u);
+  }
+}
+
+// x += alpha p, r -= alpha q, w -= alpha U, y -= alpha M U, z = M r, rho = r^T z
+// and the stop test (nothing when the first half asked for a restart).
+__global__ void __launch_bounds__(kThreads) car_update_b_kernel(long long n2, IpmVectors w, double* partials,
+                                                                unsigned* counter, DevScalars* sc, int max_cg,
+                                                                LoopCtl cg_loop) {
+  pdl_wait();
+  __shared__ double scratch[32];
+  count_launch(sc);
+  if (sc->cg_done || sc->refine_now) return;
+  const double alpha = sc->alpha_cg;
+  double v[1] = {0.0};
+  const int ops[1] = {RED_SUM};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double a = w.pa[i], b = w.pb[i], c = w.pc[i];
+    w.x[i] += alpha * w.p[i];
+    w.x[n2 + i] += alpha * w.p[n2 + i];
+    const double rb = w.r[i] - alpha * w.q[i], rz = w.r[n2 + i] - alpha * w.q[n2 + i];
+    const double Ub = w.Ucar[i], Uz = w.Ucar[n2 + i];
+    w.wcr[i] -= alpha * Ub;
+    w.wcr[n2 + i] -= alpha * Uz;
+    w.ucr[i] -= alpha * (a * Ub - b * Uz);
+    w.ucr[n2 + i] -= alpha * (-b * Ub + c * Uz);
+    const double zb = a * rb - b * rz, zz = -b * rb + c * rz;
+    w.r[i] = rb; w.r[n2 + i] = rz;
+    w.zv[i] = zb; w.zv[n2 + i] = zz;
+    v[0] += rb * zb + rz * zz;
+  }
+  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double rho_new = v[0];
+    sc->rho = rho_new;
+    sc->cg_iter += 1;
+    const bool conv = sqrt(fmax(rho_new, 0.0)) <= sc->cg_stop;
+    if (!isfinite(rho_new)) { sc->cg_status = 2; sc->cg_done = 1; }
+    else if (conv) sc->cg_done = 1;
+    else if (sc->cg_iter >= max_cg) { sc->cg_status = 1; sc->cg_done = 1; }
     set_cond(cg_loop, sc->cg_done ? 0u : 1u);
   }
 }
@@ -651,8 +768,8 @@ cudaError_t k_certificate(const Layout& lay, const double* beta, const double* G
   return launch_k(certificate_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, beta, Gb, c, red.partials, red.counter, sc, gap_tol, max_ipm, loop);
 }
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, double rho, cudaStream_t st) {
-  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho);
+                      LoopCtl loop, double rho, int car, cudaStream_t st) {
+  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho, car);
 }
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
                          IpmVectors w, DevScalars* sc, double rho, cudaStream_t st) {
@@ -675,6 +792,19 @@ cudaError_t k_cr_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalar
 cudaError_t k_cr_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
                           cudaStream_t st) {
   return launch_k(cr_update_b_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+                  red.counter, sc, max_cg, loop);
+}
+cudaError_t k_car_start(const Layout& lay, IpmVectors w, DevScalars* sc, cudaStream_t st) {
+  return launch_k(car_start_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, sc);
+}
+cudaError_t k_car_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double restart_eps, LoopCtl loop,
+                           cudaStream_t st) {
+  return launch_k(car_update_a_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+                  red.counter, sc, restart_eps, loop);
+}
+cudaError_t k_car_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
+                           cudaStream_t st) {
+  return launch_k(car_update_b_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
                   red.counter, sc, max_cg, loop);
 }
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st) {

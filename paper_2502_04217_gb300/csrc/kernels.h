@@ -15,7 +15,9 @@ struct IpmVectors {
   double *is1, *is2;                          // 1/s1, 1/s2 at the current iterate (step kernels)
   double *x, *r, *zv, *p, *q;                 // PCG vectors, 2 blocks each (4H)
   double *rhs;                                // right-hand side of the current Newton system (4H)
-  double *wcr, *ucr;                          // conjugate residuals: w = K z and u = P^{-1} q (4H each)
+  double *wcr, *ucr;                          // conjugate residuals: w = K z and u = P^{-1} q (4H each);
+                                              // conjugate A-residuals: w = K z and y = P^{-1} w
+  double *vcar, *Ucar;                        // conjugate A-residuals: v = K y and U = v + beta U (4H each)
   double *Gp, *Gx;                            // incremental G beta: (G p)_beta of the last PCG product and
                                               // (G x)_beta = sum alpha (G p)_beta over the PCG solve (2H each)
 };
@@ -54,7 +56,7 @@ cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, do
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
                           DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st);
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, double rho, cudaStream_t st);
+                      LoopCtl loop, double rho, int car, cudaStream_t st);
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
                          IpmVectors w, DevScalars* sc, double rho, cudaStream_t st);
 cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st);
@@ -64,6 +66,11 @@ cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc
 cudaError_t k_cr_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st);
 cudaError_t k_cr_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
                           cudaStream_t st);
+cudaError_t k_car_start(const Layout& lay, IpmVectors w, DevScalars* sc, cudaStream_t st);
+cudaError_t k_car_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double restart_eps, LoopCtl loop,
+                           cudaStream_t st);
+cudaError_t k_car_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
+                           cudaStream_t st);
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st);
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           int sigma_rule, double sigma_min, cudaStream_t st);

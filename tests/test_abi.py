@@ -91,7 +91,8 @@ def test_default_options_of_the_solver_variants(lib):
 
 
 @pytest.mark.parametrize("field,value", [("tile_engine", 3), ("sigma_rule", 2), ("sigma_min", 0.0),
-                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0), ("pdl", 2), ("krylov", 2),
+                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0), ("pdl", 2), ("krylov", 3),
+                                         ("krylov", -1),
                                          ("precond_rho", float("inf"))])
 def test_create_rejects_bad_variant_options(lib, field, value):
     h = ctypes.c_void_p()
@@ -101,4 +102,16 @@ def test_create_rejects_bad_variant_options(lib, field, value):
     st = lib.ipm_create(ctypes.byref(h), 1, d, ctypes.cast(dummy, ctypes.c_void_p),
                         ctypes.cast(dummy, ctypes.c_void_p), 1.0, ctypes.byref(o), None)
     assert st == binding.IPM_ERR_ARG and field in binding.ipm_last_error(None)
+    assert h.value is None
+
+
+@pytest.mark.parametrize("krylov", [1, 2])
+def test_cr_and_car_reject_residual_replacement(lib, krylov):
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int64 * 1)(8)
+    dummy = (ctypes.c_double * 8)()
+    o = binding.default_options(krylov=krylov, refine_every=5)
+    st = lib.ipm_create(ctypes.byref(h), 1, d, ctypes.cast(dummy, ctypes.c_void_p),
+                        ctypes.cast(dummy, ctypes.c_void_p), 1.0, ctypes.byref(o), None)
+    assert st == binding.IPM_ERR_ARG and "refine_every" in binding.ipm_last_error(None)
     assert h.value is None

@@ -695,6 +695,50 @@ def test_programmatic_dependent_launch_is_bit_identical(precision, dims):
 
 
 @pytest.mark.parametrize("precision,dims", [(binding.IPM_FP64, (32, 24, 16)), (binding.IPM_FP64, (64, 48)),
+                                            (binding.IPM_FP64, (15, 21)), (binding.IPM_MIXED, (32, 24, 16))])
+def test_conjugate_a_residuals_match_oracle(precision, dims):
+    """krylov = 2 (conjugate A-residuals, with restarts): the same optimum as the oracle's
+    CAr solve, and in FP64 the same IPM iteration count.  The Krylov counts agree to
+    a couple of iterations: a restart fires when y^T K y has fallen by the unit
+    round-off, a level at which the FFT's and the direct DFT's rounding differ, so the
+    two sides may restart one iteration apart (one FP64 case came out 105 vs 106)."""
+    w = _workload(dims, seed=37)
+    h = _handle(w, precision, gap_tol=1e-8, krylov=2)
+    try:
+        res = binding.ipm_solve(h)
+    finally:
+        binding.ipm_destroy(h)
+    ora = oipm.solve(_oracle(w, res["lambda"]), gap_tol=1e-8, sigma_rule="adaptive", sigma_min=0.03, krylov="car")
+    assert res["status"] == binding.IPM_OK and ora["status"] == "converged"
+    tol = 1e-8 if precision == binding.IPM_FP64 else 1e-6
+    assert abs(res["primal"] - ora["primal"]) <= tol * abs(ora["primal"])
+    # the PCG solves cost their iterations plus the start and restart products
+    assert res["kkt_products"] > res["cg_iters_total"]
+    if precision == binding.IPM_FP64:
+        assert res["ipm_iters"] == ora["ipm_iters"]
+        total = sum(ora["cg_counts"])
+        assert abs(res["cg_iters_total"] - total) <= 2 + 0.02 * total
+
+
+def test_krylov_method_switched_after_create():
+    """ipm_set_options may switch CG -> CAr -> CR on a live handle (their vectors are
+    allocated then); every method reaches the same optimum."""
+    w = _workload((48, 64), seed=39)
+    h = _handle(w, binding.IPM_FP64, gap_tol=1e-9)
+    try:
+        prim = []
+        for k in (0, 2, 1, 0):
+            o = binding.default_options(precision=binding.IPM_FP64, lambda_relative=1, gap_tol=1e-9, krylov=k)
+            binding.ipm_set_options(h, o)
+            res = binding.ipm_solve(h)
+            assert res["status"] == binding.IPM_OK
+            prim.append(res["primal"])
+    finally:
+        binding.ipm_destroy(h)
+    assert max(prim) - min(prim) <= 1e-8 * abs(prim[0])
+
+
+@pytest.mark.parametrize("precision,dims", [(binding.IPM_FP64, (32, 24, 16)), (binding.IPM_FP64, (64, 48)),
                                             (binding.IPM_MIXED, (32, 24, 16))])
 def test_conjugate_residuals_match_oracle(precision, dims):
     """krylov = 1 (preconditioned conjugate residuals): the same optimum as the oracle's
