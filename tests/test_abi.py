@@ -115,3 +115,15 @@ def test_cr_and_car_reject_residual_replacement(lib, krylov):
                         ctypes.cast(dummy, ctypes.c_void_p), 1.0, ctypes.byref(o), None)
     assert st == binding.IPM_ERR_ARG and "refine_every" in binding.ipm_last_error(None)
     assert h.value is None
+
+
+@pytest.mark.parametrize("dims", [(9,), (16, 15), (15, 16, 8)])
+def test_noalloc_rejects_odd_extents_without_gpu_work(lib, dims):
+    """The allocation-free G product keeps its even 2^a 3^b extents: odd grids (which
+    ipm_create accepts) are refused before any GPU work."""
+    d = (ctypes.c_int64 * len(dims))(*dims)
+    dummy = (ctypes.c_double * 8)()
+    st = lib.gapply_noalloc(len(dims), d, ctypes.cast(dummy, ctypes.c_void_p), ctypes.cast(dummy, ctypes.c_void_p),
+                            ctypes.cast(dummy, ctypes.c_void_p), None)
+    assert st == binding.IPM_ERR_ARG
+    assert "even" in binding.ipm_last_error(None)
