@@ -582,9 +582,19 @@ ODD_SIZES = [(9,), (15,), (105,), (243,), (343,), (729,),
 REPEATED_ODD_FACTOR_SIZES = [(36,), (18, 36), (72, 18, 12), (54, 50), (98,), (50, 98), (36, 20, 18)]
 
 
-def _check_g_and_k(dims, precision, seed, **opt):
+def _plain_workload(dims, seed):
+    """Random signal and mask (about 20 % missing, at least one sample observed) for
+    grids too small for the sparse-spectrum generator."""
+    from paper_2502_04217_gb300.synth import Workload
+    rng = np.random.default_rng(seed)
+    mask = (rng.random(dims) > 0.2).astype(np.uint8)
+    mask.reshape(-1)[0] = 1
+    return Workload(tuple(dims), mask, rng.standard_normal(dims), 0.1)
+
+
+def _check_g_and_k(dims, precision, seed, w=None, **opt):
     n = int(np.prod(dims))
-    w = _workload(dims, seed=seed)
+    w = _workload(dims, seed=seed) if w is None else w
     h = _handle(w, precision, **opt)
     try:
         prob = _oracle(w, 1.0)
@@ -669,6 +679,39 @@ def test_odd_extents_mixed_solve_reaches_gap():
     finally:
         binding.ipm_destroy(h)
     assert res["status"] == binding.IPM_OK and res["rel_gap"] <= 1e-6
+
+
+# smallest and largest extents: length-1 and length-2 halved-axis transforms,
+# length-2 and length-3 in-plane passes, and the 1024 maximum on every axis
+EDGE_SIZES = [(2,), (3,), (4,), (2, 2), (2, 3), (3, 2), (3, 3), (2, 2, 2), (3, 2, 3), (2, 3, 4),
+              (1024,), (1024, 6), (6, 1024), (4, 6, 1024), (1024, 4, 2), (2, 1024, 3)]
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+@pytest.mark.parametrize("dims", EDGE_SIZES)
+def test_smallest_and_largest_extents_match_oracle(dims, precision):
+    _check_g_and_k(dims, precision, seed=51, w=_plain_workload(dims, 51))
+
+
+@pytest.mark.parametrize("dims", [(64,), (15, 21), (8, 6, 4)])
+def test_lambda_at_or_above_lambda_max_gives_zero(dims):
+    """Degenerate case: lambda >= ||M_perp^T b||_inf makes beta = 0 optimal (the
+    subgradient condition holds at 0); the GPU solve returns it."""
+    w = _workload(dims, seed=53)
+    h = _handle(w, binding.IPM_FP64, lam_rel=1.01, gap_tol=1e-9)
+    try:
+        res = binding.ipm_solve(h)
+        H, n = binding.ipm_sizes(h)
+        v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+        binding.ipm_get_spectrum(h, v)
+        v = v.cpu().numpy()
+    finally:
+        binding.ipm_destroy(h)
+    prob = _oracle(w, res["lambda"])
+    assert res["status"] == binding.IPM_OK
+    assert np.abs(v).max() <= 1e-6 * prob.lambda_max()
+    # the objective at beta = 0 is ||b||^2 / 2
+    assert abs(res["primal"] - 0.5 * float(prob.b @ prob.b)) <= 1e-8 * float(prob.b @ prob.b)
 
 
 @pytest.mark.parametrize("precision,dims", [(binding.IPM_FP64, (64, 48)), (binding.IPM_MIXED, (32, 24, 16))])

@@ -193,7 +193,7 @@ def test_training_steps_reduce_the_loss():
 def test_trained_network_beats_the_cold_start():
     """What the learned part gains: a network trained on 24 solved 32^3 instances
     starts held-out solves closer to the solution, so they need fewer IPM
-    iterations; the cold-start IPM stays the judge: both reach the same gap and
+    iterations; the cold-start IPM stays the arbiter: both reach the same gap and
     their objectives agree within it."""
     from paper_2502_04217_gb300 import warmstart as ws
     data = ws.Dataset(32, 24, seed=0, gap_tol=1e-8)
