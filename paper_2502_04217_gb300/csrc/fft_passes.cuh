@@ -8,12 +8,13 @@
 //   d = 3: row(inv) -> column(inv) -> middle -> column(fwd) -> row(fwd)
 // Row passes transform the contiguous in-plane axis, column passes the other
 // in-plane axis (stride N1), the middle pass the halved axis (stride M) through
-// a real transform of length Nl computed as a complex one of length Nl/2.
+// a real transform of length Nl: for even Nl a complex one of length Nl/2 per
+// pencil, for odd Nl one complex transform of length Nl per two pencils.
 //
-// The beta -> v map is folded into the first pass.  On the two edge planes
-// kl in {0, Nl/2} only representatives carry data; instead of filling their
-// conjugate twins we feed 2 v at the representative and 0 at the twin, and the
-// middle pass keeps only the real part of those two planes.  After the
+// The beta -> v map is folded into the first pass.  On the edge planes (kl = 0,
+// and kl = Nl/2 for even Nl) only representatives carry data; instead of filling
+// their conjugate twins we feed 2 v at the representative and 0 at the twin, and
+// the middle pass keeps only the real part of those planes.  After the
 // in-plane inverse transforms the edge planes of the true (Hermitian) input are
 // real, and Re(sum_k 2 v_k e_k) over representatives plus the self-conjugate
 // terms equals that real value, so the result is exact.
@@ -323,8 +324,8 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) col_pass_kernel(PassAr
 }
 
 // ---------------------------------------------------------------------------
-// Middle pass: pencils along the halved axis (Hl complex, stride M), P
-// consecutive in-plane positions x' per tile.  Computes, per pencil,
+// Middle pass for even Nl: pencils along the halved axis (Hl complex, stride
+// M), P consecutive in-plane positions x' per tile.  Computes, per pencil,
 //   x = C2R(X) (length Nl, unnormalised; Re taken on the two edge planes),
 //   y = x * m / n,   Y = R2C(y),
 // with the real transforms done as complex transforms of length h = Nl/2 on

@@ -68,7 +68,7 @@ enum MapOut { MAPOUT_NONE = 0, MAPOUT_BETA = 1, MAPOUT_K = 2 };
 // (2H per block); the work buffer holds H complex values of the pass type.
 struct PassArgs {
   Layout lay;
-  FftPlan plan;          // length L (row/column passes) or h = Nl/2 (middle pass)
+  FftPlan plan;          // length L (row/column passes); middle pass: h = Nl/2 (even Nl) or Nl (odd Nl)
   int lgP, PP;           // pencils per tile = 1 << lgP, smem pencil stride
   int nwork;             // threads carrying FFT work = P * L / E
   long long npencils;    // pencils of the pass (row: number of rows; middle: M)
