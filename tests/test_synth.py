@@ -1,6 +1,7 @@
 """The seeded workload generator (no GPU): shapes, mask geometry, seeds."""
 
 import numpy as np
+import pytest
 
 from paper_2502_04217_gb300.synth import batch_workloads, lattice_mask, make_problem, paper_signal
 
@@ -30,8 +31,11 @@ def test_batch_workload_shapes():
     assert len({w.dims[0] for w in ws}) >= 2
 
 
-def test_sparse_spectrum_is_what_was_planted():
-    w = make_problem("custom", dims=(16, 12), k=5, noise=0.0, missing=0.0, seed=3)
+@pytest.mark.parametrize("dims", [(16, 12), (15, 9), (16, 9), (9, 16), (7, 5, 9)])
+def test_sparse_spectrum_is_what_was_planted(dims):
+    """The planted frequencies lie on interior slots of the halved axis (for odd
+    extents too), so the signal's half spectrum has exactly those entries."""
+    w = make_problem("custom", dims=dims, k=5, noise=0.0, missing=0.0, seed=3)
     spec = np.fft.rfftn(w.y, norm="ortho").reshape(-1)
     big = np.flatnonzero(np.abs(spec) > 1e-9)
     assert sorted(big.tolist()) == sorted(int(f) for f in w.freqs)
@@ -42,6 +46,11 @@ def test_paper_generator():
     slots of the half spectrum), the noise is U(0, 1), and balls of radius 2 on a
     period-6 lattice remove 33/216 = 15.3 % of the samples ("about 15 %")."""
     N = 24
+    spec = np.fft.rfftn(paper_signal(N), norm="ortho")
+    big = {tuple(int(v) for v in k) for k in np.argwhere(np.abs(spec) > 1e-9)}
+    assert big == {(1, 2, 3), (1, N - 2, 3), (N - 1, 2, 3), (N - 1, N - 2, 3)}
+    # an odd side: the same three frequencies, no Nyquist entry
+    N = 27
     spec = np.fft.rfftn(paper_signal(N), norm="ortho")
     big = {tuple(int(v) for v in k) for k in np.argwhere(np.abs(spec) > 1e-9)}
     assert big == {(1, 2, 3), (1, N - 2, 3), (N - 1, 2, 3), (N - 1, N - 2, 3)}
