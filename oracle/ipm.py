@@ -287,7 +287,7 @@ def next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min):
 
 
 def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative=True,
-          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.01,
+          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.03,
           precond_rho=1.0, krylov="cg"):
     """Run the IPM; returns a dict with the point, counts and the certificate."""
     w = [np.array(v, dtype=np.float64, copy=True) for v in (w0 or starting_point(prob))]

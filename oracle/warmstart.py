@@ -21,6 +21,18 @@ conv(x, W)[v, o] = sum_{t in {-1,0,1}^3} sum_i x[v + t, i] W[t + 1, i, o]
 with f_i = min(k_i, N_i - k_i) / (N_i / 2) (0 for a missing axis).  Outputs:
 y[..., 0:2] correct the soft-threshold guess, beta0 = lambda (soft(c) + y[0:2]);
 y[..., 2:4] are logits of "coordinate is non-zero".
+
+The start point the IPM is given (``start_point``): with mu0 = mu_scale lambda^2 and
+p = sigmoid(logit) per coordinate,
+    beta0 = lambda (soft(c / lambda, 1) + y_corr),  z0 = |beta0| + (mu0 / lambda)(2 - p),
+    s1 = z0 + beta0,  s2 = z0 - beta0,  nu_i = mu0 / s_i,
+so every complementarity product s_i nu_i equals mu0 (the point lies on the
+central path's complementarity target for mu0), z0 > |beta0| keeps both slacks
+positive, and the rows z - beta - s2 = 0, z + beta - s1 = 0 of Eq. (slackproblem)
+hold exactly.  A coordinate predicted inactive (p = 0) gets the slack 2 mu0/lambda
+on both sides and nu1 = nu2 = lambda/2 (so nu1 + nu2 = lambda, the row-2 residual
+of Eq. (kkt) is 0 there); one predicted active (p = 1) gets mu0/lambda on the side
+of its sign.
 """
 
 import numpy as np
@@ -148,3 +160,16 @@ def targets(c_slots, bstar_slots, lam, dims, ghost):
     sup = (np.abs(b) > 1e-6 * lam).astype(float)
     sup[np.asarray(ghost).reshape(D0, D1, D2, 2)] = -1.0
     return t, sup
+
+
+def start_point(c, y_corr, logit, lam, mu_scale):
+    """Interior start point (beta, z, s1, s2, nu1, nu2) from a prediction, coordinate by
+    coordinate (any shape; ghosts are the caller's business): c = M_perp^T b, y_corr the
+    network's correction of the soft-threshold guess and logit its support logit."""
+    c, y_corr, logit = (np.asarray(a, dtype=np.float64) for a in (c, y_corr, logit))
+    mu0 = mu_scale * lam * lam
+    beta = lam * (soft1(c / lam) + y_corr)
+    p = 1.0 / (1.0 + np.exp(-logit))
+    z = np.abs(beta) + (mu0 / lam) * (2.0 - p)
+    s1, s2 = z + beta, z - beta
+    return beta, z, s1, s2, mu0 / s1, mu0 / s2
