@@ -50,3 +50,19 @@ def ghost_mask(h, dims):
     # pack a vector of all ones in every beta coordinate: ghosts come back as 0
     ones = oracle_to_lib(h, np.ones(n), dims).cpu().numpy()
     return ones == 0.0
+
+
+def half_to_beta(v_half, dims):
+    """Canonical half spectrum (interleaved re/im, flat) -> beta in the oracle's order:
+    the full spectrum is rebuilt by conjugate symmetry, v_{-k} = conj(v_k), then Eq. (beta)."""
+    dims = tuple(int(d) for d in dims)
+    Nl = dims[-1]
+    Hl = Nl // 2 + 1
+    v_half = np.asarray(v_half)
+    vh = (v_half[0::2] + 1j * v_half[1::2]).reshape(dims[:-1] + (Hl,))
+    full = np.zeros(dims, dtype=np.complex128)
+    full[..., :Hl] = vh
+    mirrored = vh[np.ix_(*[(-np.arange(N)) % N for N in dims[:-1]])] if len(dims) > 1 else vh
+    for kd in range(Hl, Nl):
+        full[..., kd] = np.conj(mirrored[..., Nl - kd])
+    return mapping.v_to_beta(full, dims)

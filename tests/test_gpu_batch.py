@@ -87,12 +87,16 @@ def test_batch_with_odd_members_equals_standalone_solves(precision):
 
 def test_batch_members_match_oracle():
     ws = _problems()[:4]
-    opt = binding.default_options(lambda_relative=1, gap_tol=1e-10)
-    b = binding.ipm_create_batch([(w.dims, w.mask, w.y, 0.1) for w in ws], opt)
+    probs = []
+    for w in ws:
+        prob = Problem(w.dims, w.mask.astype(bool), w.y, 1.0)
+        prob.lam = 0.1 * prob.lambda_max()          # the oracle's lambda, passed as an absolute value
+        probs.append(prob)
+    opt = binding.default_options(lambda_relative=0, gap_tol=1e-10)
+    b = binding.ipm_create_batch([(w.dims, w.mask, w.y, p.lam) for w, p in zip(ws, probs)], opt)
     try:
         res = binding.ipm_solve_batch(b)
-        for i, w in enumerate(ws):
-            prob = Problem(w.dims, w.mask.astype(bool), w.y, res[i]["lambda"])
+        for i, (w, prob) in enumerate(zip(ws, probs)):
             ora = oipm.solve(prob, gap_tol=1e-10)
             assert abs(res[i]["primal"] - ora["primal"]) <= 1e-8 * abs(ora["primal"])
             v = _spectrum(binding.ipm_batch_member(b, i))

@@ -121,17 +121,20 @@ def _layers(params_flat):
 
 
 def test_network_gradient_matches_reference():
+    from oracle import ipm as oipm
     dims = (8, 12, 16)
     w = make_problem("custom", dims=dims, missing=0.15, seed=60)
-    opt = binding.default_options(lambda_relative=1, gap_tol=1e-8)
-    h = binding.ipm_create(dims, w.mask, w.y, 0.1, opt)
+    prob = Problem(dims, w.mask.astype(bool), w.y, 1.0)
+    prob.lam = 0.1 * prob.lambda_max()
+    # the training target is the oracle's own solution (nothing the reference sees comes from the GPU)
+    bstar_o = oipm.solve(prob, gap_tol=1e-8)["beta"]
+    opt = binding.default_options(lambda_relative=0)
+    h = binding.ipm_create(dims, w.mask, w.y, prob.lam, opt)
     net = binding.ws_create(seed=7)
     try:
-        res = binding.ipm_solve(h)
+        res = {"lambda": prob.lam}
         H, n = binding.ipm_sizes(h)
-        pt = [torch.empty(2 * H, dtype=torch.float64, device="cuda") for _ in range(6)]
-        binding.ipm_get_point(h, pt)
-        bstar = pt[0]
+        bstar = oracle_to_lib(h, bstar_o, dims)
         loss = binding.ws_train_step(net, h, bstar, 0.0)
         npar = binding.ws_num_params(net)
         params = np.empty(npar, dtype=np.float32)
@@ -141,7 +144,6 @@ def test_network_gradient_matches_reference():
         y = torch.empty(H * 8, dtype=torch.float32, device="cuda")
         binding.ws_forward(net, h, y)
         # reference on the same slot grid
-        prob = Problem(dims, w.mask.astype(bool), w.y, res["lambda"])
         c_lib = oracle_to_lib(h, prob.c, dims).cpu().numpy()
         x = ows.features(c_lib, res["lambda"], dims)
         x = torch.as_tensor(x.astype(np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
@@ -167,6 +169,94 @@ def test_network_gradient_matches_reference():
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         cos = got @ ref / (np.linalg.norm(got) * np.linalg.norm(ref))
         assert rel < 0.05 and cos > 0.995, (rel, cos)
+    finally:
+        binding.ws_destroy(net)
+        binding.ipm_destroy(h)
+
+
+def _params(layers):
+    """FP32 parameter vector from per-layer (W [27][cout][cin], b [cout]) in the stored channel counts."""
+    return np.concatenate([np.concatenate([W.reshape(-1), b]) for W, b in layers]).astype(np.float32)
+
+
+def _zero_layers():
+    return [(np.zeros((27, cout, cin), np.float32), np.zeros(cout, np.float32))
+            for cin, cout in [(16, 32), (32, 32), (32, 32), (32, 8)]]
+
+
+@pytest.mark.parametrize("dims", [(6, 10, 14), (12, 20), (30,), (5, 9, 7)])
+def test_features_kernel_matches_oracle(dims):
+    """The input features of every slot against the oracle's definition, element by
+    element.  The network is set to pass four features straight to its output: the
+    centre tap of layer 1 splits each feature x into relu(x) and relu(-x), layers 2 and 3
+    copy them (identity centre tap), and layer 4 forms relu(x) - relu(-x) = x.  All
+    products are by 1 and sums have one non-zero term, so y is the BF16 feature exactly;
+    the oracle's FP64 feature is rounded to BF16 the same way (through FP32)."""
+    w = make_problem("custom", dims=dims, missing=0.1, seed=62)
+    prob = Problem(dims, w.mask.astype(bool), w.y, 1.0)
+    lam = 0.1 * prob.lambda_max()
+    h = binding.ipm_create(dims, w.mask, w.y, lam, binding.default_options(lambda_relative=0))
+    net = binding.ws_create(seed=9)
+    try:
+        H, n = binding.ipm_sizes(h)
+        c_lib = oracle_to_lib(h, prob.c, dims).cpu().numpy()
+        ref = ows.features(c_lib, lam, dims).reshape(-1, 8)
+        ref = torch.as_tensor(ref.astype(np.float32)).to(torch.bfloat16).float().numpy()
+        got = np.zeros_like(ref)
+        for half in (0, 1):
+            L = _zero_layers()
+            for i in range(8):
+                L[0][0][13, i, i] = 1.0
+                L[0][0][13, 8 + i, i] = -1.0
+            for l in (1, 2):
+                for o in range(16):
+                    L[l][0][13, o, o] = 1.0
+            for j in range(4):
+                L[3][0][13, j, 4 * half + j] = 1.0
+                L[3][0][13, j, 8 + 4 * half + j] = -1.0
+            binding.ws_set_params(net, _params(L))
+            y = torch.empty(H * 8, dtype=torch.float32, device="cuda")
+            binding.ws_forward(net, h, y)
+            got[:, 4 * half:4 * half + 4] = y.cpu().numpy().reshape(H, 8)[:, :4]
+        ulp = np.abs(ref) * 2.0 ** -8 + 1e-30
+        assert np.all(np.abs(got - ref) <= ulp), np.abs(got - ref).max()
+        assert np.mean(got == ref) > 0.99
+    finally:
+        binding.ws_destroy(net)
+        binding.ipm_destroy(h)
+
+
+@pytest.mark.parametrize("bias", [(0.25, -0.125, 0.0, 0.0), (-1.5, 2.0, 3.0, -2.5), (0.0, 0.0, -8.0, 8.0)])
+def test_start_point_kernel_matches_oracle(bias):
+    """The interior start point built from a prediction against the oracle's
+    start_point, element by element: every weight 0 and the last layer's bias set, so
+    the network's outputs are exactly (y0, y1, logit0, logit1) = bias at every slot;
+    the point then varies with c = M_perp^T b from slot to slot."""
+    dims = (12, 10, 16)
+    w = make_problem("custom", dims=dims, missing=0.1, seed=63)
+    prob = Problem(dims, w.mask.astype(bool), w.y, 1.0)
+    lam = 0.05 * prob.lambda_max()
+    h = binding.ipm_create(dims, w.mask, w.y, lam, binding.default_options(lambda_relative=0))
+    net = binding.ws_create(seed=10)
+    try:
+        L = _zero_layers()
+        L[3][1][:4] = bias
+        binding.ws_set_params(net, _params(L))
+        mu_scale = 0.5
+        binding.ws_predict(net, h, mu_scale)
+        H, n = binding.ipm_sizes(h)
+        pt = [torch.empty(2 * H, dtype=torch.float64, device="cuda") for _ in range(6)]
+        binding.ipm_get_point(h, pt)
+        got = [v.cpu().numpy() for v in pt]
+        c_lib = oracle_to_lib(h, prob.c, dims).cpu().numpy()
+        cc = np.arange(2 * H) & 1
+        y_corr = np.where(cc == 0, bias[0], bias[1])
+        logit = np.where(cc == 0, bias[2], bias[3])
+        ref = ows.start_point(c_lib, y_corr, logit, lam, mu_scale)
+        ghost = ghost_mask(h, dims)
+        for g, r in zip(got, ref):
+            assert np.all(g[ghost] == 0.0)
+            assert np.all(np.abs(g[~ghost] - r[~ghost]) <= 1e-12 * np.maximum(1.0, np.abs(r[~ghost])))
     finally:
         binding.ws_destroy(net)
         binding.ipm_destroy(h)
