@@ -67,7 +67,10 @@ typedef enum {
   IPM_ERR_OOM = 3,          /* device allocation failed                          */
   IPM_MAXITER = 4,          /* the IPM stopped at max_ipm before reaching gap_tol */
   IPM_KRYLOV_MAXITER = 5,   /* a PCG solve stopped at max_cg (solve continued)    */
-  IPM_NUMERICAL = 6         /* non-finite value or loss of positive definiteness */
+  IPM_NUMERICAL = 6,        /* non-finite value or loss of positive definiteness */
+  IPM_TIMEOUT = 7           /* a bounded device-side wait expired: the kernel gave up,
+                               released what it held and returned; the context stays
+                               usable (see ws_test_conv_stall)                      */
 } ipm_status;
 
 typedef enum { IPM_FP64 = 0, IPM_MIXED = 1 } ipm_precision;
@@ -241,7 +244,9 @@ ipm_status ipm_unpack_beta(sdft_ipm* h, const double* beta, double* v_half);
 /* Per-kernel timing with CUDA events around every launch (0 = off, default;
  * each call resets the counters).  ipm_profile_get returns, for kernel class
  * k (0: FFT row pass, 1: column pass, 2: middle pass, 3: PCG update, 4: other
- * IPM kernels), the number of launches and their summed duration in
+ * IPM kernels, 6: the Newton-system kernel that forms Sigma, P^{-1} and the
+ * right-hand side, 7: the step-length and step kernels, 8: the duality-gap
+ * certificate), the number of launches and their summed duration in
  * milliseconds since the last reset (timed only while profiling is on); for
  * k = 5 it returns the number of kernels the library launched since the last
  * reset, timed or not, and *ms = 0. */
@@ -262,14 +267,18 @@ ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms);
  *              handle-based API (the layout depends only on dims); p's ghost
  *              coordinates must be 0, q's are written as 0.
  *  stream      cudaStream_t the work is queued on (NULL = legacy default
- *              stream); the call returns without waiting for it.
+ *              stream).  The call queues one memset and kernels only (the
+ *              twiddle tables are built on the device) and returns without
+ *              waiting for the stream.
  * The caller still owns every input and output.  Scratch is one fixed
  * file-scope device array of about 4.7 MB that each GPU loading the library
- * keeps until the process exits.  The first call on a device (with that device
- * current) looks up the array's device address once; make that first call
- * before any stream capture.  All calls share the array and each rewrites what
- * it needs, so calls that overlap on the GPU (other streams, other host threads
- * on the same device) race: order them on one stream.  FP64 arithmetic. */
+ * keeps until the process exits.  The first call in each CUDA context (with
+ * the device current) looks up the array's device address once and caches it
+ * for that context; make that first call before any stream capture.  After
+ * cudaDeviceReset destroys a context that has made a call, do not call again
+ * in the process.  All calls share the array and each rewrites what it needs,
+ * so calls that overlap on the GPU (other streams, other host threads on the
+ * same device) race: order them on one stream.  FP64 arithmetic. */
 ipm_status gapply_noalloc(int ndim, const int64_t* dims, const uint8_t* mask, const double* p, double* q,
                           void* stream);
 
@@ -353,7 +362,7 @@ ipm_status ws_conv_forward(int cin, int cout, int d0, int d1, int d2, const uint
  * tcgen05 kernel skips, in every CTA, the copy of its input triple number
  * drop_triple (>= 1) together with its barrier arrival, and every pipeline wait
  * gives up after 2^wait_log2 polls (8..24).  That call must then return
- * IPM_ERR_CUDA ("a pipeline wait expired") without hanging, and the context
+ * IPM_TIMEOUT ("a pipeline wait expired") without hanging, and the context
  * stays usable.  IPM_ERR_ARG for out-of-range arguments. */
 ipm_status ws_test_conv_stall(int drop_triple, int wait_log2);
 /* Weight and bias gradients of such a convolution: dw[t][o][i] = sum_v dy[v][o]

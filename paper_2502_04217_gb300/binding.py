@@ -15,11 +15,12 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsdft_ipm.so")
 
-IPM_OK, IPM_ERR_ARG, IPM_ERR_CUDA, IPM_ERR_OOM, IPM_MAXITER, IPM_KRYLOV_MAXITER, IPM_NUMERICAL = range(7)
+IPM_OK, IPM_ERR_ARG, IPM_ERR_CUDA, IPM_ERR_OOM, IPM_MAXITER, IPM_KRYLOV_MAXITER, IPM_NUMERICAL, IPM_TIMEOUT = range(8)
 IPM_FP64, IPM_MIXED = 0, 1
 STATUS_NAMES = {0: "IPM_OK", 1: "IPM_ERR_ARG", 2: "IPM_ERR_CUDA", 3: "IPM_ERR_OOM", 4: "IPM_MAXITER",
-                5: "IPM_KRYLOV_MAXITER", 6: "IPM_NUMERICAL"}
-PROFILE_CLASSES = {"fft_row": 0, "fft_col": 1, "fft_middle": 2, "pcg_update": 3, "ipm": 4}
+                5: "IPM_KRYLOV_MAXITER", 6: "IPM_NUMERICAL", 7: "IPM_TIMEOUT"}
+PROFILE_CLASSES = {"fft_row": 0, "fft_col": 1, "fft_middle": 2, "pcg_update": 3, "ipm_other": 4, "prepare": 6,
+                   "step": 7, "certificate": 8}
 
 
 class ipm_options(ctypes.Structure):

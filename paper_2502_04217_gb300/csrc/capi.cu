@@ -54,6 +54,11 @@ struct PassSet {
   PassCfg row_inv_beta;     // first row pass reading a plain beta-layout vector (G and K products, residuals)
 };
 
+// Kernel classes of the per-launch timing (ipm_profile_get): 0 row, 1 column and
+// 2 middle FFT passes, 3 PCG updates, 4 other IPM kernels, 5 the launch counter (no
+// timing), 6 the Newton-system kernel (prepare), 7 the step kernels, 8 the certificate.
+constexpr int kProfClasses = 9, kProfPrepare = 6, kProfStep = 7, kProfCertificate = 8;
+
 struct ProfEntry {
   int cls;
   cudaEvent_t a, b;
@@ -121,8 +126,8 @@ struct sdft_ipm {
   bool prof = false;
   std::vector<ProfEntry> prof_live;
   std::vector<cudaEvent_t> ev_pool;
-  long long prof_count[5] = {0, 0, 0, 0, 0};
-  double prof_ms[5] = {0, 0, 0, 0, 0};
+  long long prof_count[kProfClasses] = {};
+  double prof_ms[kProfClasses] = {};
   unsigned long long launch_base = 0;   // device launch counter at the last profile reset
   // whole-solve CUDA graph (two nested conditional WHILE loops)
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};
@@ -285,6 +290,25 @@ bool plan_tile(PassCfg& c, int L, int rows, long long npen, bool fp32) {
       if (make_cfg(c, L, rows, npen, fp32, e, q)) return true;
   return false;
 }
+
+}  // namespace
+
+namespace sdft {
+bool default_tile(int L, int rows, long long npen, bool fp32, TileChoice* out) {
+  PassCfg c;
+  if (!plan_tile(c, L, rows, npen, fp32)) return false;
+  out->plan = c.plan;
+  out->E = c.E;
+  out->lgP = c.lgP;
+  out->PP = c.PP;
+  out->nwork = c.nwork;
+  out->threads = c.threads;
+  out->smem = c.smem;
+  return true;
+}
+}  // namespace sdft
+
+namespace {
 
 // The FFT passes of a layout (length, shared-memory rows) all have a
 // launchable tile in FP64 (whose tiles are the larger).  Odd lengths without a
@@ -966,14 +990,14 @@ ipm_status queue_residual_and_test(sdft_ipm* h, LoopCtl ipm_loop) {
   g.exact = incremental_gb(h) != 0;                    // incremental mode: only when a stop test is to be confirmed
   ipm_status s = run_g(h, false, g);                   // residual always in FP64
   if (s != IPM_OK) return s;
-  ProfScope ps(h, 4);
+  ProfScope ps(h, kProfCertificate);
   CK(k_certificate(L, h->w.beta, h->w.Gb, h->w.c, red, h->d_sc, o.gap_tol, o.max_ipm, ipm_loop, h->st));
   return IPM_OK;
 }
 
 ipm_status queue_prepare(sdft_ipm* h, LoopCtl cg_loop) {
   Reduce red{h->d_partials, h->d_counter};
-  ProfScope ps(h, 4);
+  ProfScope ps(h, kProfPrepare);
   CK(k_prepare(h->lay, h->w, red, h->d_sc, h->opt.cg_tol, h->opt.cg_relative, cg_loop, h->opt.precond_rho,
                h->opt.krylov == 2 ? 1 : 0, h->st));
   return IPM_OK;
@@ -1051,10 +1075,10 @@ ipm_status queue_pcg_iteration(sdft_ipm* h, LoopCtl cg_loop) {
 ipm_status queue_step(sdft_ipm* h) {
   Reduce red{h->d_partials, h->d_counter};
   {
-    ProfScope ps(h, 4);
+    ProfScope ps(h, kProfStep);
     CK(k_step_length(h->lay, h->w, red, h->d_sc, h->opt.tau, h->st));
   }
-  ProfScope ps(h, 4);
+  ProfScope ps(h, kProfStep);
   CK(k_step_update(h->lay, h->w, red, h->d_sc, h->opt.sigma, h->opt.sigma_slow, h->opt.sigma_rule,
                    h->opt.sigma_min, h->st));
   return IPM_OK;
@@ -1286,7 +1310,7 @@ ipm_status ipm_profile_enable(sdft_ipm* h, int on) {
   if (!h) return fail_arg(nullptr, "handle is NULL");
   prof_collect(h);
   h->prof = on != 0;
-  for (int k = 0; k < 5; ++k) { h->prof_count[k] = 0; h->prof_ms[k] = 0; }
+  for (int k = 0; k < kProfClasses; ++k) { h->prof_count[k] = 0; h->prof_ms[k] = 0; }
   ipm_status s = read_scalars(h);
   if (s != IPM_OK) return s;
   h->launch_base = h->h_sc->launches;
@@ -1294,7 +1318,7 @@ ipm_status ipm_profile_enable(sdft_ipm* h, int on) {
 }
 
 ipm_status ipm_profile_get(sdft_ipm* h, int k, int64_t* launches, double* ms) {
-  if (!h || k < 0 || k > 5) return fail_arg(h, "bad kernel class");
+  if (!h || k < 0 || k >= kProfClasses) return fail_arg(h, "bad kernel class");
   prof_collect(h);
   if (k == 5) {
     ipm_status s = read_scalars(h);

@@ -120,6 +120,15 @@ cudaError_t launch_k(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, c
   return cudaLaunchKernelEx(&cfg, fn, static_cast<KArgs>(args)...);
 }
 
+// The tile a pass gets without the autotuner (FFT length L, `rows` shared-memory
+// rows, npen pencils): the same choice as a handle with autotune = 0 (capi.cu).
+struct TileChoice {
+  FftPlan plan;
+  int E, lgP, PP, nwork, threads;
+  size_t smem;
+};
+bool default_tile(int L, int rows, long long npen, bool fp32, TileChoice* out);
+
 // Launchers (fft_passes.cu).  `pass_kind`: 0 row, 1 column, 2 middle.
 cudaError_t launch_pass(int pass_kind, bool inv, bool fp32, int E, const PassArgs& a, int threads,
                         size_t smem, dim3 grid, cudaStream_t st);

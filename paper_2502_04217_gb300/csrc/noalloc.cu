@@ -8,18 +8,22 @@
 // Scratch lives in one file-scope __device__ array of fixed size
 // (kNoAllocScratchBytes, about 4.7 MB) that every GPU which loads the library
 // keeps until the process exits.  Host code cannot use the array's name as a
-// device address, so the first call on each device (with that device current)
-// asks the runtime for the address once with cudaGetSymbolAddress and caches
-// it; make that first call before any stream capture.  Every call shares the
-// array and finds the previous call's contents: the parts that must start from
-// a known state (the launch counter, the packed mask, the twiddle tables) are
-// rewritten by each call.  Two calls whose work overlaps on the GPU (different
-// streams, or different host threads on one device) race on the array: order
-// them on one stream.
+// device address, so the first call in each CUDA context asks the runtime for
+// the address once with cudaGetSymbolAddress (the device current, the context
+// current) and caches it per context; make that first call before any stream
+// capture.  A context destroyed after its first call (cudaDeviceReset) must not
+// be followed by further calls in a new context whose handle reuses the old one.
+// Every call shares the array and finds the previous call's contents: the parts
+// that must start from a known state (the launch counter, the packed mask, the
+// twiddle tables) are rewritten on the device by each call, so a call queues
+// only kernels and one memset and returns without waiting for the stream.  Two
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads on one device) race on the array: order them on one stream.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 #include <string>
-#include <vector>
 
 #include "../../include/sdft_ipm.h"
 #include "internal.h"
@@ -43,9 +47,53 @@ constexpr size_t kNoAllocScratchBytes = kScalarBytes + kMaskBytes + kTableBytes 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 static_assert(sizeof(DevScalars) <= kScalarBytes, "scalar region too small");
 
-constexpr int kMaxDevices = 256;
+// Device address of the scratch array per CUDA context (looked up once per context).
+constexpr int kMaxContexts = 64;
 std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct CtxAddr {
+  CUcontext ctx;
+  void* addr;
+};
+CtxAddr g_addr[kMaxContexts] = {};
+int g_naddr = 0;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(f);
+  }
+  return fn;
+}
+
+// The scratch array's device address in the current context.  Called with
+// g_setup_mu held.  Without a context handle (no driver entry point) the address
+// is looked up on every call instead of cached.
+cudaError_t scratch_address(void** out) {
+  CUcontext ctx = nullptr;
+  CtxGetCurrentFn get = ctx_get_current();
+  const bool keyed = get && get(&ctx) == CUDA_SUCCESS && ctx;
+  if (keyed)
+    for (int i = 0; i < g_naddr; ++i)
+      if (g_addr[i].ctx == ctx) {
+        *out = g_addr[i].addr;
+        return cudaSuccess;
+      }
+  void* a = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  if (!a) return cudaErrorInvalidSymbol;
+  if (keyed && g_naddr < kMaxContexts) g_addr[g_naddr++] = {ctx, a};
+  *out = a;
+  return cudaSuccess;
+}
 
 bool length_ok(int64_t L) {
   if (L < 2 || L % 2 || L > 512) return false;
@@ -60,42 +108,30 @@ ipm_status arg_error(const char* msg) {
   return IPM_ERR_ARG;
 }
 
-// Tile plan of one FP64 pass: FFT length L, `rows` shared-memory rows, npen pencils.
-struct Plan {
-  FftPlan fft{};
-  int E = 8, lgP = 0, PP = 1, nwork = 0, threads = 64;
-  size_t smem = 0;
-};
-
-Plan plan_fp64(int L, int rows, long long npen) {
-  Plan c;
-  c.E = (L % 3 == 0) ? 12 : 8;
-  c.fft.L = L;
-  int m = L;
-  const bool three = (m % 3 == 0);
-  if (three) m /= 3;
-  while (c.E % 8 == 0 && m % 8 == 0) { c.fft.radix[c.fft.nst++] = 8; m /= 8; }
-  while (m % 4 == 0) { c.fft.radix[c.fft.nst++] = 4; m /= 4; }
-  while (m % 2 == 0) { c.fft.radix[c.fft.nst++] = 2; m /= 2; }
-  if (three) c.fft.radix[c.fft.nst++] = 3;
-  int P = 8;
-  while (P > 2 && (npen + P - 1) / P < 2 * 152) P /= 2;
-  while ((P * L) % c.E != 0) P *= 2;
-  while (P > 1 && ((P * L) / c.E > 512 || (size_t)rows * (P + 1) * 16 > 200 * 1024)) P /= 2;
-  while ((1 << c.lgP) < P) ++c.lgP;
-  c.PP = (P >= 8) ? P + 1 : P;
-  c.nwork = (P * L) / c.E;
-  c.threads = ((c.nwork + 31) / 32) * 32;
-  if (c.threads < 64) c.threads = 64;
-  c.smem = (size_t)rows * c.PP * 16;
-  return c;
-}
-
-void push_table(std::vector<double>& t, int L) {
-  for (int k = 0; k < L; ++k) {
-    const long double ang = 2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)L;
-    t.push_back((double)cosl(ang));
-    t.push_back((double)(-sinl(ang)));
+// The twiddle tables of the passes, back to back: tables of lengths L0..L3 (0: absent),
+// entry k of a length-L table exp(-2 pi i k / L) as (cos, -sin) of pi (2k / L).
+__global__ void noalloc_twiddles_kernel(double* __restrict__ t, int L0, int L1, int L2, int L3, DevScalars* sc) {
+  count_launch(sc);
+  const long long total = (long long)L0 + L1 + L2 + L3;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < total; j += (long long)gridDim.x * blockDim.x) {
+    long long k = j;
+    int L = L0;
+    if (k >= L0) {
+      k -= L0;
+      L = L1;
+      if (k >= L1) {
+        k -= L1;
+        L = L2;
+        if (k >= L2) {
+          k -= L2;
+          L = L3;
+        }
+      }
+    }
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)L, &sn, &cs);
+    t[2 * j] = cs;
+    t[2 * j + 1] = -sn;
   }
 }
 
@@ -115,59 +151,46 @@ extern "C" ipm_status gapply_noalloc(int ndim, const int64_t* dims, const uint8_
   const size_t mask_words = (size_t)((L.Nl + 31) / 32) * L.M;
   if (mask_words * 4 > kMaskBytes) return arg_error("gapply_noalloc: mask does not fit the fixed scratch");
 
-  // once per device, with that device current: the device address of the scratch array
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    record_error("gapply_noalloc: no usable current CUDA device");
-    return IPM_ERR_CUDA;
-  }
+  // once per CUDA context (the device current): the device address of the scratch array
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-      void* a = nullptr;
-      e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
-      if (e != cudaSuccess || !a) {
-        record_error((std::string("gapply_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e)).c_str());
-        return IPM_ERR_CUDA;
-      }
-      g_scratch_addr[dev] = a;
+    void* a = nullptr;
+    cudaError_t e = scratch_address(&a);
+    if (e != cudaSuccess) {
+      record_error((std::string("gapply_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e)).c_str());
+      return IPM_ERR_CUDA;
     }
-    base = (unsigned char*)g_scratch_addr[dev];
+    base = (unsigned char*)a;
   }
+  cudaError_t e = cudaSuccess;
   DevScalars* sc = (DevScalars*)base;
   uint32_t* maskw = (uint32_t*)(base + kScalarBytes);
   double* tables = (double*)(base + kScalarBytes + kMaskBytes);
   void* work = base + kScalarBytes + kMaskBytes + kTableBytes;
   cudaStream_t st = (cudaStream_t)stream;
 
-  // twiddle tables: row axis, column axis, h = Nl/2 and Nl
+  // twiddle tables, built on the device: row axis, column axis, h = Nl/2 and Nl
   const int Lrow = L.d == 3 ? L.N1 : L.N0, Lcol = L.N0, h = L.Nl / 2;
-  std::vector<double> t;
-  t.reserve(2 * (size_t)(Lrow + Lcol + h + L.Nl));
+  const int t_row = L.d >= 2 ? Lrow : 0, t_col = L.d == 3 ? Lcol : 0;
   const size_t off_row = 0;
-  if (L.d >= 2) push_table(t, Lrow);
-  const size_t off_col = t.size();
-  if (L.d == 3) push_table(t, Lcol);
-  const size_t off_h = t.size();
-  push_table(t, h);
-  const size_t off_N = t.size();
-  push_table(t, L.Nl);
+  const size_t off_col = off_row + 2 * (size_t)t_row;
+  const size_t off_h = off_col + 2 * (size_t)t_col;
+  const size_t off_N = off_h + 2 * (size_t)h;
 
   auto fail = [](cudaError_t err) {
     record_error((std::string("gapply_noalloc: ") + cudaGetErrorString(err)).c_str());
     return IPM_ERR_CUDA;
   };
   if ((e = cudaMemsetAsync(sc, 0, sizeof(DevScalars), st)) != cudaSuccess) return fail(e);
-  if ((e = cudaMemcpyAsync(tables, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-    return fail(e);
+  noalloc_twiddles_kernel<<<8, 256, 0, st>>>(tables, t_row, t_col, h, L.Nl, sc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
   if ((e = k_pack_mask(mask, maskw, L.Nl, L.M, sc, st)) != cudaSuccess) return fail(e);
 
-  auto args = [&](const Plan& c, long long npen, size_t tw_off) {
+  auto args = [&](const TileChoice& c, long long npen, size_t tw_off) {
     PassArgs a{};
     a.lay = L;
-    a.plan = c.fft;
+    a.plan = c.plan;
     a.lgP = c.lgP;
     a.PP = c.PP;
     a.nwork = c.nwork;
@@ -182,7 +205,8 @@ extern "C" ipm_status gapply_noalloc(int ndim, const int64_t* dims, const uint8_
     return a;
   };
   auto grid1 = [](long long npen, int lgP) { return dim3((unsigned)((npen + (1 << lgP) - 1) >> lgP)); };
-  const Plan mid = plan_fp64(h, L.Hl, L.M);
+  TileChoice mid{}, row{}, col{};
+  if (!default_tile(h, L.Hl, L.M, false, &mid)) return arg_error("gapply_noalloc: no launchable tile");
   if (L.d == 1) {
     PassArgs a = args(mid, L.M, off_h);
     a.mapin = MAPIN_BETA;
@@ -194,8 +218,9 @@ extern "C" ipm_status gapply_noalloc(int ndim, const int64_t* dims, const uint8_
     return IPM_OK;
   }
   const long long nrows = L.H / Lrow;
-  const Plan row = plan_fp64(Lrow, Lrow, nrows);
-  const Plan col = L.d == 3 ? plan_fp64(Lcol, Lcol, (long long)L.N1 * L.Hl) : Plan{};
+  if (!default_tile(Lrow, Lrow, nrows, false, &row) ||
+      (L.d == 3 && !default_tile(Lcol, Lcol, (long long)L.N1 * L.Hl, false, &col)))
+    return arg_error("gapply_noalloc: no launchable tile");
   const dim3 gcol((unsigned)((L.N1 + (1 << col.lgP) - 1) >> col.lgP), (unsigned)L.Hl);
   {
     PassArgs a = args(row, nrows, off_row);

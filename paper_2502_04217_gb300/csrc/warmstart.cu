@@ -551,7 +551,7 @@ ipm_status sync_check(cudaStream_t st) {
   CKW(conv_tc_take_error(&code, st));
   if (code)
     return ws_err("tensor-core convolution: a pipeline wait expired (code " + std::to_string(code) + ")",
-                  IPM_ERR_CUDA);
+                  IPM_TIMEOUT);
   return IPM_OK;
 }
 

@@ -168,7 +168,7 @@ def test_config_512_warm_start_mixed_certified():
     finally:
         binding.ipm_destroy(h64)
     err = _coefficient_error(vw, v64)
-    assert err <= 1e-2
+    assert err <= 1e-3
     print(f"PARITY 3d 512^3 warm mixed: oracle gap {gapw:.3e} (GPU {rw['rel_gap']:.3e}), {rw['ipm_iters']} IPM / "
           f"{rw['cg_iters_total']} PCG; cold FP64: oracle gap {gap64:.3e}, {r64['ipm_iters']} IPM; coefficient "
           f"difference warm mixed vs cold FP64 (both at 1e-6): {err:.3e} of max |v|")

@@ -66,7 +66,7 @@ def test_conv_forward_matches_reference(cin, cout, dims):
 def test_conv_pipeline_wait_expires_with_an_error():
     """Failure detection without a GPU fault: one TMA copy of the tcgen05 pipeline
     never arrives (a barrier nothing completes); every pipeline wait is bounded,
-    so the call returns IPM_ERR_CUDA instead of hanging, and the next call on the
+    so the call returns IPM_TIMEOUT instead of hanging, and the next call on the
     same context computes the right result."""
     dims, cin, cout = (3, 40, 256), 32, 32
     rng = np.random.default_rng(3)
@@ -78,7 +78,7 @@ def test_conv_pipeline_wait_expires_with_an_error():
     binding.ws_test_conv_stall(5, 14)
     with pytest.raises(binding.IpmError) as e:
         binding.ws_conv_forward(cin, cout, dims, *args, y)
-    assert e.value.status == binding.IPM_ERR_CUDA and "expired" in str(e.value)
+    assert e.value.status == binding.IPM_TIMEOUT and "expired" in str(e.value)
     binding.ws_conv_forward(cin, cout, dims, *args, y)
     W = w.float().numpy().reshape(3, 3, 3, cout, cin).transpose(0, 1, 2, 4, 3)
     ref = np.maximum(ows.conv3d(x.float().numpy().astype(np.float64), W.astype(np.float64), b.astype(np.float64)), 0)
