@@ -54,6 +54,22 @@ Our readings (the paper leaves them to MadNLP or prints them with typos)
   After a PCG solve that stopped at max_cg (an inexact direction) the fixed rule
   applies instead: with the aggressive centring, mu then ran to 0 while the gap
   stalled.
+* Single-step predictor-corrector (``sigma_rule="single"``), the adaptation of
+  Mehrotra's method to one Krylov solve per iteration that Sec. 5 proposes (its form
+  is ours).  Mehrotra's method solves two systems with the same K per iteration:
+  the affine-scaling predictor (sigma = 0), then the corrector whose complementarity
+  rows target sigma mu e - ds_aff o dnu_aff with sigma = (mu_aff / mu)^3.  Here the
+  predictor costs no Krylov solve: it is P^{-1} rhs_aff with the closed-form P^{-1}
+  of Eq. (invprecond1).  P differs from K by [G - I, 0; 0, 0] = -[M^T M, 0; 0, 0]
+  (M the rows of missing samples), so the estimate is exact on the complement of
+  the span of the missing samples and wholly exact when none is missing (the
+  asymptotic spectrum result Prop. limitprecond is the same statement for P^{-1} K).
+  alpha_aff = min(1, largest step keeping (s, nu) >= 0 along the predictor),
+  mu_aff = (s + alpha_aff ds)^T (nu + alpha_aff dnu) / 2n, sigma = (mu_aff / mu)^3
+  clamped to [sigma_min, sigma_max], and the one Krylov solve is the corrector's.
+  ``sigma_rule="mehrotra"`` is the two-solve method (exact predictor), kept for
+  comparison.  After a PCG solve that stopped at max_cg the next direction takes
+  the fixed rule and no second-order term.
 * Stop when the relative duality gap (``Problem.certificate``) is <= gap_tol.
 * PCG: x0 = 0, stop when sqrt(r^T z) <= cg_tol * sqrt(r0^T z0) (relative,
   the default) or sqrt(r^T z) <= cg_tol (absolute, as the paper's 1e-12 rule),
@@ -279,6 +295,41 @@ def starting_point(prob):
     return [beta, z, z.copy(), z.copy(), nu, nu.copy()]
 
 
+def affine_predictor(prob, w, res_aff, Sig1, Sig2, solve_K=None, rho=1.0):
+    """Affine-scaling predictor of Mehrotra's method: the Newton direction for sigma = 0.
+    With solve_K (a Krylov solve of K d = rhs) it is the exact direction; without it,
+    P^{-1} rhs (Sec. 3.5): P differs from K only by [G - I, 0; 0, 0], minus the projector
+    onto the missing samples, so the estimate is exact on the complement of that subspace
+    (and wholly exact without missing samples).  Returns (dbeta, dz, ds1, ds2, dnu1, dnu2,
+    Krylov iterations)."""
+    rhs = condensed_rhs(res_aff, w)
+    if solve_K is not None:
+        (db, dz), its = solve_K(rhs)
+    else:
+        db, dz = Pinv_apply(Sig1, Sig2, rhs[0], rhs[1], rho)
+        its = 0
+    return (db, dz) + back_substitute(res_aff, w, db, dz) + (its,)
+
+
+def predictor_corrector(prob, w, Gbeta, Sig1, Sig2, sigma_min, sigma_max, solve_K=None, rho=1.0):
+    """Mehrotra's centring and second-order correction from an affine predictor.
+
+    alpha_aff = min(1, largest step keeping (s, nu) >= 0 along the predictor),
+    mu_aff = ((s + alpha_aff ds)^T (nu + alpha_aff dnu)) / 2n, sigma = (mu_aff / mu)^3
+    clamped to [sigma_min, sigma_max], and the complementarity rows of the corrector
+    system target sigma mu e - ds_aff o dnu_aff:
+        r_ci = s_i o nu_i - sigma mu e + ds_i,aff o dnu_i,aff.
+    Returns (residuals of the corrector system, sigma, predictor's Krylov iterations)."""
+    res_aff, mu = residuals(prob, Gbeta, w, 0.0)
+    _, _, ds1, ds2, dn1, dn2, its = affine_predictor(prob, w, res_aff, Sig1, Sig2, solve_K, rho)
+    s1, s2, nu1, nu2 = w[2], w[3], w[4], w[5]
+    a_aff = min(1.0, max_step((s1, s2, nu1, nu2), (ds1, ds2, dn1, dn2)))
+    mu_aff = ((s1 + a_aff * ds1) @ (nu1 + a_aff * dn1) + (s2 + a_aff * ds2) @ (nu2 + a_aff * dn2)) / (2 * prob.n)
+    sigma = min(sigma_max, max(sigma_min, (mu_aff / mu) ** 3))
+    (r_d, r_z, r_p1, r_p2, r_c1, r_c2), _ = residuals(prob, Gbeta, w, sigma)
+    return (r_d, r_z, r_p1, r_p2, r_c1 + ds1 * dn1, r_c2 + ds2 * dn2), sigma, its
+
+
 def next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min):
     """Centring parameter for the next direction after a step of length alpha."""
     if rule == "adaptive":
@@ -288,11 +339,12 @@ def next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min):
 
 def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative=True,
           sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.03,
-          precond_rho=1.0, krylov="cg"):
+          precond_rho=1.0, krylov="cg", sigma_max=1.0):
     """Run the IPM; returns a dict with the point, counts and the certificate."""
     w = [np.array(v, dtype=np.float64, copy=True) for v in (w0 or starting_point(prob))]
     sigma = sigma0
-    cg_counts = []
+    cg_counts, pred_counts, sigmas_used = [], [], []
+    after_cap = False
     status = "maxiter"
     for it in range(max_ipm + 1):
         beta = w[0]
@@ -305,20 +357,34 @@ def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative
             break
         if it == max_ipm:
             break
-        res, mu = residuals(prob, Gbeta, w, sigma)
         Sig1, Sig2 = sigmas(w[2], w[4], w[3], w[5])
-        rhs = condensed_rhs(res, w)
         solver = {"cg": pcg, "cr": pcr, "car": pcar}[krylov]
-        (dbeta, dz), ncg, _ = solver(lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b),
-                                  lambda a, b: Pinv_apply(Sig1, Sig2, a, b, precond_rho),
-                                  rhs, cg_tol, max_cg, cg_relative)
+        apply_K = lambda a, b: K_apply(prob.G, Sig1, Sig2, a, b)
+        apply_Pinv = lambda a, b: Pinv_apply(Sig1, Sig2, a, b, precond_rho)
+        n_pred = 0
+        if sigma_rule in ("mehrotra", "single") and not after_cap:
+            exact = None
+            if sigma_rule == "mehrotra":
+                def exact(rhs):
+                    x, k, _ = solver(apply_K, apply_Pinv, rhs, cg_tol, max_cg, cg_relative)
+                    return x, k
+            res, sigma, n_pred = predictor_corrector(prob, w, Gbeta, Sig1, Sig2, sigma_min, sigma_max, exact,
+                                                     precond_rho)
+        else:
+            res, mu = residuals(prob, Gbeta, w, sigma)
+        rhs = condensed_rhs(res, w)
+        (dbeta, dz), ncg, _ = solver(apply_K, apply_Pinv, rhs, cg_tol, max_cg, cg_relative)
         cg_counts.append(ncg)
+        pred_counts.append(n_pred)
+        sigmas_used.append(sigma)
         ds1, ds2, dnu1, dnu2 = back_substitute(res, w, dbeta, dz)
         amax = max_step(w[2:], (ds1, ds2, dnu1, dnu2))
         alpha = min(1.0, tau * amax)
         for v, d in zip(w, (dbeta, dz, ds1, ds2, dnu1, dnu2)):
             v += alpha * d
-        sigma = next_sigma(alpha, sigma_rule if ncg < max_cg else "fixed", sigma0, sigma_slow, sigma_min)
+        after_cap = ncg >= max_cg
+        rule = "fixed" if (after_cap or sigma_rule not in ("fixed", "adaptive")) else sigma_rule
+        sigma = next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min)
     P, D, gap = prob.certificate(w[0])
     return dict(status=status, point=w, beta=w[0], primal=P, dual=D, gap=gap,
-                ipm_iters=len(cg_counts), cg_counts=cg_counts)
+                ipm_iters=len(cg_counts), cg_counts=cg_counts, predictor_counts=pred_counts, sigmas=sigmas_used)

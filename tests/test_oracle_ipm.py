@@ -211,3 +211,43 @@ def test_conjugate_a_residual_ipm_same_solution():
     b = ipm.solve(prob, gap_tol=1e-12, krylov="car")
     assert b["status"] == "converged"
     assert np.abs(a["beta"] - b["beta"]).max() < 1e-7
+
+
+@pytest.mark.parametrize("dims", [(16,), (4, 4, 4), (9, 5)])
+def test_predictor_corrector_unmasked_equals_soft_threshold(dims):
+    """The single-step predictor-corrector (and the two-solve Mehrotra method) change
+    the path, not the solution."""
+    rng = np.random.default_rng(33)
+    prob = Problem(dims, np.ones(dims, bool), rng.standard_normal(dims), 1.0)
+    prob.lam = 0.3 * prob.lambda_max()
+    for rule in ("single", "mehrotra"):
+        res = ipm.solve(prob, gap_tol=1e-12, sigma_rule=rule, sigma_min=0.01)
+        assert res["status"] == "converged"
+        assert np.abs(res["beta"] - brute.soft_threshold(prob.c, prob.lam)).max() < 1e-8
+
+
+@pytest.mark.parametrize("dims,seed", [((8,), 14), ((10,), 16), ((2, 4), 14), ((2, 2, 2), 15), ((7,), 14),
+                                       ((3, 3), 15)])
+def test_predictor_corrector_masked_tiny_against_enumeration(dims, seed):
+    prob = _masked(dims, seed, missing=0.25, lam_rel=0.3)
+    Mp = _dense(prob.A, prob.n)[prob.mask.reshape(-1)]
+    sols = brute.enumerate_active_sets(Mp, prob.b, prob.lam)
+    res = ipm.solve(prob, gap_tol=1e-12, sigma_rule="single", sigma_min=0.01)
+    assert res["status"] == "converged"
+    assert np.abs(res["beta"] - sols[0]).max() < 1e-7
+
+
+@pytest.mark.parametrize("dims,seed", [((32,), 19), ((8, 8), 20), ((4, 4, 4), 21)])
+def test_predictor_corrector_masked_against_proximal_gradient(dims, seed):
+    prob = _masked(dims, seed, missing=0.2, lam_rel=0.2)
+    Mp = _dense(prob.A, prob.n)[prob.mask.reshape(-1)]
+    ref = brute.proximal_gradient(Mp, prob.b, prob.lam)
+    res = ipm.solve(prob, gap_tol=1e-10, sigma_rule="single", sigma_min=0.01)
+    assert res["status"] == "converged"
+    assert np.abs(res["beta"] - ref).max() < 1e-5
+    assert abs(res["primal"] - prob.objective(ref)) < 2e-9 * max(1, abs(res["primal"]))
+    # one Krylov solve per iteration and no predictor solves; fewer iterations than the
+    # adaptive rule on these problems
+    assert sum(res["predictor_counts"]) == 0
+    ad = ipm.solve(prob, gap_tol=1e-10, sigma_rule="adaptive")
+    assert res["ipm_iters"] <= ad["ipm_iters"]

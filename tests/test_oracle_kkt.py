@@ -281,3 +281,86 @@ def test_krylov_iterates_minimise_their_norms(k):
         assert it == k
         x = np.concatenate([xb, xz])
         assert np.abs(x - x_ref).max() < 1e-8 * np.abs(xs).max(), name
+
+
+def _pc_point(n, rng):
+    beta = rng.standard_normal(n) * 0.3
+    z = np.abs(beta) + rng.uniform(0.2, 1.0, n)
+    s1 = z + beta + rng.uniform(-0.05, 0.05, n)       # infeasible rows 5, 6 as well
+    s2 = z - beta + rng.uniform(-0.05, 0.05, n)
+    nu1, nu2 = rng.uniform(0.05, 0.2, n), rng.uniform(0.05, 0.2, n)
+    return [beta, z, s1, s2, nu1, nu2]
+
+
+def _full_newton_rows(prob, w, d, r_c):
+    """The six linearised rows of Eq. (kktmu) at w for the direction d, with the
+    complementarity residuals r_c = (r_c1, r_c2) given: returns each row's value."""
+    beta, z, s1, s2, nu1, nu2 = w
+    db, dz, ds1, ds2, dn1, dn2 = d
+    r_d = prob.G(beta) - prob.c - nu1 + nu2
+    return [prob.G(db) - dn1 + dn2 + r_d,                  # row 1: G dbeta - dnu1 + dnu2 = -r_d
+            -dn1 - dn2 + (prob.lam - nu1 - nu2),           # row 2
+            dz + db - ds1 + (z + beta - s1),               # row 5
+            dz - db - ds2 + (z - beta - s2),               # row 6
+            s1 * dn1 + nu1 * ds1 + r_c[0],                 # complementarity 1
+            s2 * dn2 + nu2 * ds2 + r_c[1]]                 # complementarity 2
+
+
+@pytest.mark.parametrize("dims", [(8,), (4, 4), (2, 2, 4), (9,)])
+def test_affine_predictor_without_missing_samples_is_the_newton_direction(dims):
+    """No missing samples: G = I, so P = K and the predictor P^{-1} rhs_aff is the exact
+    affine-scaling direction: it satisfies all six linearised rows of Eq. (kktmu) with
+    sigma = 0 (r_c = s o nu)."""
+    prob = _problem(dims, missing=0.0, lam=0.2)
+    prob.mask[:] = True
+    prob.b_hat = np.asarray(prob.b_hat)
+    rng = np.random.default_rng(11)
+    w = _pc_point(prob.n, rng)
+    S1, S2 = ipm.sigmas(w[2], w[4], w[3], w[5])
+    res_aff, mu = ipm.residuals(prob, prob.G(w[0]), w, 0.0)
+    d = ipm.affine_predictor(prob, w, res_aff, S1, S2)[:6]
+    for row in _full_newton_rows(prob, w, d, (w[2] * w[4], w[3] * w[5])):
+        assert np.abs(row).max() < 1e-12
+
+
+@pytest.mark.parametrize("dims", [(8,), (4, 4), (2, 2, 4), (3, 5)])
+def test_predictor_corrector_direction_solves_the_second_order_system(dims):
+    """The single-step predictor-corrector's direction (the PCG solve of the corrector
+    system, solved here to 1e-14) satisfies the linearised rows of Eq. (kktmu) with the
+    complementarity target sigma mu e - ds_aff o dnu_aff:
+        S dnu + V ds = -(s o nu - sigma mu e + ds_aff o dnu_aff),
+    the predictor being P^{-1} rhs_aff (masked problem: an estimate); and sigma is
+    (mu_aff / mu)^3 with alpha_aff the largest step along the predictor keeping s, nu >= 0,
+    found here by bisection on positivity."""
+    prob = _problem(dims, lam=0.2)
+    rng = np.random.default_rng(12)
+    w = _pc_point(prob.n, rng)
+    S1, S2 = ipm.sigmas(w[2], w[4], w[3], w[5])
+    Gb = prob.G(w[0])
+    res, sigma, its = ipm.predictor_corrector(prob, w, Gb, S1, S2, 0.0, 1.0)
+    assert its == 0
+    # the predictor, independently
+    res_aff, mu = ipm.residuals(prob, Gb, w, 0.0)
+    rhs_aff = ipm.condensed_rhs(res_aff, w)
+    Pd = _dense(lambda v: np.concatenate(ipm.P_apply(S1, S2, v[:prob.n], v[prob.n:])), 2 * prob.n)
+    daff = np.linalg.solve(Pd, np.concatenate(rhs_aff))
+    ds1, ds2, dn1, dn2 = ipm.back_substitute(res_aff, w, daff[:prob.n], daff[prob.n:])
+    lo, hi = 0.0, 1.0
+    pos = lambda a: all(np.all(v + a * dv >= 0) for v, dv in zip(w[2:], (ds1, ds2, dn1, dn2)))
+    if not pos(1.0):
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if pos(mid) else (lo, mid)
+    a = 1.0 if pos(1.0) else lo
+    mu_aff = ((w[2] + a * ds1) @ (w[4] + a * dn1) + (w[3] + a * ds2) @ (w[5] + a * dn2)) / (2 * prob.n)
+    assert abs(sigma - min(1.0, (mu_aff / mu) ** 3)) < 1e-9 * max(sigma, 1e-12) + 1e-15
+    # the corrector's residuals and direction
+    r_c1 = w[2] * w[4] - sigma * mu + ds1 * dn1
+    r_c2 = w[3] * w[5] - sigma * mu + ds2 * dn2
+    assert np.abs(res[4] - r_c1).max() < 1e-13 and np.abs(res[5] - r_c2).max() < 1e-13
+    rhs = ipm.condensed_rhs(res, w)
+    (db, dz), it, _ = ipm.pcg(lambda u, v: ipm.K_apply(prob.G, S1, S2, u, v),
+                              lambda u, v: ipm.Pinv_apply(S1, S2, u, v), rhs, 1e-14, 500)
+    d = (db, dz) + ipm.back_substitute(res, w, db, dz)
+    for row in _full_newton_rows(prob, w, d, (r_c1, r_c2)):
+        assert np.abs(row).max() < 1e-9
