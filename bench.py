@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the sparse-DFT recovery IPM on GB300.
 
-One step = one full interior-point solve, to a 1e-6 relative duality gap, of the
-512 x 512 FP64 workload (synthetic: 200 Laplace-amplitude frequencies, noise
-0.02, discs of radius 3 removed on a period-16 lattice, lambda = 0.02
-lambda_max).  Inputs are resident on the device when the timed region starts;
-L2 is flushed (512 MB write) between steps, outside the timed events.
+Default line (the largest single-GPU configuration): one step = the learned warm
+start (network inference and the predicted interior point) plus one mixed-precision
+interior-point solve, to a 1e-6 relative duality gap, of the 512^3 workload
+(synthetic: 100000 frequencies, background 1e-3, noise 0.01, radius-2 balls removed
+on a period-8 lattice, lambda = 0.05 lambda_max).  Inputs are resident on the device
+when the timed region starts; the 25 GB solver state is far larger than L2.  The line
+carries the cold FP64 plain solve of the same instance and the ratio, the per-class
+CUDA-event breakdown of one warm solve with the dominant class's roofline, KKT
+products at 512^3 and 256^3, the 512^2 FP64 solve, an end-to-end time through the C
+ABI with pinned host buffers and the oracle's (extrapolated) time.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
-Prints one JSON line.  Several GPUs run independent replicas (one problem per
-rank, no collective on the data path); value = timed wall / solves of all ranks.
---impl reference times the CPU oracle (numpy FP64, direct DFT) on the same
-workload on the host cores.
+Prints one JSON line.  Several GPUs run independent replicas (one instance per rank,
+no collective on the data path); value = timed wall / solves of all ranks.
+--impl reference times the CPU oracle (numpy FP64, direct DFT) on the host cores.
 """
 
 import argparse
@@ -68,11 +72,16 @@ def _args():
                     help="run the IPM and PCG loops from the host (use_graph = 0: the same kernels, launched one by "
                          "one; ncu cannot profile kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--size", type=int, default=256, help="--workload paper: grid side N (N x N x N)")
+    ap.add_argument("--sigma-rule", type=int, default=None,
+                    help="centring rule of every solve (library option sigma_rule; default: the library's)")
+    ap.add_argument("--sigma-min", type=float, default=None, help="library option sigma_min (default: the library's)")
+    ap.add_argument("--exact-residual", type=int, default=None,
+                    help="library option exact_residual (default: the library's)")
     ap.add_argument("--workload", choices=["1d", "2d", "3d", "batch", "warm512", "infer256", "conv256", "kkt256", "paper"],
-                    default="2d",
-                    help="2d: 512^2 FP64 (default); 1d: n=256 FP64; 3d: 256^3 mixed precision; "
+                    default="warm512",
+                    help="warm512 (default): 512^3, learned warm start + mixed precision against the cold FP64 "
+                         "solve; 2d: 512^2 FP64; 1d: n=256 FP64; 3d: 256^3 mixed precision; "
                          "batch: 48 uneven 3D problems in one graph launch, mixed precision; "
-                         "warm512: 512^3, learned warm start + mixed precision against the cold FP64 solve; "
                          "infer256: the warm-start network alone on the 256^3 slot grid (tensor-core roofline); "
                          "conv256: one of its 32->32 convolution layers; kkt256: KKT products at 256^3 (mixed)")
     return ap.parse_args()
@@ -83,6 +92,15 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+_OPT_OVERRIDES = {}
+
+
+def _options(binding, **kw):
+    """binding.default_options with the command line's solver overrides applied."""
+    kw.update(_OPT_OVERRIDES)
+    return binding.default_options(**kw)
 
 
 def _workload_desc(name):
@@ -156,7 +174,7 @@ def _oracle_solve_seconds(w):
     t0 = time.perf_counter()
     prob = Problem(w.dims, w.mask.astype(bool), w.y, 1.0)
     prob.lam = w.lam_rel * prob.lambda_max()
-    res = oipm.solve(prob, gap_tol=GAP_TOL, sigma_rule="adaptive", sigma_min=0.03)   # the library's default rule
+    res = oipm.solve(prob, gap_tol=GAP_TOL, sigma_rule="single", sigma_min=0.01)   # the library's default rule
     return time.perf_counter() - t0, res
 
 
@@ -172,7 +190,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2502_04217_gb300.synth import make_problem
-    if args.workload in ("3d", "batch", "warm512", "infer256", "conv256", "kkt256") or (
+    if args.workload == "warm512":
+        return _run_reference_512(args)
+    if args.workload in ("3d", "batch", "infer256", "conv256", "kkt256") or (
             args.workload == "paper" and args.size > 32):
         print(json.dumps({"impl": "reference", "unavailable": "the oracle on this workload takes hours on the host "
                           "cores; its CPU baseline is reported (extrapolated from a bounded sample) in the GPU line"}))
@@ -192,8 +212,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": _workload_desc(args.workload), "parallelism": "host cores of rank 0"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": _cores(), "kind": "oracle",
-                         "sample": "full oracle solve (numpy FP64, direct DFT by Vandermonde matrices) of the "
-                                   "512x512 workload to gap 1e-6, per step"},
+                         "sample": f"full oracle solve (numpy FP64, direct DFT by Vandermonde matrices) of the "
+                                   f"{args.workload} workload to gap 1e-6, per step"},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "solve": {"ipm_iters": res["ipm_iters"], "cg_iters_total": int(sum(res["cg_counts"])),
                   "rel_gap": res["gap"], "primal": res["primal"]},
@@ -202,15 +222,75 @@ def run_reference(args):
     return 0
 
 
-def _pass_model(dims, prec, ipm_iters, cg_iters):
-    """Algorithmic work of the FFT pass classes over one solve.
+def _run_reference_512(args):
+    """The oracle on the 512^3 workload: a direct-DFT IPM there takes days, so each step is a
+    bounded sample -- one oracle product with M_perp^T M_perp at 256^3, timed -- scaled to
+    512^3 (x16) and by the products the plain FP64 method takes on this instance.  The value
+    is that extrapolated solve time, labelled as such."""
+    for _ in range(min(args.warmup, 1)):
+        _oracle_product_512_seconds()
+    ts, t256 = [], []
+    for _ in range(args.steps):
+        t512, t = _oracle_product_512_seconds()
+        ts.append(t512 * COLD_FP64_PRODUCTS_512)
+        t256.append(t)
+    v = sum(ts) / len(ts)
+    sample = (f"per step one oracle product with M_perp^T M_perp at 256^3 (numpy FP64 direct DFT, mean "
+              f"{sum(t256) / len(t256):.2f} s), scaled by n (N0 + N1 + N2) to 512^3 (x16) and by the "
+              f"{COLD_FP64_PRODUCTS_512} products of the plain FP64 IPM on this instance: an extrapolated solve time")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * v, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "extrapolated": True,
+        "config": {"workload": _workload_desc("warm512"), "dims": [512, 512, 512],
+                   "parallelism": "host cores of rank 0"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": _cores(), "kind": "oracle", "extrapolated": True,
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
 
-    Products with G: ipm_iters + 1 residual products (FP64, beta in / beta out)
-    and cg_iters PCG products (pass type FP64, or FP32 in mixed mode; the first
-    pass also forms p = z + beta p on both blocks, the last adds the diagonal of
-    K, writes q and reduces p^T q).  Per launch, FLOPs are 5 L log2 L per complex
-    transform of length L and 2.5 L log2 L per real one; bytes are the
-    compulsory reads and writes of the launch (each operand touched once).
+
+CLASSES = {"fft_row": 0, "fft_col": 1, "fft_middle": 2, "pcg_update": 3, "ipm_other": 4, "prepare": 6, "step": 7,
+           "certificate": 8}
+
+
+def _breakdown(binding, h):
+    """Per-class launches and summed CUDA-event milliseconds since the last profile reset."""
+    out = {}
+    for nm, k in CLASSES.items():
+        n, ms = binding.ipm_profile_get(h, k)
+        out[nm] = {"launches": int(n), "ms": ms}
+    return out
+
+
+def _class_model(dims, prec, res, opt):
+    """Algorithmic work of each kernel class over one solve, from the solve's own counts.
+
+    Products with G: the PCG products (cg_iters_total; FP32 passes in mixed mode) and
+    the FP64 products that computed G beta exactly (kkt_products - cg_iters_total -
+    refinements).  Bytes per half-spectrum slot (H slots; a beta-layout vector is 16 B
+    per slot, a two-block PCG vector 32 B):
+      PCG product: first row pass reads z, p and writes p (96 B) and the work buffer;
+        last row pass reads the buffer, p, Lambda1, Lambda2 and writes q (96 B);
+      FP64 product: reads beta (16 B), writes G beta (16 B);
+      every pass between reads and writes the work buffer (8 B per slot in FP32, 16 B in
+        FP64); the middle pass also reads the mask bits (n / 8 B);
+      pcg_update: reads x, r, p, q and P^{-1}'s three coefficients, writes x, r, z (272 B);
+      prepare: reads beta, z, s1, s2, nu1, nu2, G beta, c (128 B), writes 1/s1, 1/s2,
+        Lambda1, Lambda2, P^{-1}'s coefficients (112 B) and x, r, rhs, z, p (160 B);
+        with the predictor-corrector (sigma_rule 2) the class holds two kernels: the
+        predictor reads the iterate (128 B) and writes 1/s, Lambda, P^{-1} and the two
+        second-order terms (144 B), prepare reads the iterate, 1/s, P^{-1} and the terms
+        (240 B) and writes x, r, rhs, z, p (160 B);
+      step: step_length reads x, beta, z, s, nu, 1/s (160 B), step_update reads the same
+        and writes beta, z, s, nu (96 B); with the predictor-corrector each also reads
+        the two terms (32 B);
+      certificate: reads beta, G beta, c (48 B);
+      G beta carried (exact_residual 0, CG, no refinement): the last pass of a PCG
+        product also writes (G p)_beta (16 B), pcg_update updates G x (48 B), prepare
+        clears G x (16 B), step_update updates G beta (32 B).
+    FLOPs: 5 L log2 L per complex transform of length L, 2.5 L log2 L per real one.
     Returns {class: (working launches, flops, bytes)} for one solve.
     """
     import math
@@ -221,28 +301,115 @@ def _pass_model(dims, prec, ipm_iters, cg_iters):
         M *= x
     H = (Nl // 2 + 1) * M
     n = Nl * M
-    esz = 8 if prec == "mixed" else 16       # bytes of one complex value of the PCG passes
-    n_res, n_pcg = ipm_iters + 1, cg_iters
+    mixed = prec == "mixed"
+    pc = opt.sigma_rule == 2                       # predictor-corrector kernels in the prepare class
+    incr = not opt.exact_residual and opt.krylov == 0 and opt.refine_every == 0   # G beta carried
+    esz = 8 if mixed else 16                 # bytes of one complex value of the PCG passes
+    n_pcg = res["cg_iters_total"]
+    n_res = res["kkt_products"] - res["cg_iters_total"] - res.get("refinements", 0)
+    it = res["ipm_iters"]
     out = {}
-    mid_flops = M * 2 * 2.5 * Nl * math.log2(Nl)
+    mid_flops = M * 2 * 2.5 * Nl * math.log2(max(Nl, 2))
+    gp = 16 * H if incr else 0
     if d == 1:
         res_b = 16 * H + 16 * H + n / 8
-        pcg_b = 96 * H + 96 * H + n / 8
+        pcg_b = 96 * H + 96 * H + gp + n / 8
         out["fft_middle"] = (n_res + n_pcg, (n_res + n_pcg) * mid_flops, n_res * res_b + n_pcg * pcg_b)
-        return out
-    L = dims[1] if d == 3 else dims[0]
-    row_flops = (H // L) * 5 * L * math.log2(L)
-    # row class: one inverse (first) and one forward (last) launch per product
-    res_row = (16 * H + 16 * H) + (16 * H + 16 * H)
-    pcg_row = (96 * H + esz * H) + (esz * H + 96 * H)
-    out["fft_row"] = (2 * (n_res + n_pcg), 2 * (n_res + n_pcg) * row_flops, n_res * res_row + n_pcg * pcg_row)
-    out["fft_middle"] = (n_res + n_pcg, (n_res + n_pcg) * mid_flops,
-                         n_res * (32 * H + n / 8) + n_pcg * (2 * esz * H + n / 8))
-    if d == 3:
-        col_flops = (H // dims[0]) * 5 * dims[0] * math.log2(dims[0])
-        out["fft_col"] = (2 * (n_res + n_pcg), 2 * (n_res + n_pcg) * col_flops,
-                          n_res * 2 * 32 * H + n_pcg * 2 * 2 * esz * H)
+    else:
+        L = dims[1] if d == 3 else dims[0]
+        row_flops = (H // L) * 5 * L * math.log2(L)
+        res_row = (16 * H + 16 * H) + (16 * H + 16 * H)
+        pcg_row = (96 * H + esz * H) + (esz * H + 96 * H + gp)
+        out["fft_row"] = (2 * (n_res + n_pcg), 2 * (n_res + n_pcg) * row_flops, n_res * res_row + n_pcg * pcg_row)
+        out["fft_middle"] = (n_res + n_pcg, (n_res + n_pcg) * mid_flops,
+                             n_res * (32 * H + n / 8) + n_pcg * (2 * esz * H + n / 8))
+        if d == 3:
+            col_flops = (H // dims[0]) * 5 * dims[0] * math.log2(dims[0])
+            out["fft_col"] = (2 * (n_res + n_pcg), 2 * (n_res + n_pcg) * col_flops,
+                              n_res * 2 * 32 * H + n_pcg * 2 * 2 * esz * H)
+    out["pcg_update"] = (n_pcg, 0.0, n_pcg * (272 * H + (48 * H if incr else 0)))
+    gx = 16 * H if incr else 0
+    if pc:
+        out["prepare"] = (2 * it, 0.0, it * ((128 + 144) * H + (240 + 160) * H + gx))
+    else:
+        out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 160 * H + gx))
+    out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (32 * H if incr else 0) + (64 * H if pc else 0)))
     return out
+
+
+def _rooflines(dims, prec, res, breakdown, steps, opt):
+    """Per-class achieved rates over the breakdown's event times (HBM GB/s over algorithmic
+    bytes for every class; FP64 TFLOP/s for the FFT classes of FP64 solves) and the
+    dominant class (the most event time among the modelled classes)."""
+    model = _class_model(dims, prec, res, opt)
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    cert = breakdown.get("certificate", {"launches": 0})
+    Hn = _sizes(dims)[0]
+    model["certificate"] = (cert["launches"] // max(steps, 1), 0.0, (cert["launches"] // max(steps, 1)) * 48 * Hn)
+    classes = {}
+    for nm, (work, flops, nbytes) in model.items():
+        b = breakdown.get(nm)
+        if not b or not b["launches"] or b["ms"] <= 0:
+            continue
+        t = b["ms"] / 1e3
+        c = {"launches": b["launches"], "working_launches": work * steps, "ms": round(b["ms"], 4),
+             "algorithmic_bytes": nbytes * steps, "gbs": nbytes * steps / t / 1e9,
+             "frac_of_hbm": nbytes * steps / t / 1e9 / peak}
+        if flops:
+            c["algorithmic_flops"] = flops * steps
+            c["tflops"] = flops * steps / t / 1e12
+        classes[nm] = c
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    return classes, dom
+
+
+def _roofline_line(dims, prec, res, breakdown, steps, workload, opt):
+    """The JSON roofline object of the dominant class (see _rooflines), with every class's
+    figures beside it; FP64 FFT classes are reported against the FP64 ALU peak."""
+    classes, dom = _rooflines(dims, prec, res, breakdown, steps, opt)
+    c = classes[dom]
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    if prec == "fp64" and dom.startswith("fft"):
+        r = {"bound": "alu", "achieved": c["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+             "frac": c["tflops"] / FP64_PEAK_TFLOPS,
+             "peak_source": "nominal GB300 FP64 rate (profiling recipe; no FP64 entry in MEASURED_PEAKS.json)"}
+    else:
+        r = {"bound": "hbm", "achieved": c["gbs"], "peak": peak, "unit": "GB/s", "frac": c["frac_of_hbm"],
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    r.update({"kernel": dom, "traffic": _traffic(dom, workload), "per_launch_us": 1e3 * c["ms"] / c["launches"],
+              "launches": c["launches"], "working_launches": c["working_launches"],
+              "algorithmic_bytes": c["algorithmic_bytes"], "algorithmic_flops": c.get("algorithmic_flops"),
+              "event_ms": c["ms"], "ncu_share": _ncu_share(dom, workload),
+              "how": "achieved = algorithmic bytes (or FLOPs) of the class's working launches over the summed "
+                     "CUDA-event time of all its launches (launches that find nothing to do included)",
+              "classes": classes,
+              "breakdown": {k: {"launches": v["launches"], "ms": round(v["ms"], 4)} for k, v in breakdown.items()}})
+    return r
+
+
+def _ncu_share(kernel_class, workload):
+    """Share of the class in the committed ncu launch list of this workload
+    (profiles/shares_<workload>.txt, lines "class<TAB>share"), or None."""
+    try:
+        rows = {}
+        with open(os.path.join(ROOT, "profiles", f"shares_{workload}.txt")) as f:
+            for ln in f:
+                if "\t" in ln and not ln.startswith("#"):
+                    k, v = ln.rstrip("\n").split("\t", 1)
+                    rows[k] = v
+        if rows.get("csrc_sha256") != _csrc_sha256():
+            return None
+        return float(rows[kernel_class]) if kernel_class in rows else None
+    except Exception:
+        return None
+
+
+def _sizes(dims):
+    Nl = dims[-1]
+    M = 1
+    for x in dims[:-1]:
+        M *= x
+    return (Nl // 2 + 1) * M, Nl * M
 
 
 def run_ours(args):
@@ -262,7 +429,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     w = make_problem("paper", dims=(args.size,)) if args.workload == "paper" else make_problem(args.workload, index=rank)
     prec = WORKLOADS[args.workload][1]
-    opt = binding.default_options(precision=binding.IPM_MIXED if prec == "mixed" else binding.IPM_FP64,
+    opt = _options(binding, precision=binding.IPM_MIXED if prec == "mixed" else binding.IPM_FP64,
                                   gap_tol=GAP_TOL, lambda_relative=1, use_graph=0 if args.host_loop else 1)
     mask_d = torch.from_numpy(np.ascontiguousarray(w.mask)).cuda()
     y_d = torch.from_numpy(np.ascontiguousarray(w.y)).cuda()
@@ -311,34 +478,9 @@ def run_ours(args):
     binding.ipm_profile_enable(h, True)
     for _ in range(args.steps):
         one_step(True)
-    cls_names = ["fft_row", "fft_col", "fft_middle", "pcg_update", "ipm_other"]
-    breakdown = {}
-    for k, nm in enumerate(cls_names):
-        n, ms = binding.ipm_profile_get(h, k)
-        breakdown[nm] = {"launches": n, "ms": ms}
+    breakdown = _breakdown(binding, h)
     binding.ipm_profile_enable(h, False)
-    fft = {k: v for k, v in breakdown.items() if k.startswith("fft") and v["launches"]}
-    dom = max(fft, key=lambda k: fft[k]["ms"])
-    model = _pass_model(w.dims, prec, res["ipm_iters"], res["cg_iters_total"])
-    work_launches, flops, nbytes = (x * args.steps for x in model[dom])
-    dom_s = breakdown[dom]["ms"] / 1e3
-    per_launch_us = 1e6 * dom_s / breakdown[dom]["launches"]
-    if prec == "fp64":
-        achieved = flops / dom_s / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "nominal GB300 FP64 rate (profiling recipe); no FP64 entry in MEASURED_PEAKS.json"}
-    else:
-        peak = _peaks().get("hbm_gbs", 6800.0)
-        achieved = nbytes / dom_s / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roofline.update({"kernel": dom, "traffic": _traffic(dom, args.workload), "per_launch_us": per_launch_us,
-                     "launches": breakdown[dom]["launches"], "working_launches": work_launches,
-                     "algorithmic_flops": flops, "algorithmic_bytes": nbytes,
-                     "hbm_gbs_algorithmic": nbytes / dom_s / 1e9,
-                     "breakdown_ms": {k: round(v["ms"], 3) for k, v in breakdown.items()},
-                     "breakdown_launches": {k: v["launches"] for k, v in breakdown.items()}})
+    roofline = _roofline_line(w.dims, prec, res, breakdown, args.steps, args.workload, opt)
 
     # ---- end to end through the C ABI with pinned host buffers -------------------------
     mask_h = torch.from_numpy(np.ascontiguousarray(w.mask)).pin_memory()
@@ -461,17 +603,24 @@ def _traffic(kernel, workload):
         return None
 
 
-def _kkt_throughput(binding, torch, np, reps=20, w=None):
-    """Back-to-back products with K on the 256^3 workload in mixed precision (inside the NVTX range "kkt")."""
+def _kkt_throughput(binding, torch, np, reps=20, w=None, h=None, label="3d 256^3 mixed (FP32 FFT, FP64 diagonal)"):
+    """Back-to-back products with K through kkt_apply (inside the NVTX range "kkt"): on the
+    handle h with its current Sigma, else on a new mixed-precision handle of the 256^3
+    workload with Sigma1 = 1/2, Sigma2 = 2."""
     from paper_2502_04217_gb300.synth import make_problem
-    w = w if w is not None else make_problem("3d")
-    opt = binding.default_options(precision=binding.IPM_MIXED, lambda_relative=1)
     stream = torch.cuda.current_stream()
-    h = binding.ipm_create(w.dims, w.mask, w.y, w.lam_rel, opt, stream=stream.cuda_stream)
+    own = h is None
+    if own:
+        w = w if w is not None else make_problem("3d")
+        opt = _options(binding, precision=binding.IPM_MIXED, lambda_relative=1)
+        h = binding.ipm_create(w.dims, w.mask, w.y, w.lam_rel, opt, stream=stream.cuda_stream)
+    p = q = None
     try:
         H, n = binding.ipm_sizes(h)
-        ones = torch.ones(2 * H, dtype=torch.float64, device="cuda")
-        binding.ipm_set_sigma(h, ones, ones * 0.5, ones * 2.0, ones)
+        if own:
+            ones = torch.ones(2 * H, dtype=torch.float64, device="cuda")
+            binding.ipm_set_sigma(h, ones, ones * 0.5, ones * 2.0, ones)
+            del ones
         p = torch.randn(4 * H, dtype=torch.float64, device="cuda")
         binding.ipm_pack_beta(h, p[: 2 * H].clone(), p[: 2 * H])
         binding.ipm_pack_beta(h, p[2 * H:].clone(), p[2 * H:])
@@ -492,11 +641,14 @@ def _kkt_throughput(binding, torch, np, reps=20, w=None):
         # compulsory bytes of one product: p, q (FP64, 2 blocks), Lambda1, Lambda2 (FP64), mask bits
         algo = (4 * H * 8) * 2 + (2 * H * 8) * 2 + n / 8
         peak = _peaks().get("hbm_gbs", 6800.0)
-        return {"workload": "3d 256^3 mixed (FP32 FFT, FP64 diagonal)", "matvecs_per_s": 1.0 / t,
+        return {"workload": label, "matvecs_per_s": 1.0 / t,
                 "ms_per_matvec": t * 1e3, "algorithmic_bytes": algo, "algorithmic_gbs": algo / t / 1e9,
-                "hbm_peak_gbs": peak, "frac_of_hbm": algo / t / 1e9 / peak, "tiles": binding.ipm_describe(h)}
+                "hbm_peak_gbs": peak, "frac_of_hbm": algo / t / 1e9 / peak, "reps": reps,
+                "tiles": binding.ipm_describe(h)}
     finally:
-        binding.ipm_destroy(h)
+        del p, q
+        if own:
+            binding.ipm_destroy(h)
 
 
 def run_batch(args):
@@ -519,7 +671,7 @@ def run_batch(args):
     from paper_2502_04217_gb300 import shard
     ws = [allw[i] for i in shard.rank_share([w.dims for w in allw], ws_n, rank)]
     stream = torch.cuda.current_stream()
-    opt = binding.default_options(precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
+    opt = _options(binding, precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
     b = binding.ipm_create_batch([(w.dims, w.mask, w.y, w.lam_rel) for w in ws], opt, stream=stream.cuda_stream)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
@@ -557,14 +709,27 @@ def run_batch(args):
     # aggregate algorithmic bytes of all FFT passes of all members, per batch
     nbytes = 0.0
     for w, r in zip(ws, res):
-        for cls, (_, _, by) in _pass_model(w.dims, "mixed", r["ipm_iters"], r["cg_iters_total"]).items():
-            nbytes += by
+        for cls, (_, _, by) in _class_model(w.dims, "mixed", r, opt).items():
+            if cls.startswith("fft"):
+                nbytes += by
     peak = _peaks().get("hbm_gbs", 6800.0)
     ach = nbytes / value / 1e9
     roofline = {"bound": "hbm", "kernel": "all FFT passes of the batch (aggregate)", "achieved": ach, "peak": peak,
                 "unit": "GB/s", "frac": ach / peak, "traffic": None,
                 "note": "graph branches run concurrently, so per-kernel event times do not exist; algorithmic bytes "
                         "of every FFT pass of every member over the batch wall time"}
+    # what the concurrent branches buy: the same members solved one after another
+    serial = 0.0
+    for h in members:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        binding.ipm_solve(h)
+        e1.record(stream)
+        e1.synchronize()
+        serial += e0.elapsed_time(e1) / 1e3
+    all_bytes = 0.0
+    for w, r in zip(ws, res):
+        all_bytes += sum(by for _, _, by in _class_model(w.dims, "mixed", r, opt).values())
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         t_cpu, solved, extrap = 0.0, 0, 0
@@ -613,6 +778,8 @@ def run_batch(args):
                        "l2": "flushed between steps (512 MB write outside the timed events)",
                        "parallelism": "problems split across ranks" if ws_n > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "serial_members_s": serial, "concurrency_speedup": serial / value,
+            "all_classes_hbm_frac": all_bytes / value / 1e9 / peak,
             "solve": {"problems_per_s": len(allw) / value, "ipm_iters": [r["ipm_iters"] for r in res],
                       "cg_iters_total": int(sum(r["cg_iters_total"] for r in res)),
                       "max_rel_gap": max(r["rel_gap"] for r in res),
@@ -623,8 +790,56 @@ def run_batch(args):
     return 0
 
 
+def _fp64_2d_extra(binding, torch, reps=10):
+    """The 512^2 FP64 plain solve (the 2d workload), a short extra measurement beside the
+    default line: solve time (CUDA events, L2 flushed between solves) and counts."""
+    import numpy as np
+    from paper_2502_04217_gb300.synth import make_problem
+    w = make_problem("2d")
+    stream = torch.cuda.current_stream()
+    opt = _options(binding, precision=binding.IPM_FP64, gap_tol=GAP_TOL, lambda_relative=1)
+    h = binding.ipm_create(w.dims, np.ascontiguousarray(w.mask), np.ascontiguousarray(w.y), w.lam_rel, opt,
+                           stream=stream.cuda_stream)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    try:
+        ts, res = [], None
+        for i in range(reps + 3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = binding.ipm_solve(h)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1))
+        return {"workload": _workload_desc("2d"), "ms_per_solve": sum(ts) / len(ts), "ipm_iters": res["ipm_iters"],
+                "cg_iters_total": res["cg_iters_total"], "kkt_products": res["kkt_products"],
+                "rel_gap": res["rel_gap"], "solves": reps}
+    finally:
+        binding.ipm_destroy(h)
+        del flush
+
+
+# Products with M_perp^T M_perp the oracle's IPM performs on the 512^3 instance: the
+# plain FP64 method with the library's default rules takes 8 IPM iterations and 43 PCG
+# iterations there (measured on a GB300 with this library), and the oracle forms G beta
+# once per IPM iteration plus once at the end: 43 + 9 = 52.  The reference arm multiplies
+# the oracle's measured time per product by it.
+COLD_FP64_PRODUCTS_512 = 52
+
+
+def _oracle_product_512_seconds():
+    """The oracle's time for one product with M_perp^T M_perp at 512^3, extrapolated from
+    one timed product at 256^3 (direct DFT along each axis: cost n (N0 + N1 + N2), 16x
+    from 256^3 to 512^3).  Returns (seconds at 512^3, seconds measured at 256^3)."""
+    from paper_2502_04217_gb300.synth import make_problem
+    t = _oracle_g_seconds(make_problem("3d"))
+    return 16.0 * t, t
+
+
 def run_warm512(args):
-    """Warm-started mixed solve (network inference included) vs cold FP64 solve, 512^3."""
+    """Default line: the 512^3 learned-warm-start mixed-precision solve to a 1e-6 gap
+    (network inference included), against the cold FP64 plain solve of the same instance."""
     import numpy as np
     import torch
 
@@ -634,12 +849,17 @@ def run_warm512(args):
 
     ws_n, rank, local = _dist()
     torch.cuda.set_device(local)
+    dist = None
+    if ws_n > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     binding.load()
     stream = torch.cuda.current_stream()
     w = make_problem("3d512", index=rank)
     net = wsm.load(stream=stream.cuda_stream)
-    o64 = binding.default_options(precision=binding.IPM_FP64, gap_tol=GAP_TOL, lambda_relative=1)
-    o32 = binding.default_options(precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
+    graph = 0 if args.host_loop else 1
+    o64 = _options(binding, precision=binding.IPM_FP64, gap_tol=GAP_TOL, lambda_relative=1, use_graph=graph)
+    o32 = _options(binding, precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1, use_graph=graph)
     mask_d = torch.from_numpy(np.ascontiguousarray(w.mask)).cuda()
     y_d = torch.from_numpy(np.ascontiguousarray(w.y)).cuda()
     h64 = binding.ipm_create(w.dims, mask_d, y_d, w.lam_rel, o64, stream=stream.cuda_stream)
@@ -660,52 +880,58 @@ def run_warm512(args):
 
     for _ in range(args.warmup):
         warm()
-    binding.ipm_solve(h64)
+    # ---- timed region: K warm-start solves ------------------------------------------
     binding.ipm_profile_enable(h32, False)        # resets the device launch counter
     clocks = ClockSampler(local)
     clocks.start()
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     wt, rw = [], None
+    torch.cuda.nvtx.range_push("solve")          # lets ncu select exactly the timed solves
     for _ in range(args.steps):
         t, rw = timed(warm)
         wt.append(t)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
     launches, _ = binding.ipm_profile_get(h32, 5)
     launches += 6 * args.steps                     # features, 4 convolutions, start point per step
-    t_inf = timed(lambda: binding.ws_forward(net, h32, None))[0]
-    t64, r64 = timed(lambda: binding.ipm_solve(h64))
-    tcold32, rc32 = timed(lambda: binding.ipm_solve(h32))
-    clk = clocks.stop()
-    value = sum(wt) / len(wt)
+    total = sum(wt)
+    if dist:
+        tt = torch.tensor([total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = tt.item()
+    value = total / (args.steps * ws_n)
 
-    # kernel classes of one warm solve (per-launch events), dominant FFT pass class -> HBM roofline
+    # ---- the plain method on the same instance: cold FP64 (and cold mixed) -------------
+    binding.ipm_solve(h64)
+    c64 = [timed(lambda: binding.ipm_solve(h64)) for _ in range(2)]
+    t64, r64 = sum(t for t, _ in c64) / len(c64), c64[-1][1]
+    tcold32, rc32 = timed(lambda: binding.ipm_solve(h32))
+    t_inf = timed(lambda: binding.ws_forward(net, h32, None))[0]
+
+    # ---- per-launch CUDA events of one warm solve: classes and the dominant one --------
     binding.ipm_profile_enable(h32, True)
     binding.ws_predict(net, h32, wsm.MU_SCALE)
     rp = binding.ipm_solve(h32)
-    cls_names = ["fft_row", "fft_col", "fft_middle", "pcg_update", "ipm_other"]
-    breakdown = {}
-    for k, nm in enumerate(cls_names):
-        nl, ms = binding.ipm_profile_get(h32, k)
-        breakdown[nm] = {"launches": nl, "ms": ms}
+    breakdown = _breakdown(binding, h32)
     binding.ipm_profile_enable(h32, False)
-    fft = {k: v for k, v in breakdown.items() if k.startswith("fft") and v["launches"]}
-    dom = max(fft, key=lambda k: fft[k]["ms"])
-    _, flops, nbytes = _pass_model(w.dims, "mixed", rp["ipm_iters"], rp["cg_iters_total"])[dom]
-    dom_s = breakdown[dom]["ms"] / 1e3
-    peak = _peaks().get("hbm_gbs", 6800.0)
-    roofline = {"bound": "hbm", "achieved": nbytes / dom_s / 1e9, "peak": peak, "unit": "GB/s",
-                "frac": nbytes / dom_s / 1e9 / peak, "traffic": _traffic(dom, "warm512"), "kernel": dom,
-                "per_launch_us": 1e6 * dom_s / breakdown[dom]["launches"], "algorithmic_bytes": nbytes,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "breakdown_ms": {k: round(v["ms"], 3) for k, v in breakdown.items()},
-                "breakdown_launches": {k: v["launches"] for k, v in breakdown.items()}}
+    roofline = _roofline_line(w.dims, "mixed", rp, breakdown, 1, "warm512", o32)
 
-    # end to end: problem from pinned host buffers, spectrum back to the host
+    # ---- KKT products at 512^3 (this instance, Sigma of the last iterate) and 256^3 ------
+    kkt512 = _kkt_throughput(binding, torch, np, reps=10, h=h32, label="3d 512^3 mixed (FP32 FFT, FP64 diagonal)")
+
+    # ---- end to end: problem from pinned host buffers, spectrum back to the host -------
     mask_h = mask_d.cpu().pin_memory()
     y_h = y_d.cpu().pin_memory()
     H, n = binding.ipm_sizes(h32)
     spec_h = torch.empty(2 * H, dtype=torch.float64).pin_memory()
+    e2e_steps = min(args.steps, 5)
     e2e_t = []
-    for i in range(args.steps + 1):
+    for i in range(e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         binding.ipm_set_problem(h32, mask_h, y_h, w.lam_rel)
@@ -715,36 +941,49 @@ def run_warm512(args):
         if i > 0:
             e2e_t.append(t1 - t0)
     e2e = {"value": sum(e2e_t) / len(e2e_t), "unit": "s", "h2d_bytes_per_step": int(mask_h.numel() + y_h.numel() * 8),
-           "d2h_bytes_per_step": int(spec_h.numel() * 8)}
-
-    cpu = None
-    if not args.no_cpu_baseline and rank == 0:
-        ws_ = make_problem("custom", dims=(128, 128, 128), missing=0.06, seed=3)
-        t_g = _oracle_g_seconds(ws_)
-        scale = (512 / 128) ** 4            # direct DFT along each axis: n * (N0 + N1 + N2)
-        cpu = {"value": t_g * scale * rw["kkt_products"], "unit": "s", "cores": _cores(), "kind": "oracle",
-               "extrapolated": True,
-               "sample": f"one oracle product with M_perp^T M_perp at 128^3 ({t_g:.2f} s, direct DFT), scaled by "
-                         f"n (N0 + N1 + N2) to 512^3 and by the {rw['kkt_products']} products of the warm solve"}
+           "d2h_bytes_per_step": int(spec_h.numel() * 8), "steps": e2e_steps,
+           "path": "ipm_set_problem (pinned host mask and signal) + ws_predict + ipm_solve + ipm_get_spectrum "
+                   "(pinned host), wall clock"}
     binding.ipm_destroy(h64)
     binding.ipm_destroy(h32)
     binding.ws_destroy(net)
+    del mask_d, y_d
+    torch.cuda.empty_cache()
+    kkt256 = _kkt_throughput(binding, torch, np, reps=20)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        t512, t256 = _oracle_product_512_seconds()
+        cpu = {"value": t512 * rw["kkt_products"], "unit": "s", "cores": _cores(), "kind": "oracle",
+               "extrapolated": True,
+               "sample": f"one oracle product with M_perp^T M_perp at 256^3 ({t256:.2f} s, numpy FP64 direct DFT), "
+                         f"scaled by n (N0 + N1 + N2) to 512^3 (x16) and by the {rw['kkt_products']} products of "
+                         "the warm solve"}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws_n, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * value, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32+f64", "data": "synthetic",
             "config": {"workload": _workload_desc("warm512"), "dims": list(w.dims), "gap_tol": GAP_TOL,
                        "network": "4-layer 3x3x3 conv, 32 channels, BF16, trained on 128^3 instances (weights file)",
-                       "mu_scale": wsm.MU_SCALE, "l2": "inputs far larger than L2 (512^3)"},
-            "warm_vs_cold_fp64": value / t64, "cold_fp64_s": t64, "cold_mixed_s": tcold32, "inference_s": t_inf,
-            "solve": {"warm_ipm_iters": rw["ipm_iters"], "cold_fp64_ipm_iters": r64["ipm_iters"],
-                      "cold_mixed_ipm_iters": rc32["ipm_iters"], "warm_rel_gap": rw["rel_gap"],
-                      "cold_fp64_rel_gap": r64["rel_gap"],
+                       "mu_scale": wsm.MU_SCALE, "l2": "inputs far larger than L2 (512^3 state: 25 GB)",
+                       "parallelism": "replicas (one instance per rank)" if ws_n > 1 else "single GPU",
+                       "launch": "network kernels + " + ("host-driven loops" if args.host_loop else
+                                                          "one CUDA graph per solve")},
+            "vs_fp64_plain": value / t64, "cold_fp64_s": t64, "cold_mixed_s": tcold32, "inference_s": t_inf,
+            "solve": {"warm_ipm_iters": rw["ipm_iters"], "warm_cg_iters": rw["cg_iters_total"],
+                      "warm_kkt_products": rw["kkt_products"], "cold_fp64_ipm_iters": r64["ipm_iters"],
+                      "cold_fp64_cg_iters": r64["cg_iters_total"], "cold_fp64_kkt_products": r64["kkt_products"],
+                      "cold_mixed_ipm_iters": rc32["ipm_iters"], "cold_mixed_cg_iters": rc32["cg_iters_total"],
+                      "warm_rel_gap": rw["rel_gap"], "cold_fp64_rel_gap": r64["rel_gap"],
                       "objective_rel_diff": abs(rw["primal"] - r64["primal"]) / abs(r64["primal"]),
                       "step_s": [round(x, 4) for x in wt]},
             "clocks": clk, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "kkt_matvec": {"512^3": kkt512, "256^3": kkt256},
+            "fp64_2d": _fp64_2d_extra(binding, torch),
         }))
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -899,7 +1138,7 @@ def run_infer256(args):
     binding.load()
     stream = torch.cuda.current_stream()
     w = make_problem("3d", index=rank)
-    opt = binding.default_options(precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
+    opt = _options(binding, precision=binding.IPM_MIXED, gap_tol=GAP_TOL, lambda_relative=1)
     h = binding.ipm_create(w.dims, w.mask, w.y, w.lam_rel, opt, stream=stream.cuda_stream)
     net = wsm.load(stream=stream.cuda_stream)
     H, n = binding.ipm_sizes(h)
@@ -978,6 +1217,12 @@ def run_infer256(args):
 
 def main():
     args = _args()
+    if args.sigma_rule is not None:
+        _OPT_OVERRIDES["sigma_rule"] = args.sigma_rule
+    if args.sigma_min is not None:
+        _OPT_OVERRIDES["sigma_min"] = args.sigma_min
+    if args.exact_residual is not None:
+        _OPT_OVERRIDES["exact_residual"] = args.exact_residual
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

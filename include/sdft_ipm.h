@@ -113,22 +113,29 @@ typedef struct {
                            registers straight from / to global memory) wherever the length
                            allows it (32, 64, 128, 256 or 512; the middle pass uses Nl/2),
                            else the shared-memory one.  tile_e is ignored by engine 2.       */
-  int sigma_rule;       /* centring parameter for the next direction.  1 (default): adaptive,
-                           sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow) from the last
-                           step alpha (Mehrotra's (mu_aff / mu)^3 heuristic with the previous
-                           step standing in for an affine predictor: one Newton system per
-                           iteration; the first direction uses sigma; after a PCG solve
-                           stopped at max_cg the fixed rule applies); 0: sigma, or
-                           sigma_slow after a step alpha < 0.1                               */
-  double sigma_min;     /* lower clamp of the adaptive rule (default 0.03; at 0.01 the PCG
-                           of tiny problems broke down below a 1e-12 gap)                    */
-  int exact_residual;   /* IPM_FP64 only.  0 (default): G beta is carried along with beta
-                           (the last pass of each PCG product also stores (G p)_beta, PCG
-                           accumulates G x = sum alpha G p beside x, the step adds alpha G x),
-                           and an FP64 product recomputes it only to confirm a stop test that
-                           passed on the carried value; 1: an FP64 product recomputes G beta
-                           every IPM iteration (IPM_MIXED always does, its PCG products being
-                           FP32)                                                            */
+  int sigma_rule;       /* centring parameter of each direction.  2 (default): the single-step
+                           predictor-corrector (Mehrotra's method adapted to one Krylov solve
+                           per iteration, as Sec. 5 proposes): the affine predictor is
+                           P^{-1} rhs_aff (no product with G), sigma = (mu_aff / mu)^3
+                           clamped to [sigma_min, 1], and the corrector's complementarity
+                           rows target sigma mu - ds_aff o dnu_aff; after a PCG solve
+                           stopped at max_cg the next direction takes the fixed rule.
+                           1: adaptive, sigma = clamp((1 - alpha)^3, sigma_min, sigma_slow)
+                           from the last step alpha (the previous step standing in for an
+                           affine predictor; the first direction uses sigma; the fixed rule
+                           after a capped PCG solve); 0: sigma, or sigma_slow after a step
+                           alpha < 0.1                                                      */
+  double sigma_min;     /* lower clamp of sigma for rules 1 and 2 (default 0.01; rule 1 wants
+                           0.03: at 0.01 its PCG broke down on tiny problems below a 1e-12
+                           gap; rule 2 at 0 stalled on a 64^3 problem at a 1e-10 gap)        */
+  int exact_residual;   /* 0 (default): G beta is carried along with beta (the last pass of
+                           each PCG product also stores (G p)_beta -- from FP32 products in
+                           IPM_MIXED --, PCG accumulates G x = sum alpha G p in FP64 beside x,
+                           the step adds alpha G x), and an FP64 product recomputes it exactly
+                           only to confirm a stop test that passed on the carried value, so
+                           the reported gap is always an exact one; 1: an FP64 product
+                           recomputes G beta every IPM iteration.  Carrying applies with
+                           krylov = 0 and refine_every = 0; otherwise G beta is recomputed   */
   double precond_rho;   /* identity scale rho of the preconditioner
                            P = [rho I + Lambda1, Lambda2; Lambda2, Lambda1] (Sec. 3.5).
                            1 (default): the paper's P; 0: rho = n / m with m the number of

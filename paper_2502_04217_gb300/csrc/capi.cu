@@ -152,7 +152,7 @@ namespace {
 // and recomputes it with an FP64 product only to confirm a passed stop test;
 // mixed precision recomputes it every iteration (its PCG products are FP32).
 int incremental_gb(const sdft_ipm* h) {
-  return (h->opt.precision == IPM_FP64 && !h->opt.exact_residual && h->opt.krylov == 0) ? 1 : 0;
+  return (!h->opt.exact_residual && h->opt.krylov == 0 && h->opt.refine_every == 0) ? 1 : 0;
 }
 
 ipm_status fail_arg(sdft_ipm* h, const char* msg) {
@@ -639,7 +639,7 @@ ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
     a.check_done = (g.pcg || g.cr) ? 1 : 0;
     a.check_refine = g.refine ? 1 : 0;
     a.check_exact = g.exact ? 1 : 0;
-    if (last) a.gp_out = (g.pcg && !fp32 && incremental_gb(h)) ? h->w.Gp : nullptr;
+    if (last) a.gp_out = (g.pcg && incremental_gb(h)) ? h->w.Gp : nullptr;
   };
   ipm_status s;
   if (L.d == 1) {
@@ -746,7 +746,7 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (o.max_ipm < 0 || o.max_cg < 1 || o.cg_chunk < 1) return fail_arg(h, "iteration caps must be positive");
   if (o.refine_every < 0) return fail_arg(h, "refine_every must be >= 0");
   if (o.tile_engine < 0 || o.tile_engine > 2) return fail_arg(h, "tile_engine must be 0, 1 or 2");
-  if (o.sigma_rule < 0 || o.sigma_rule > 1) return fail_arg(h, "sigma_rule must be 0 or 1");
+  if (o.sigma_rule < 0 || o.sigma_rule > 2) return fail_arg(h, "sigma_rule must be 0, 1 or 2");
   if (o.exact_residual < 0 || o.exact_residual > 1) return fail_arg(h, "exact_residual must be 0 or 1");
   if (!(o.precond_rho >= 0.0) || !std::isfinite(o.precond_rho)) return fail_arg(h, "precond_rho must be >= 0 and finite");
   if (o.pdl < 0 || o.pdl > 1) return fail_arg(h, "pdl must be 0 or 1");
@@ -754,6 +754,8 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (o.krylov >= 1 && o.refine_every > 0) return fail_arg(h, "krylov = 1 (CR) or 2 (CAr) does not combine with refine_every");
   if (o.sigma_rule == 1 && !(o.sigma_min > 0 && o.sigma_min <= o.sigma_slow))
     return fail_arg(h, "sigma_min must lie in (0, sigma_slow]");
+  if (o.sigma_rule == 2 && !(o.sigma_min >= 0 && o.sigma_min < 1))
+    return fail_arg(h, "sigma_min must lie in [0, 1) for the predictor-corrector");
   if (!(o.sigma > 0 && o.sigma < 1) || !(o.sigma_slow > 0 && o.sigma_slow < 1)) return fail_arg(h, "sigma must lie in (0,1)");
   if (!(o.tau > 0 && o.tau < 1)) return fail_arg(h, "tau must lie in (0,1)");
   return IPM_OK;
@@ -782,8 +784,8 @@ void ipm_default_options(ipm_options* o) {
   o->tile_p = 0;
   o->refine_every = 0;
   o->tile_engine = 0;
-  o->sigma_rule = 1;
-  o->sigma_min = 0.03;
+  o->sigma_rule = 2;
+  o->sigma_min = 0.01;
   o->exact_residual = 0;
   o->precond_rho = 1.0;
   o->pdl = 1;
@@ -842,6 +844,12 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   // vectors of the other Krylov methods only when they are chosen
   if (o.krylov >= 1) for (double** p : {&h->w.wcr, &h->w.ucr}) CKC(dalloc(h, p, v4));
   if (o.krylov == 2) for (double** p : {&h->w.vcar, &h->w.Ucar}) CKC(dalloc(h, p, v4));
+  // the predictor-corrector's affine direction only when it is chosen
+  if (o.sigma_rule == 2)
+    for (double** p : {&h->w.ds1a, &h->w.ds2a}) {
+      CKC(dalloc(h, p, v2));
+      CKC(cudaMemsetAsync(*p, 0, v2, h->st));
+    }
   CKC(dalloc(h, &h->d_U, (size_t)L.H * 2 * sizeof(double)));
   CKC(cudaMemsetAsync(h->d_U, 0, (size_t)L.H * 2 * sizeof(double), h->st));
   CKC(dalloc(h, &h->d_sc, sizeof(DevScalars)));
@@ -901,6 +909,11 @@ ipm_status ipm_set_options(sdft_ipm* h, const ipm_options* opt) {
     for (double** p : {&h->w.wcr, &h->w.ucr}) CK(dalloc(h, p, v4));
   if (opt->krylov == 2 && !h->w.vcar)
     for (double** p : {&h->w.vcar, &h->w.Ucar}) CK(dalloc(h, p, v4));
+  if (opt->sigma_rule == 2 && !h->w.ds1a)
+    for (double** p : {&h->w.ds1a, &h->w.ds2a}) {
+      CK(dalloc(h, p, v4 / 2));
+      CK(cudaMemsetAsync(*p, 0, v4 / 2, h->st));
+    }
   h->opt = *opt;
   h->graph_valid = false;            // kernel arguments of the graph depend on the options
   if (rel_changed) {
@@ -997,9 +1010,16 @@ ipm_status queue_residual_and_test(sdft_ipm* h, LoopCtl ipm_loop) {
 
 ipm_status queue_prepare(sdft_ipm* h, LoopCtl cg_loop) {
   Reduce red{h->d_partials, h->d_counter};
+  const int pc = h->opt.sigma_rule == 2 ? 1 : 0;
+  if (pc) {
+    // single-step predictor-corrector: affine predictor from P^{-1}, Mehrotra's sigma and the
+    // second-order terms in one pass, then the Newton system of the corrector
+    ProfScope ps(h, kProfPrepare);
+    CK(k_predictor(h->lay, h->w, red, h->d_sc, h->opt.precond_rho, h->opt.sigma_min, 1.0, h->st));
+  }
   ProfScope ps(h, kProfPrepare);
   CK(k_prepare(h->lay, h->w, red, h->d_sc, h->opt.cg_tol, h->opt.cg_relative, cg_loop, h->opt.precond_rho,
-               h->opt.krylov == 2 ? 1 : 0, h->st));
+               h->opt.krylov == 2 ? 1 : 0, pc, h->st));
   return IPM_OK;
 }
 
@@ -1076,7 +1096,7 @@ ipm_status queue_step(sdft_ipm* h) {
   Reduce red{h->d_partials, h->d_counter};
   {
     ProfScope ps(h, kProfStep);
-    CK(k_step_length(h->lay, h->w, red, h->d_sc, h->opt.tau, h->st));
+    CK(k_step_length(h->lay, h->w, red, h->d_sc, h->opt.tau, h->opt.sigma_rule == 2 ? 1 : 0, h->st));
   }
   ProfScope ps(h, kProfStep);
   CK(k_step_update(h->lay, h->w, red, h->d_sc, h->opt.sigma, h->opt.sigma_slow, h->opt.sigma_rule,

@@ -52,6 +52,19 @@ __device__ __forceinline__ double f2d_int(float x) {
   const unsigned long long b = (e == 0u) ? s : (e == 255u ? (s | 0x7FF0000000000000ull | mant) : nrm);
   return __longlong_as_double((long long)b);
 }
+
+// 1/x by ONE Newton step y <- y + y (1 - x y) from the single-precision seed
+// (conversions on the integer pipe): relative error about (1.2e-7)^2 = 1.4e-14,
+// used for the barrier scalings of the Newton system, whose perturbation at that
+// level is invisible next to the PCG tolerance.  GB300 executes FP64 divides at
+// ~58 G/s; outside 2^+-120 (and for 0, inf, NaN) this falls back to a divide.
+__device__ __forceinline__ double rcp1(double x) {
+  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
+  if (ex < -120 || ex > 120) return 1.0 / x;
+  const double y = f2d_int(__frcp_rn(d2f_int(x)));
+  return fma(y, fma(-x, y, 1.0), y);
+}
 template <typename T> __device__ __forceinline__ T from_double(double x);
 template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_int(x); }

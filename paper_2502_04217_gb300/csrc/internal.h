@@ -31,6 +31,8 @@ struct DevScalars {
   double mu;         // duality measure (nu1^T s1 + nu2^T s2) / 2n
   double sigma;      // centring parameter for the next direction
   double alpha;      // last IPM step
+  double alpha_aff;  // predictor-corrector: step to the boundary along the affine predictor (<= 1)
+  double mu_aff;     // predictor-corrector: duality measure after that step
   double primal, dual, gap;
   double yy;         // ||b||^2 over observed samples
   double cmax;       // ||M_perp^T b||_inf
@@ -52,6 +54,10 @@ struct DevScalars {
   int incr;          // 1: G beta is updated from the PCG products and recomputed only to confirm the stop
   int exact_now;     // (incr) G beta is recomputed by an FP64 product in this IPM iteration
   int gb_products;   // FP64 products that recomputed G beta over the solve
+  int pc_skip;       // predictor-corrector: the last PCG solve stopped at max_cg, so this direction
+                     // takes the fixed centring rule and no second-order term
+  int confirming;    // (incr) this iteration's exact product confirms a stop test passed on the
+                     // carried G beta; if it fails, G beta is recomputed every iteration from then on
   int pad1;
   unsigned long long launches;   // kernels launched by the library (every kernel adds 1)
 };

@@ -21,19 +21,6 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ bool first_thread() { return threadIdx.x == 0 && blockIdx.x == 0; }
 
-// 1/x by ONE Newton step y <- y + y (1 - x y) from the single-precision seed
-// (conversions on the integer pipe): relative error about (1.2e-7)^2 = 1.4e-14,
-// used for the barrier scalings of the Newton system, whose perturbation at that
-// level is invisible next to the PCG tolerance.  GB300 executes FP64 divides at
-// ~58 G/s; outside 2^+-120 (and for 0, inf, NaN) this falls back to a divide.
-__device__ __forceinline__ double rcp1(double x) {
-  const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(x) >> 32);
-  const int ex = (int)((hi >> 20) & 0x7ffu) - 1023;
-  if (ex < -120 || ex > 120) return 1.0 / x;
-  const double y = f2d_int(__frcp_rn(d2f_int(x)));
-  return fma(y, fma(-x, y, 1.0), y);
-}
-
 __device__ __forceinline__ void set_cond(const LoopCtl& c, unsigned v) {
   if (c.use) cudaGraphSetConditional(c.handle, v);
 }
@@ -88,6 +75,8 @@ __global__ void __launch_bounds__(kThreads) cmax_kernel(const double* __restrict
 
 __device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double sigma0, int incr) {
   sc->incr = incr;
+  sc->pc_skip = 0;
+  sc->confirming = 0;
   sc->exact_now = 1;
   sc->gb_products = 0;
   sc->mu = mu;
@@ -182,14 +171,20 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
     sc->dual = D;
     sc->gap = gap;
     // incremental G beta: a stop test passed on the updated G beta is confirmed
-    // by an exact FP64 product first (this iteration takes no step)
+    // by an exact FP64 product first (this iteration takes no step).  A confirmation
+    // that fails shows the carried value is not accurate enough at this gap any more:
+    // from then on G beta is recomputed by an FP64 product every iteration (incr = 0,
+    // exact_now = 1: the residual product runs and the iteration steps as usual).
     const bool exact = !sc->incr || sc->exact_now;
+    const bool confirm = sc->confirming != 0;
+    sc->confirming = 0;
     if (exact) sc->gb_products += 1;
     if (!isfinite(gap) || !isfinite(sc->mu)) { sc->ipm_done = 1; sc->ipm_status = 6; }
     else if (gap <= gap_tol && exact) { sc->ipm_done = 1; sc->ipm_status = 0; }
-    else if (gap <= gap_tol) sc->exact_now = 1;
+    else if (gap <= gap_tol) { sc->exact_now = 1; sc->confirming = 1; }
     else if (sc->ipm_it >= max_ipm) { sc->ipm_done = 1; sc->ipm_status = 4; }
-    else sc->exact_now = 0;
+    else if (confirm) { sc->incr = 0; sc->exact_now = 1; }
+    else sc->exact_now = sc->incr ? 0 : 1;
     set_cond(ipm_loop, sc->ipm_done ? 0u : 1u);
   }
 }
@@ -201,9 +196,12 @@ __device__ __forceinline__ double precond_scale(double rho, const Layout& lay, c
   return rho > 0.0 ? rho : (double)lay.n / fmax(sc->nobs, 1.0);
 }
 
+// pc = 1 (predictor-corrector): 1/s, Lambda and P^{-1} were formed by predictor_kernel for this
+// iterate and are read back; the complementarity rows carry the second-order terms
+// ds_i,aff o dnu_i,aff left in ds1a, ds2a by predictor_kernel: r_ci = s_i nu_i - sigma mu + ds_i o dnu_i.
 __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                            DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop,
-                                                           double rho_opt, int car) {
+                                                           double rho_opt, int car, int pc) {
   pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
@@ -218,32 +216,48 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
-    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, rb = 0, rc = 0, zb = 0, zz = 0, is1 = 0, is2 = 0;
+    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc_ = 0, rb = 0, rc = 0, zb = 0, zz = 0, is1 = 0, is2 = 0;
     if (!is_ghost(lay, i)) {
       const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
-      is1 = rcp1(s1);
-      is2 = rcp1(s2);
-      const double S1 = n1 * is1, S2 = n2_ * is2;              // Sigma_i = S_i^{-1} V_i
+      double c1 = 0.0, c2 = 0.0;
+      if (pc) {
+        is1 = w.is1[i];
+        is2 = w.is2[i];
+        c1 = w.ds1a[i];
+        c2 = w.ds2a[i];
+      } else {
+        is1 = rcp1(s1);
+        is2 = rcp1(s2);
+      }
       const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
       const double r_z = lam - n1 - n2_;
       const double r_p1 = z + b - s1, r_p2 = z - b - s2;
-      // r_c_i / s_i + Sigma_i r_p_i = nu_i + (nu_i r_p_i - sigma mu) / s_i
-      const double A1 = fma(is1, fma(n1, r_p1, -smu), n1);
-      const double A2 = fma(is2, fma(n2_, r_p2, -smu), n2_);
+      // r_c_i / s_i + Sigma_i r_p_i = nu_i + (nu_i r_p_i + c_i - sigma mu) / s_i
+      const double A1 = fma(is1, fma(n1, r_p1, c1 - smu), n1);
+      const double A2 = fma(is2, fma(n2_, r_p2, c2 - smu), n2_);
       rb = -r_d - A1 + A2;
       rc = -r_z - A1 - A2;
-      l1 = S1 + S2;
-      l2 = S1 - S2;
-      const double iD = rcp1(fma(4.0 * S1, S2, prho * l1));     // D = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2
-      pa = l1 * iD;
-      pb = l2 * iD;
-      pc = (prho + l1) * iD;
+      if (pc) {
+        pa = w.pa[i];
+        pb = w.pb[i];
+        pc_ = w.pc[i];
+      } else {
+        const double S1 = n1 * is1, S2 = n2_ * is2;              // Sigma_i = S_i^{-1} V_i
+        l1 = S1 + S2;
+        l2 = S1 - S2;
+        const double iD = rcp1(fma(4.0 * S1, S2, prho * l1));   // D = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2
+        pa = l1 * iD;
+        pb = l2 * iD;
+        pc_ = (prho + l1) * iD;
+      }
       zb = pa * rb - pb * rc;
-      zz = -pb * rb + pc * rc;
+      zz = -pb * rb + pc_ * rc;
     }
-    w.is1[i] = is1; w.is2[i] = is2;
-    w.lam1[i] = l1; w.lam2[i] = l2;
-    w.pa[i] = pa; w.pb[i] = pb; w.pc[i] = pc;
+    if (!pc) {
+      w.is1[i] = is1; w.is2[i] = is2;
+      w.lam1[i] = l1; w.lam2[i] = l2;
+      w.pa[i] = pa; w.pb[i] = pb; w.pc[i] = pc_;
+    }
     w.x[i] = 0.0; w.x[n2 + i] = 0.0;
     w.r[i] = rb; w.r[n2 + i] = rc;
     w.rhs[i] = rb; w.rhs[n2 + i] = rc;
@@ -265,6 +279,91 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     sc->rho_car0 = 0.0;
     if (!isfinite(rho)) { sc->cg_status = 2; sc->cg_done = 1; }
     set_cond(cg_loop, sc->cg_done ? 0u : 1u);
+  }
+}
+
+// Single-step predictor-corrector (Mehrotra's method with one Krylov solve per
+// iteration).  The affine-scaling predictor (the Newton direction for sigma = 0) is
+// taken as P^{-1} rhs_aff with the closed-form inverse of Eq. (invprecond1): P differs
+// from K only by [G - I, 0; 0, 0], minus the projector onto the missing samples, so
+// the estimate costs no product with G.  This kernel forms, at the current iterate,
+// everything of the Newton system that does not depend on sigma (1/s, Lambda1,
+// Lambda2, P^{-1}'s coefficients, exactly as prepare_kernel would), then the predictor
+// ds_i = dz +- dbeta + r_p_i, dnu_i = -nu_i - Sigma_i ds_i and the corrector's
+// second-order terms ds1 o dnu1, ds2 o dnu2 (written to ds1a, ds2a; 0 when pc_skip),
+// all in FP64: near convergence Sigma_i reaches 1e10 and more, and dnu_i = -nu_i -
+// Sigma_i ds_i amplifies any rounding of ds_i by that much (an FP32 predictor drove
+// solves into the iteration cap).  One grid reduction gives the largest step
+// alpha_aff <= 1 keeping (s, nu) >= 0 (ratio test in FP32 on FP32 roundings, as
+// step_length_kernel) and ds^T dnu; the predictor satisfies s o dnu + nu o ds = -s o nu
+// by construction of dnu, so (s + a ds)^T (nu + a dnu) = (1 - a) s^T nu + a^2 ds^T dnu and
+//     mu_aff = (1 - alpha_aff) mu + alpha_aff^2 ds^T dnu / 2n;
+// sigma = (mu_aff / mu)^3 clamped to [sigma_min, sigma_max] follows in the last block.
+// After a PCG solve stopped at max_cg (pc_skip) sigma stays the fixed rule's.
+__global__ void __launch_bounds__(kThreads) predictor_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
+                                                             DevScalars* sc, double rho_opt, double sigma_min,
+                                                             double sigma_max) {
+  pdl_wait();
+  __shared__ double scratch[2 * 32];
+  count_launch(sc);
+  if (sc->ipm_done || (sc->incr && sc->exact_now)) return;
+  const long long n2 = 2 * lay.H;
+  const double lam = sc->lambda;
+  const double prho = precond_scale(rho_opt, lay, sc);
+  const bool skip = sc->pc_skip != 0;
+  float best = __int_as_float(0x7f800000);   // +inf
+  auto consider = [&](double wv, double dw) {
+    if (__double_as_longlong(dw) < 0) best = fminf(best, d2f_int(wv) / d2f_int(-dw));
+  };
+  double a2 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, is1 = 0, is2 = 0, c1 = 0, c2 = 0;
+    if (!is_ghost(lay, i)) {
+      const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
+      is1 = rcp1(s1);
+      is2 = rcp1(s2);
+      const double S1 = n1 * is1, S2 = n2_ * is2;
+      l1 = S1 + S2;
+      l2 = S1 - S2;
+      const double iD = rcp1(fma(4.0 * S1, S2, prho * l1));
+      pa = l1 * iD;
+      pb = l2 * iD;
+      pc = (prho + l1) * iD;
+      const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
+      const double r_z = lam - n1 - n2_;
+      const double r_p1 = z + b - s1, r_p2 = z - b - s2;
+      // sigma = 0: r_c_i / s_i + Sigma_i r_p_i = nu_i + Sigma_i r_p_i
+      const double A1 = fma(S1, r_p1, n1), A2 = fma(S2, r_p2, n2_);
+      const double rb = -r_d - A1 + A2, rc = -r_z - A1 - A2;
+      const double db = fma(pa, rb, -pb * rc), dz = fma(pc, rc, -pb * rb);
+      const double ds1 = dz + db + r_p1, ds2 = dz - db + r_p2;
+      const double dn1 = -fma(S1, ds1, n1), dn2 = -fma(S2, ds2, n2_);
+      consider(s1, ds1);
+      consider(s2, ds2);
+      consider(n1, dn1);
+      consider(n2_, dn2);
+      c1 = ds1 * dn1;
+      c2 = ds2 * dn2;
+      a2 += c1 + c2;
+    }
+    w.is1[i] = is1; w.is2[i] = is2;
+    w.lam1[i] = l1; w.lam2[i] = l2;
+    w.pa[i] = pa; w.pb[i] = pb; w.pc[i] = pc;
+    w.ds1a[i] = skip ? 0.0 : c1;
+    w.ds2a[i] = skip ? 0.0 : c2;
+  }
+  double v[2] = {(double)best, a2};
+  const int ops[2] = {RED_MIN, RED_SUM};
+  if (grid_reduce<2>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    const double al = fmin(1.0, v[0]);
+    const double mu = sc->mu;
+    const double mu_aff = fma(1.0 - al, mu, al * al * v[1] / (2.0 * (double)lay.n));
+    sc->alpha_aff = al;
+    sc->mu_aff = mu_aff;
+    if (!skip) {
+      const double t = mu_aff / mu;
+      sc->sigma = fmin(sigma_max, fmax(sigma_min, t * t * t));
+    }
   }
 }
 
@@ -579,23 +678,26 @@ __global__ void __launch_bounds__(kThreads) refine_kernel(long long n2, IpmVecto
   }
 }
 
-// Newton direction of the eliminated variables (same arithmetic in both step kernels)
+// Newton direction of the eliminated variables (same arithmetic in both step kernels):
+// ds1 = dz + dbeta + r_p1, ds2 = dz - dbeta + r_p2, dnu_i = -r_ci / s_i - Sigma_i ds_i with
+// r_ci = s_i nu_i - sigma mu (+ the predictor-corrector's second-order term c_i when pc).
 struct Dir { double ds1, ds2, dn1, dn2; };
-__device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long long n2, double smu) {
+__device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long long n2, double smu, int pc) {
   const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
   const double db = w.x[i], dz = w.x[n2 + i];
   const double is1 = w.is1[i], is2 = w.is2[i];       // 1/s of this iterate, from prepare_kernel
+  const double c1 = pc ? w.ds1a[i] : 0.0, c2 = pc ? w.ds2a[i] : 0.0;
   Dir d;
   d.ds1 = dz + db + (z + b - s1);
   d.ds2 = dz - db + (z - b - s2);
-  d.dn1 = -(n1 - smu * is1) - (n1 * is1) * d.ds1;
-  d.dn2 = -(n2_ - smu * is2) - (n2_ * is2) * d.ds2;
+  d.dn1 = -fma(c1 - smu, is1, n1) - (n1 * is1) * d.ds1;
+  d.dn2 = -fma(c2 - smu, is2, n2_) - (n2_ * is2) * d.ds2;
   return d;
 }
 
 // Largest step keeping (s, nu) >= 0; alpha = min(1, tau * alpha_max)
 __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
-                                                               DevScalars* sc, double tau) {
+                                                               DevScalars* sc, double tau, int pc) {
   pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
@@ -611,7 +713,7 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
   };
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i)) continue;
-    const Dir d = direction(w, i, n2, smu);
+    const Dir d = direction(w, i, n2, smu, pc);
     consider(w.s1[i], d.ds1);
     consider(w.s2[i], d.ds2);
     consider(w.nu1[i], d.dn1);
@@ -637,7 +739,7 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i)) continue;
-    const Dir d = direction(w, i, n2, smu);
+    const Dir d = direction(w, i, n2, smu, sigma_rule == 2);
     w.beta[i] += alpha * w.x[i];
     if (incr) w.Gb[i] += alpha * w.Gx[i];        // G beta follows beta (G is linear)
     w.z[i] += alpha * w.x[n2 + i];
@@ -656,8 +758,11 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
       const double t = 1.0 - alpha;
       sc->sigma = fmin(sigma_slow, fmax(sigma_min, t * t * t));
     } else {
+      // the fixed rule; with the predictor-corrector (sigma_rule 2) the next corrector
+      // replaces it unless this PCG solve stopped at max_cg
       sc->sigma = (alpha < 0.1) ? sigma_slow : sigma0;
     }
+    sc->pc_skip = sc->cg_status == 1 ? 1 : 0;
     sc->ipm_it += 1;
     sc->cg_total += sc->cg_iter;
     if (sc->cg_iter > sc->cg_max) sc->cg_max = sc->cg_iter;
@@ -768,8 +873,13 @@ cudaError_t k_certificate(const Layout& lay, const double* beta, const double* G
   return launch_k(certificate_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, beta, Gb, c, red.partials, red.counter, sc, gap_tol, max_ipm, loop);
 }
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, double rho, int car, cudaStream_t st) {
-  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho, car);
+                      LoopCtl loop, double rho, int car, int pc, cudaStream_t st) {
+  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho, car, pc);
+}
+cudaError_t k_predictor(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double rho, double sigma_min,
+                        double sigma_max, cudaStream_t st) {
+  return launch_k(predictor_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter,
+                  sc, rho, sigma_min, sigma_max);
 }
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
                          IpmVectors w, DevScalars* sc, double rho, cudaStream_t st) {
@@ -807,8 +917,9 @@ cudaError_t k_car_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScala
   return launch_k(car_update_b_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
                   red.counter, sc, max_cg, loop);
 }
-cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st) {
-  return launch_k(step_length_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, tau);
+cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, int pc,
+                          cudaStream_t st) {
+  return launch_k(step_length_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, tau, pc);
 }
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           int sigma_rule, double sigma_min, cudaStream_t st) {

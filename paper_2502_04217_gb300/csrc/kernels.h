@@ -20,6 +20,8 @@ struct IpmVectors {
   double *vcar, *Ucar;                        // conjugate A-residuals: v = K y and U = v + beta U (4H each)
   double *Gp, *Gx;                            // incremental G beta: (G p)_beta of the last PCG product and
                                               // (G x)_beta = sum alpha (G p)_beta over the PCG solve (2H each)
+  double *ds1a, *ds2a;                        // predictor-corrector: the second-order terms ds1 o dnu1,
+                                              // ds2 o dnu2 of the affine predictor (2H each)
 };
 
 // grid size used by every elementwise kernel (also sizes the partials buffer)
@@ -56,7 +58,9 @@ cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, do
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
                           DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st);
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, double rho, int car, cudaStream_t st);
+                      LoopCtl loop, double rho, int car, int pc, cudaStream_t st);
+cudaError_t k_predictor(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double rho, double sigma_min,
+                        double sigma_max, cudaStream_t st);
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
                          IpmVectors w, DevScalars* sc, double rho, cudaStream_t st);
 cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st);
@@ -71,7 +75,8 @@ cudaError_t k_car_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScala
                            cudaStream_t st);
 cudaError_t k_car_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
                            cudaStream_t st);
-cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, cudaStream_t st);
+cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, int pc,
+                          cudaStream_t st);
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           int sigma_rule, double sigma_min, cudaStream_t st);
 cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, DevScalars* sc, cudaStream_t st);

@@ -326,7 +326,9 @@ __global__ void loss_kernel(Layout lay, const float* __restrict__ y, const doubl
 // s1 = z + beta0, s2 = z - beta0, nu_i = mu0 / s_i.  A coordinate predicted
 // inactive gets s1 = s2 = 2 mu0/lambda and nu1 = nu2 = lambda/2 (feasible and
 // centred); an active one gets its small slack mu0/lambda with multiplier
-// lambda.  Every s_i nu_i equals mu0.
+// lambda.  Every s_i nu_i equals mu0 (to the Newton reciprocal's 1.4e-14).  The
+// sigmoid only shapes the margin delta in [mu0/lambda, 2 mu0/lambda] and is
+// evaluated in FP32 (z, s within 1.2e-7 mu0/lambda of an FP64 evaluation).
 __global__ void point_kernel(Layout lay, const float* __restrict__ y, const double* __restrict__ c, const DevScalars* sc,
                              double mu_scale, IpmVectors w) {
   const double lam = sc->lambda, il = 1.0 / lam;
@@ -340,15 +342,15 @@ __global__ void point_kernel(Layout lay, const float* __restrict__ y, const doub
     const long long s = i >> 1;
     const int cc = (int)(i & 1);
     const double b0 = lam * (soft1(c[i] * il) + (double)y[s * 8 + cc]);
-    const double p = 1.0 / (1.0 + exp(-(double)y[s * 8 + 2 + cc]));
-    const double z = fabs(b0) + (mu0 * il) * (2.0 - p);
+    const float p = 1.0f / (1.0f + expf(-y[s * 8 + 2 + cc]));
+    const double z = fabs(b0) + (mu0 * il) * (2.0 - f2d_int(p));
     const double s1 = z + b0, s2 = z - b0;
     w.beta[i] = b0;
     w.z[i] = z;
     w.s1[i] = s1;
     w.s2[i] = s2;
-    w.nu1[i] = mu0 / s1;
-    w.nu2[i] = mu0 / s2;
+    w.nu1[i] = mu0 * rcp1(s1);
+    w.nu2[i] = mu0 * rcp1(s2);
   }
 }
 

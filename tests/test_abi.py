@@ -86,19 +86,20 @@ def test_null_handle_calls_fail_cleanly(lib):
 
 def test_default_options_of_the_solver_variants(lib):
     o = binding.default_options()
-    assert o.tile_engine == 0 and o.sigma_rule == 1 and o.sigma_min == 0.03
+    assert o.tile_engine == 0 and o.sigma_rule == 2 and o.sigma_min == 0.01
     assert o.exact_residual == 0 and o.precond_rho == 1.0 and o.pdl == 1 and o.krylov == 0
 
 
-@pytest.mark.parametrize("field,value", [("tile_engine", 3), ("sigma_rule", 2), ("sigma_min", 0.0),
-                                         ("sigma_min", 0.9), ("exact_residual", 2), ("precond_rho", -1.0), ("pdl", 2), ("krylov", 3),
-                                         ("krylov", -1),
-                                         ("precond_rho", float("inf"))])
-def test_create_rejects_bad_variant_options(lib, field, value):
+@pytest.mark.parametrize("field,value,extra", [("tile_engine", 3, {}), ("sigma_rule", 3, {}), ("sigma_rule", -1, {}),
+                                               ("sigma_min", -0.1, {}), ("sigma_min", 1.0, {}),
+                                               ("sigma_min", 0.0, {"sigma_rule": 1}), ("sigma_min", 0.9, {"sigma_rule": 1}),
+                                               ("exact_residual", 2, {}), ("precond_rho", -1.0, {}), ("pdl", 2, {}),
+                                               ("krylov", 3, {}), ("krylov", -1, {}), ("precond_rho", float("inf"), {})])
+def test_create_rejects_bad_variant_options(lib, field, value, extra):
     h = ctypes.c_void_p()
     d = (ctypes.c_int64 * 1)(8)
     dummy = (ctypes.c_double * 8)()
-    o = binding.default_options(**{field: value})
+    o = binding.default_options(**{field: value}, **extra)
     st = lib.ipm_create(ctypes.byref(h), 1, d, ctypes.cast(dummy, ctypes.c_void_p),
                         ctypes.cast(dummy, ctypes.c_void_p), 1.0, ctypes.byref(o), None)
     assert st == binding.IPM_ERR_ARG and field in binding.ipm_last_error(None)
