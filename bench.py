@@ -278,11 +278,12 @@ def _class_model(dims, prec, res, opt):
         FP64); the middle pass also reads the mask bits (n / 8 B);
       pcg_update: reads x, r, p, q and P^{-1}'s three coefficients, writes x, r, z (272 B);
       prepare: reads beta, z, s1, s2, nu1, nu2, G beta, c (128 B), writes 1/s1, 1/s2,
-        Lambda1, Lambda2, P^{-1}'s coefficients (112 B) and x, r, rhs, z, p (160 B);
+        Lambda1, Lambda2, P^{-1}'s coefficients (112 B) and x, r, z, p (128 B; the
+        right-hand side too, 32 B, only with FP64 residual replacement);
         with the predictor-corrector (sigma_rule 2) the class holds two kernels: the
-        predictor reads the iterate (128 B) and writes 1/s, Lambda, P^{-1} and the two
-        second-order terms (144 B), prepare reads the iterate, 1/s, P^{-1} and the terms
-        (240 B) and writes x, r, rhs, z, p (160 B);
+        predictor reads the iterate (128 B) and writes 1/s, Lambda, P^{-1}, the two
+        second-order terms and the affine right-hand side (176 B), prepare reads that
+        right-hand side, the terms, 1/s and P^{-1} (144 B) and writes x, r, z, p (128 B);
       step: step_length reads x, beta, z, s, nu, 1/s (160 B), step_update reads the same
         and writes beta, z, s, nu (96 B); with the predictor-corrector each also reads
         the two terms (32 B);
@@ -329,10 +330,11 @@ def _class_model(dims, prec, res, opt):
                               n_res * 2 * 32 * H + n_pcg * 2 * 2 * esz * H)
     out["pcg_update"] = (n_pcg, 0.0, n_pcg * (272 * H + (48 * H if incr else 0)))
     gx = 16 * H if incr else 0
+    rhs = 32 * H if (mixed and opt.refine_every > 0) else 0
     if pc:
-        out["prepare"] = (2 * it, 0.0, it * ((128 + 144) * H + (240 + 160) * H + gx))
+        out["prepare"] = (2 * it, 0.0, it * ((128 + 176) * H + (144 + 128) * H + rhs + gx))
     else:
-        out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 160 * H + gx))
+        out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 128 * H + rhs + gx))
     out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (32 * H if incr else 0) + (64 * H if pc else 0)))
     return out
 

@@ -846,7 +846,7 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   if (o.krylov == 2) for (double** p : {&h->w.vcar, &h->w.Ucar}) CKC(dalloc(h, p, v4));
   // the predictor-corrector's affine direction only when it is chosen
   if (o.sigma_rule == 2)
-    for (double** p : {&h->w.ds1a, &h->w.ds2a}) {
+    for (double** p : {&h->w.ds1a, &h->w.ds2a, &h->w.rba, &h->w.rca}) {
       CKC(dalloc(h, p, v2));
       CKC(cudaMemsetAsync(*p, 0, v2, h->st));
     }
@@ -910,7 +910,7 @@ ipm_status ipm_set_options(sdft_ipm* h, const ipm_options* opt) {
   if (opt->krylov == 2 && !h->w.vcar)
     for (double** p : {&h->w.vcar, &h->w.Ucar}) CK(dalloc(h, p, v4));
   if (opt->sigma_rule == 2 && !h->w.ds1a)
-    for (double** p : {&h->w.ds1a, &h->w.ds2a}) {
+    for (double** p : {&h->w.ds1a, &h->w.ds2a, &h->w.rba, &h->w.rca}) {
       CK(dalloc(h, p, v4 / 2));
       CK(cudaMemsetAsync(*p, 0, v4 / 2, h->st));
     }
@@ -1018,8 +1018,9 @@ ipm_status queue_prepare(sdft_ipm* h, LoopCtl cg_loop) {
     CK(k_predictor(h->lay, h->w, red, h->d_sc, h->opt.precond_rho, h->opt.sigma_min, 1.0, h->st));
   }
   ProfScope ps(h, kProfPrepare);
+  const int keep_rhs = (h->opt.precision == IPM_MIXED && h->opt.refine_every > 0) ? 1 : 0;
   CK(k_prepare(h->lay, h->w, red, h->d_sc, h->opt.cg_tol, h->opt.cg_relative, cg_loop, h->opt.precond_rho,
-               h->opt.krylov == 2 ? 1 : 0, pc, h->st));
+               h->opt.krylov == 2 ? 1 : 0, pc, keep_rhs, h->st));
   return IPM_OK;
 }
 

@@ -196,12 +196,15 @@ __device__ __forceinline__ double precond_scale(double rho, const Layout& lay, c
   return rho > 0.0 ? rho : (double)lay.n / fmax(sc->nobs, 1.0);
 }
 
-// pc = 1 (predictor-corrector): 1/s, Lambda and P^{-1} were formed by predictor_kernel for this
-// iterate and are read back; the complementarity rows carry the second-order terms
-// ds_i,aff o dnu_i,aff left in ds1a, ds2a by predictor_kernel: r_ci = s_i nu_i - sigma mu + ds_i o dnu_i.
+// pc = 1 (predictor-corrector): 1/s, P^{-1} and the affine right-hand side (rb_aff, rc_aff for
+// sigma = 0) were formed by predictor_kernel for this iterate and are read back; the
+// complementarity rows carry the second-order terms c_i = ds_i,aff o dnu_i,aff left in ds1a,
+// ds2a: r_ci = s_i nu_i - sigma mu + c_i adds e_i = (c_i - sigma mu) / s_i to r_ci / s_i, so
+// rb = rb_aff - e1 + e2, rc = rc_aff - e1 - e2.  keep_rhs: also store the right-hand side
+// (read by refine_kernel only).
 __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                            DevScalars* sc, double cg_tol, int cg_relative, LoopCtl cg_loop,
-                                                           double rho_opt, int car, int pc) {
+                                                           double rho_opt, int car, int pc, int keep_rhs) {
   pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
@@ -217,31 +220,30 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     double l1 = 0, l2 = 0, pa = 0, pb = 0, pc_ = 0, rb = 0, rc = 0, zb = 0, zz = 0, is1 = 0, is2 = 0;
-    if (!is_ghost(lay, i)) {
+    if (pc && !is_ghost(lay, i)) {
+      is1 = w.is1[i];
+      is2 = w.is2[i];
+      const double e1 = (w.ds1a[i] - smu) * is1, e2 = (w.ds2a[i] - smu) * is2;
+      rb = w.rba[i] - e1 + e2;
+      rc = w.rca[i] - e1 - e2;
+      pa = w.pa[i];
+      pb = w.pb[i];
+      pc_ = w.pc[i];
+      zb = pa * rb - pb * rc;
+      zz = -pb * rb + pc_ * rc;
+    } else if (!is_ghost(lay, i)) {
       const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
-      double c1 = 0.0, c2 = 0.0;
-      if (pc) {
-        is1 = w.is1[i];
-        is2 = w.is2[i];
-        c1 = w.ds1a[i];
-        c2 = w.ds2a[i];
-      } else {
-        is1 = rcp1(s1);
-        is2 = rcp1(s2);
-      }
+      is1 = rcp1(s1);
+      is2 = rcp1(s2);
       const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
       const double r_z = lam - n1 - n2_;
       const double r_p1 = z + b - s1, r_p2 = z - b - s2;
-      // r_c_i / s_i + Sigma_i r_p_i = nu_i + (nu_i r_p_i + c_i - sigma mu) / s_i
-      const double A1 = fma(is1, fma(n1, r_p1, c1 - smu), n1);
-      const double A2 = fma(is2, fma(n2_, r_p2, c2 - smu), n2_);
+      // r_c_i / s_i + Sigma_i r_p_i = nu_i + (nu_i r_p_i - sigma mu) / s_i
+      const double A1 = fma(is1, fma(n1, r_p1, -smu), n1);
+      const double A2 = fma(is2, fma(n2_, r_p2, -smu), n2_);
       rb = -r_d - A1 + A2;
       rc = -r_z - A1 - A2;
-      if (pc) {
-        pa = w.pa[i];
-        pb = w.pb[i];
-        pc_ = w.pc[i];
-      } else {
+      {
         const double S1 = n1 * is1, S2 = n2_ * is2;              // Sigma_i = S_i^{-1} V_i
         l1 = S1 + S2;
         l2 = S1 - S2;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
     }
     w.x[i] = 0.0; w.x[n2 + i] = 0.0;
     w.r[i] = rb; w.r[n2 + i] = rc;
-    w.rhs[i] = rb; w.rhs[n2 + i] = rc;
+    if (keep_rhs) { w.rhs[i] = rb; w.rhs[n2 + i] = rc; }
     w.zv[i] = zb; w.zv[n2 + i] = zz;
     w.p[i] = zb; w.p[n2 + i] = zz;
     if (incr) w.Gx[i] = 0.0;
@@ -288,9 +290,10 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
 // from K only by [G - I, 0; 0, 0], minus the projector onto the missing samples, so
 // the estimate costs no product with G.  This kernel forms, at the current iterate,
 // everything of the Newton system that does not depend on sigma (1/s, Lambda1,
-// Lambda2, P^{-1}'s coefficients, exactly as prepare_kernel would), then the predictor
-// ds_i = dz +- dbeta + r_p_i, dnu_i = -nu_i - Sigma_i ds_i and the corrector's
-// second-order terms ds1 o dnu1, ds2 o dnu2 (written to ds1a, ds2a; 0 when pc_skip),
+// Lambda2, P^{-1}'s coefficients, exactly as prepare_kernel would) and the affine
+// right-hand side (rba, rca), then the predictor ds_i = dz +- dbeta + r_p_i,
+// dnu_i = -nu_i - Sigma_i ds_i and the corrector's second-order terms ds1 o dnu1,
+// ds2 o dnu2 (written to ds1a, ds2a; 0 when pc_skip),
 // all in FP64: near convergence Sigma_i reaches 1e10 and more, and dnu_i = -nu_i -
 // Sigma_i ds_i amplifies any rounding of ds_i by that much (an FP32 predictor drove
 // solves into the iteration cap).  One grid reduction gives the largest step
@@ -317,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(Layout lay, IpmVect
   };
   double a2 = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
-    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, is1 = 0, is2 = 0, c1 = 0, c2 = 0;
+    double l1 = 0, l2 = 0, pa = 0, pb = 0, pc = 0, is1 = 0, is2 = 0, c1 = 0, c2 = 0, rb = 0, rc = 0;
     if (!is_ghost(lay, i)) {
       const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
       is1 = rcp1(s1);
@@ -334,7 +337,8 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(Layout lay, IpmVect
       const double r_p1 = z + b - s1, r_p2 = z - b - s2;
       // sigma = 0: r_c_i / s_i + Sigma_i r_p_i = nu_i + Sigma_i r_p_i
       const double A1 = fma(S1, r_p1, n1), A2 = fma(S2, r_p2, n2_);
-      const double rb = -r_d - A1 + A2, rc = -r_z - A1 - A2;
+      rb = -r_d - A1 + A2;
+      rc = -r_z - A1 - A2;
       const double db = fma(pa, rb, -pb * rc), dz = fma(pc, rc, -pb * rb);
       const double ds1 = dz + db + r_p1, ds2 = dz - db + r_p2;
       const double dn1 = -fma(S1, ds1, n1), dn2 = -fma(S2, ds2, n2_);
@@ -351,6 +355,8 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(Layout lay, IpmVect
     w.pa[i] = pa; w.pb[i] = pb; w.pc[i] = pc;
     w.ds1a[i] = skip ? 0.0 : c1;
     w.ds2a[i] = skip ? 0.0 : c2;
+    w.rba[i] = rb;
+    w.rca[i] = rc;
   }
   double v[2] = {(double)best, a2};
   const int ops[2] = {RED_MIN, RED_SUM};
@@ -873,8 +879,8 @@ cudaError_t k_certificate(const Layout& lay, const double* beta, const double* G
   return launch_k(certificate_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, beta, Gb, c, red.partials, red.counter, sc, gap_tol, max_ipm, loop);
 }
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, double rho, int car, int pc, cudaStream_t st) {
-  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho, car, pc);
+                      LoopCtl loop, double rho, int car, int pc, int keep_rhs, cudaStream_t st) {
+  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho, car, pc, keep_rhs);
 }
 cudaError_t k_predictor(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double rho, double sigma_min,
                         double sigma_max, cudaStream_t st) {

@@ -22,6 +22,8 @@ struct IpmVectors {
                                               // (G x)_beta = sum alpha (G p)_beta over the PCG solve (2H each)
   double *ds1a, *ds2a;                        // predictor-corrector: the second-order terms ds1 o dnu1,
                                               // ds2 o dnu2 of the affine predictor (2H each)
+  double *rba, *rca;                          // predictor-corrector: the condensed right-hand side of the
+                                              // affine system (sigma = 0, no second-order term; 2H each)
 };
 
 // grid size used by every elementwise kernel (also sizes the partials buffer)
@@ -58,7 +60,7 @@ cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, do
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
                           DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st);
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
-                      LoopCtl loop, double rho, int car, int pc, cudaStream_t st);
+                      LoopCtl loop, double rho, int car, int pc, int keep_rhs, cudaStream_t st);
 cudaError_t k_predictor(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double rho, double sigma_min,
                         double sigma_max, cudaStream_t st);
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
