@@ -269,7 +269,7 @@ def _class_model(dims, prec, res, opt):
 
     Products with G: the PCG products (cg_iters_total; FP32 passes in mixed mode) and
     the FP64 products that computed G beta exactly (kkt_products - cg_iters_total -
-    refinements).  Bytes per half-spectrum slot (H slots; a beta-layout vector is 16 B
+    refinements = exact_products).  Bytes per half-spectrum slot (H slots; a beta-layout vector is 16 B
     per slot, a two-block PCG vector 32 B):
       PCG product: first row pass reads z, p and writes p (96 B) and the work buffer;
         last row pass reads the buffer, p, Lambda1, Lambda2 and writes q (96 B);
@@ -285,8 +285,9 @@ def _class_model(dims, prec, res, opt):
         second-order terms and the affine right-hand side (176 B), prepare reads that
         right-hand side, the terms, 1/s and P^{-1} (144 B) and writes x, r, z, p (128 B);
       step: step_length reads x, beta, z, s, nu, 1/s (160 B), step_update reads the same
-        and writes beta, z, s, nu (96 B); with the predictor-corrector each also reads
-        the two terms (32 B);
+        and writes beta, z, s, nu (96 B); with the predictor-corrector step_length also
+        reads the two terms (32 B) and writes the direction ds, dnu (64 B), which
+        step_update reads instead of 1/s and the terms;
       certificate: reads beta, G beta, c (48 B);
       G beta carried (exact_residual 0, CG, no refinement): the last pass of a PCG
         product also writes (G p)_beta (16 B), pcg_update updates G x (48 B), prepare
@@ -307,26 +308,27 @@ def _class_model(dims, prec, res, opt):
     incr = not opt.exact_residual and opt.krylov == 0 and opt.refine_every == 0   # G beta carried
     esz = 8 if mixed else 16                 # bytes of one complex value of the PCG passes
     n_pcg = res["cg_iters_total"]
-    n_res = res["kkt_products"] - res["cg_iters_total"] - res.get("refinements", 0)
+    n_res = res["kkt_products"] - res["cg_iters_total"] - res.get("refinements", 0)   # FP64 G beta
     it = res["ipm_iters"]
     out = {}
     mid_flops = M * 2 * 2.5 * Nl * math.log2(max(Nl, 2))
     gp = 16 * H if incr else 0
+    nP = n_res + n_pcg                              # products of either kind
     if d == 1:
         res_b = 16 * H + 16 * H + n / 8
         pcg_b = 96 * H + 96 * H + gp + n / 8
-        out["fft_middle"] = (n_res + n_pcg, (n_res + n_pcg) * mid_flops, n_res * res_b + n_pcg * pcg_b)
+        out["fft_middle"] = (nP, nP * mid_flops, n_res * res_b + n_pcg * pcg_b)
     else:
         L = dims[1] if d == 3 else dims[0]
         row_flops = (H // L) * 5 * L * math.log2(L)
         res_row = (16 * H + 16 * H) + (16 * H + 16 * H)
         pcg_row = (96 * H + esz * H) + (esz * H + 96 * H + gp)
-        out["fft_row"] = (2 * (n_res + n_pcg), 2 * (n_res + n_pcg) * row_flops, n_res * res_row + n_pcg * pcg_row)
-        out["fft_middle"] = (n_res + n_pcg, (n_res + n_pcg) * mid_flops,
+        out["fft_row"] = (2 * nP, 2 * nP * row_flops, n_res * res_row + n_pcg * pcg_row)
+        out["fft_middle"] = (nP, nP * mid_flops,
                              n_res * (32 * H + n / 8) + n_pcg * (2 * esz * H + n / 8))
         if d == 3:
             col_flops = (H // dims[0]) * 5 * dims[0] * math.log2(dims[0])
-            out["fft_col"] = (2 * (n_res + n_pcg), 2 * (n_res + n_pcg) * col_flops,
+            out["fft_col"] = (2 * nP, 2 * nP * col_flops,
                               n_res * 2 * 32 * H + n_pcg * 2 * 2 * esz * H)
     out["pcg_update"] = (n_pcg, 0.0, n_pcg * (272 * H + (48 * H if incr else 0)))
     gx = 16 * H if incr else 0
@@ -335,7 +337,9 @@ def _class_model(dims, prec, res, opt):
         out["prepare"] = (2 * it, 0.0, it * ((128 + 176) * H + (144 + 128) * H + rhs + gx))
     else:
         out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 128 * H + rhs + gx))
-    out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (32 * H if incr else 0) + (64 * H if pc else 0)))
+    # with the predictor-corrector step_length also reads the two terms and writes the direction
+    # (+32 + 64 B); step_update reads the direction instead of 1/s and the terms (same count)
+    out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (32 * H if incr else 0) + (96 * H if pc else 0)))
     return out
 
 

@@ -133,9 +133,12 @@ typedef struct {
                            IPM_MIXED --, PCG accumulates G x = sum alpha G p in FP64 beside x,
                            the step adds alpha G x), and an FP64 product recomputes it exactly
                            only to confirm a stop test that passed on the carried value, so
-                           the reported gap is always an exact one; 1: an FP64 product
-                           recomputes G beta every IPM iteration.  Carrying applies with
-                           krylov = 0 and refine_every = 0; otherwise G beta is recomputed   */
+                           the reported gap is always an exact one; a confirmation that fails
+                           switches the rest of the solve to 1.  The cold start needs no first
+                           product (G 0 = 0); from a given point an FP64 product forms the
+                           first G beta.  1: an FP64 product recomputes G beta every IPM
+                           iteration.  Carrying applies with krylov = 0 and
+                           refine_every = 0; otherwise G beta is recomputed every iteration */
   double precond_rho;   /* identity scale rho of the preconditioner
                            P = [rho I + Lambda1, Lambda2; Lambda2, Lambda1] (Sec. 3.5).
                            1 (default): the paper's P; 0: rho = n / m with m the number of
@@ -172,9 +175,11 @@ typedef struct {
   double lambda;        /* the lambda actually used                                  */
   double lambda_max;    /* ||M_perp^T b||_inf                                        */
   double seconds;       /* wall time of ipm_solve                                    */
-  int kkt_products;     /* products with M_perp^T M_perp (PCG; the FP64 products that
-                           recomputed G beta; FP64 residual replacements)               */
+  int kkt_products;     /* products with M_perp^T M_perp (PCG; the products that formed
+                           G beta; FP64 residual replacements)                         */
   int refinements;      /* FP64 residual replacements inside PCG (refine_every > 0)  */
+  int exact_products;   /* the FP64 products that formed G beta exactly (none for the
+                           cold start, whose G beta = G 0 = 0)                         */
 } ipm_result;
 
 /* Fill *opt with the defaults listed above. */

@@ -40,7 +40,7 @@ class ipm_result(ctypes.Structure):
                 ("cg_iters_max", ctypes.c_int), ("primal", ctypes.c_double), ("dual", ctypes.c_double),
                 ("rel_gap", ctypes.c_double), ("mu", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("lambda_max", ctypes.c_double), ("seconds", ctypes.c_double), ("kkt_products", ctypes.c_int),
-                ("refinements", ctypes.c_int)]
+                ("refinements", ctypes.c_int), ("exact_products", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1163,6 +1163,7 @@ ipm_status fill_result(sdft_ipm* h, ipm_result* res, double seconds) {
     res->lambda = sc.lambda;
     res->lambda_max = sc.cmax;
     res->kkt_products = sc.cg_total + sc.gb_products + sc.refinements;
+    res->exact_products = sc.gb_products;
     res->seconds = seconds;
     res->refinements = sc.refinements;
   }

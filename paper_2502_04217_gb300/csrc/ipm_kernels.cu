@@ -73,11 +73,13 @@ __global__ void __launch_bounds__(kThreads) cmax_kernel(const double* __restrict
   }
 }
 
-__device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double sigma0, int incr) {
+// incr: G beta carried; exact0: the first residual product is needed (0 when G beta is
+// known exactly at the start, as for the cold start beta = 0).
+__device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double sigma0, int incr, int exact0) {
   sc->incr = incr;
   sc->pc_skip = 0;
   sc->confirming = 0;
-  sc->exact_now = 1;
+  sc->exact_now = exact0;
   sc->gb_products = 0;
   sc->mu = mu;
   sc->sigma = sigma0;
@@ -96,8 +98,8 @@ __device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double 
 
 // Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu; control reset
 __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double* beta, double* z, double* s1, double* s2,
-                                                              double* nu1, double* nu2, double* partials, unsigned* counter,
-                                                              DevScalars* sc, double sigma0, int incr) {
+                                                              double* nu1, double* nu2, double* Gb, double* partials,
+                                                              unsigned* counter, DevScalars* sc, double sigma0, int incr) {
   pdl_wait();
   __shared__ double scratch[32];
   count_launch(sc);
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     const bool gh = is_ghost(lay, i);
     beta[i] = 0.0;
+    Gb[i] = 0.0;                     // G beta of beta = 0, exactly: no first product
     z[i] = gh ? 0.0 : zeta;
     s1[i] = gh ? 0.0 : zeta;
     s2[i] = gh ? 0.0 : zeta;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) init_point_kernel(Layout lay, double
     if (!gh) v[0] += hl * zeta + hl * zeta;
   }
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0)
-    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0, incr);
+    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0, incr, incr ? 0 : 1);
 }
 
 // mu = (nu1^T s1 + nu2^T s2) / 2n at a given point (after ipm_set_point); control reset
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) mu_kernel(Layout lay, IpmVectors w, 
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x)
     if (!is_ghost(lay, i)) v[0] += w.nu1[i] * w.s1[i] + w.nu2[i] * w.s2[i];
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0)
-    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0, incr);
+    reset_control(sc, v[0] / (2.0 * (double)lay.n), sigma0, incr, 1);
 }
 
 // Duality-gap certificate at beta from G beta and c = M_perp^T b, and the IPM stop test:
@@ -149,12 +152,16 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
   count_launch(sc);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   const int ops[4] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
-    const double b = beta[i], g = Gb[i], ci = c[i];
-    v[0] += ci * b;
-    v[1] += b * g;
-    v[2] += fabs(b);
-    v[3] = fmax(v[3], fabs(ci - g));
+  // one half-spectrum slot (two coordinates, 16-byte loads) per step
+  const double2* b2 = reinterpret_cast<const double2*>(beta);
+  const double2* g2 = reinterpret_cast<const double2*>(Gb);
+  const double2* c2 = reinterpret_cast<const double2*>(c);
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < (n2 >> 1); j += (long long)gridDim.x * blockDim.x) {
+    const double2 b = b2[j], g = g2[j], ci = c2[j];
+    v[0] += ci.x * b.x + ci.y * b.y;
+    v[1] += b.x * g.x + b.y * g.y;
+    v[2] += fabs(b.x) + fabs(b.y);
+    v[3] = fmax(v[3], fmax(fabs(ci.x - g.x), fabs(ci.y - g.y)));
   }
   if (grid_reduce<4>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
     const double lam = sc->lambda;
@@ -175,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
     // that fails shows the carried value is not accurate enough at this gap any more:
     // from then on G beta is recomputed by an FP64 product every iteration (incr = 0,
     // exact_now = 1: the residual product runs and the iteration steps as usual).
-    const bool exact = !sc->incr || sc->exact_now;
+    const bool exact = !sc->incr || sc->exact_now;           // an FP64 product formed G beta
     const bool confirm = sc->confirming != 0;
     sc->confirming = 0;
     if (exact) sc->gb_products += 1;
@@ -410,7 +417,10 @@ __global__ void __launch_bounds__(kThreads) precond_kernel(long long n2, const d
 }
 
 // One PCG update after q = K p: x += alpha p, r -= alpha q, z = P^{-1} r, rho' = r^T z,
-// beta_cg = rho'/rho, stop test; the PCG loop condition is !cg_done.
+// beta_cg = rho'/rho, stop test; the PCG loop condition is !cg_done.  One thread step
+// handles one half-spectrum slot (both coordinates, 16-byte loads and stores) of both
+// blocks: the kernel streams about 320 bytes per slot and is bound by HBM, so the
+// loads of a slot are all issued before any is used.
 __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmVectors w, double* partials, unsigned* counter,
                                                               DevScalars* sc, int max_cg, int refine_every, LoopCtl cg_loop) {
   pdl_wait();
@@ -422,22 +432,40 @@ __global__ void __launch_bounds__(kThreads) pcg_update_kernel(long long n2, IpmV
   }
   const double alpha = sc->alpha_cg;
   const bool incr = sc->incr;
+  const long long H = n2 >> 1;                     // slots; the z block starts at slot H
+  double2* x2 = reinterpret_cast<double2*>(w.x);
+  double2* r2 = reinterpret_cast<double2*>(w.r);
+  double2* z2 = reinterpret_cast<double2*>(w.zv);
+  const double2* p2 = reinterpret_cast<const double2*>(w.p);
+  const double2* q2 = reinterpret_cast<const double2*>(w.q);
+  const double2* a2 = reinterpret_cast<const double2*>(w.pa);
+  const double2* b2 = reinterpret_cast<const double2*>(w.pb);
+  const double2* c2 = reinterpret_cast<const double2*>(w.pc);
   double v[1] = {0.0};
   const int ops[1] = {RED_SUM};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
-    const double pbv = w.p[i], pzv = w.p[n2 + i];
-    if (incr) w.Gx[i] += alpha * w.Gp[i];      // (G x)_beta alongside x_beta
-    w.x[i] += alpha * pbv;
-    w.x[n2 + i] += alpha * pzv;
-    const double rb = w.r[i] - alpha * w.q[i];
-    const double rz = w.r[n2 + i] - alpha * w.q[n2 + i];
-    w.r[i] = rb;
-    w.r[n2 + i] = rz;
-    const double a = w.pa[i], b = w.pb[i], c = w.pc[i];
-    const double zb = a * rb - b * rz, zz = -b * rb + c * rz;
-    w.zv[i] = zb;
-    w.zv[n2 + i] = zz;
-    v[0] += rb * zb + rz * zz;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < H; j += (long long)gridDim.x * blockDim.x) {
+    const double2 pb = p2[j], pz = p2[H + j], qb = q2[j], qz = q2[H + j];
+    double2 xb = x2[j], xz = x2[H + j], rb = r2[j], rz = r2[H + j];
+    const double2 a = a2[j], b = b2[j], c = c2[j];
+    if (incr) {                                    // (G x)_beta alongside x_beta
+      double2* gx2 = reinterpret_cast<double2*>(w.Gx);
+      const double2 gp = reinterpret_cast<const double2*>(w.Gp)[j];
+      double2 gx = gx2[j];
+      gx.x = fma(alpha, gp.x, gx.x);
+      gx.y = fma(alpha, gp.y, gx.y);
+      gx2[j] = gx;
+    }
+    xb.x = fma(alpha, pb.x, xb.x); xb.y = fma(alpha, pb.y, xb.y);
+    xz.x = fma(alpha, pz.x, xz.x); xz.y = fma(alpha, pz.y, xz.y);
+    rb.x = fma(-alpha, qb.x, rb.x); rb.y = fma(-alpha, qb.y, rb.y);
+    rz.x = fma(-alpha, qz.x, rz.x); rz.y = fma(-alpha, qz.y, rz.y);
+    double2 zb, zz;
+    zb.x = a.x * rb.x - b.x * rz.x; zb.y = a.y * rb.y - b.y * rz.y;
+    zz.x = -b.x * rb.x + c.x * rz.x; zz.y = -b.y * rb.y + c.y * rz.y;
+    x2[j] = xb; x2[H + j] = xz;
+    r2[j] = rb; r2[H + j] = rz;
+    z2[j] = zb; z2[H + j] = zz;
+    v[0] += (rb.x * zb.x + rz.x * zz.x) + (rb.y * zb.y + rz.y * zz.y);
   }
   if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
     const double rho_new = v[0];
@@ -701,7 +729,11 @@ __device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long 
   return d;
 }
 
-// Largest step keeping (s, nu) >= 0; alpha = min(1, tau * alpha_max)
+// Largest step keeping (s, nu) >= 0; alpha = min(1, tau * alpha_max).  With the
+// predictor-corrector (pc) the direction is also left for step_update_kernel in the
+// predictor's scratch vectors, which prepare_kernel has consumed: ds1, ds2 over the
+// second-order terms (ds1a, ds2a; each thread reads its own term before writing),
+// dnu1, dnu2 over the affine right-hand side (rba, rca).
 __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                                DevScalars* sc, double tau, int pc) {
   pdl_wait();
@@ -717,13 +749,39 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
   auto consider = [&](double wv, double dw) {
     if (__double_as_longlong(dw) < 0) best = fminf(best, d2f_int(wv) / d2f_int(-dw));
   };
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
-    if (is_ghost(lay, i)) continue;
-    const Dir d = direction(w, i, n2, smu, pc);
-    consider(w.s1[i], d.ds1);
-    consider(w.s2[i], d.ds2);
-    consider(w.nu1[i], d.dn1);
-    consider(w.nu2[i], d.dn2);
+  // one half-spectrum slot (two coordinates, 16-byte loads) per step
+  const long long H = lay.H;
+  auto ld = [&](const double* v, long long j) { return reinterpret_cast<const double2*>(v)[j]; };
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < H; j += (long long)gridDim.x * blockDim.x) {
+    const double2 b = ld(w.beta, j), z = ld(w.z, j), s1 = ld(w.s1, j), s2 = ld(w.s2, j), n1 = ld(w.nu1, j),
+                  n2_ = ld(w.nu2, j), db = ld(w.x, j), dz = ld(w.x, H + j), is1 = ld(w.is1, j), is2 = ld(w.is2, j);
+    double2 c1 = make_double2(0.0, 0.0), c2 = c1;
+    if (pc) { c1 = ld(w.ds1a, j); c2 = ld(w.ds2a, j); }
+    double2 o1, o2, o3, o4;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      auto g = [&](const double2& v) { return k ? v.y : v.x; };
+      const double ds1 = g(dz) + g(db) + (g(z) + g(b) - g(s1));
+      const double ds2 = g(dz) - g(db) + (g(z) - g(b) - g(s2));
+      const double dn1 = -fma(g(c1) - smu, g(is1), g(n1)) - (g(n1) * g(is1)) * ds1;
+      const double dn2 = -fma(g(c2) - smu, g(is2), g(n2_)) - (g(n2_) * g(is2)) * ds2;
+      if (!is_ghost(lay, 2 * j + k)) {
+        consider(g(s1), ds1);
+        consider(g(s2), ds2);
+        consider(g(n1), dn1);
+        consider(g(n2_), dn2);
+      }
+      (k ? o1.y : o1.x) = ds1;
+      (k ? o2.y : o2.x) = ds2;
+      (k ? o3.y : o3.x) = dn1;
+      (k ? o4.y : o4.x) = dn2;
+    }
+    if (pc) {       // ghost coordinates hold 0 in every operand, so their direction is 0 too
+      reinterpret_cast<double2*>(w.ds1a)[j] = o1;
+      reinterpret_cast<double2*>(w.ds2a)[j] = o2;
+      reinterpret_cast<double2*>(w.rba)[j] = o3;
+      reinterpret_cast<double2*>(w.rca)[j] = o4;
+    }
   }
   double v[1] = {(double)best};
   const int ops[1] = {RED_MIN};
@@ -745,7 +803,15 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
   const int ops[1] = {RED_SUM};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i)) continue;
-    const Dir d = direction(w, i, n2, smu, sigma_rule == 2);
+    Dir d;
+    if (sigma_rule == 2) {               // the direction step_length_kernel left
+      d.ds1 = w.ds1a[i];
+      d.ds2 = w.ds2a[i];
+      d.dn1 = w.rba[i];
+      d.dn2 = w.rca[i];
+    } else {
+      d = direction(w, i, n2, smu, 0);
+    }
     w.beta[i] += alpha * w.x[i];
     if (incr) w.Gb[i] += alpha * w.Gx[i];        // G beta follows beta (G is linear)
     w.z[i] += alpha * w.x[n2 + i];
@@ -869,7 +935,7 @@ cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Redu
 }
 cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr,
                          cudaStream_t st) {
-  return launch_k(init_point_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, red.partials, red.counter, sc, sigma0, incr);
+  return launch_k(init_point_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, w.Gb, red.partials, red.counter, sc, sigma0, incr);
 }
 cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr, cudaStream_t st) {
   return launch_k(mu_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, sigma0, incr);

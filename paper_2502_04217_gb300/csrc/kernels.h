@@ -21,9 +21,11 @@ struct IpmVectors {
   double *Gp, *Gx;                            // incremental G beta: (G p)_beta of the last PCG product and
                                               // (G x)_beta = sum alpha (G p)_beta over the PCG solve (2H each)
   double *ds1a, *ds2a;                        // predictor-corrector: the second-order terms ds1 o dnu1,
-                                              // ds2 o dnu2 of the affine predictor (2H each)
+                                              // ds2 o dnu2 of the affine predictor (2H each); after
+                                              // step_length the direction's ds1, ds2
   double *rba, *rca;                          // predictor-corrector: the condensed right-hand side of the
-                                              // affine system (sigma = 0, no second-order term; 2H each)
+                                              // affine system (sigma = 0, no second-order term; 2H each);
+                                              // after step_length the direction's dnu1, dnu2
 };
 
 // grid size used by every elementwise kernel (also sizes the partials buffer)

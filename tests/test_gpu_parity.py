@@ -906,3 +906,36 @@ def test_predictor_corrector_mixed_and_graph(dims):
     assert rg["status"] == binding.IPM_OK and rg["rel_gap"] <= 1e-8
     assert abs(rg["primal"] - r64["primal"]) <= 1e-7 * abs(r64["primal"])
     assert np.array_equal(vg, vh) and rg["cg_iters_total"] == rh["cg_iters_total"]
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+def test_carried_g_beta_from_a_given_point(precision):
+    """A solve from a given point (ipm_set_point) starts its carried G beta with an FP64
+    product and confirms its stop with another; a cold start needs no starting product
+    (G 0 = 0).  Both reach the gap, certified by the oracle.  (An FP32 starting product
+    was measured and dropped: on the 512^3 warm start its rounding cost an IPM
+    iteration.)"""
+    w = _workload((48, 40), seed=73)
+    prob = _oracle_rel(w, 0.1)
+    h = _handle(w, precision, prob=prob, gap_tol=1e-3)
+    try:
+        cold = binding.ipm_solve(h)
+        # a cold solve: every product is a PCG product or an exact confirmation
+        assert cold["kkt_products"] == cold["cg_iters_total"] + cold["exact_products"]
+        H, n = binding.ipm_sizes(h)
+        pt = [torch.empty(2 * H, dtype=torch.float64, device="cuda") for _ in range(6)]
+        binding.ipm_get_point(h, pt)
+        o = binding.default_options(precision=precision, lambda_relative=0, gap_tol=1e-9)
+        binding.ipm_set_options(h, o)
+        binding.ipm_set_point(h, pt)
+        res = binding.ipm_solve(h)
+        v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+        binding.ipm_get_spectrum(h, v)
+        v = v.cpu().numpy()
+    finally:
+        binding.ipm_destroy(h)
+    assert res["status"] == binding.IPM_OK and res["rel_gap"] <= 1e-9
+    assert res["exact_products"] >= 2
+    assert res["kkt_products"] == res["cg_iters_total"] + res["exact_products"]
+    P, D, gap = prob.certificate(half_to_beta(v, w.dims))
+    assert gap <= 1.5e-9 and abs(P - res["primal"]) <= 1e-10 * abs(P)
