@@ -77,6 +77,7 @@ def _args():
     ap.add_argument("--sigma-min", type=float, default=None, help="library option sigma_min (default: the library's)")
     ap.add_argument("--exact-residual", type=int, default=None,
                     help="library option exact_residual (default: the library's)")
+    ap.add_argument("--cg-tol", type=float, default=None, help="library option cg_tol (default: the library's)")
     ap.add_argument("--workload", choices=["1d", "2d", "3d", "batch", "warm512", "infer256", "conv256", "kkt256", "paper"],
                     default="warm512",
                     help="warm512 (default): 512^3, learned warm start + mixed precision against the cold FP64 "
@@ -1229,6 +1230,8 @@ def main():
         _OPT_OVERRIDES["sigma_min"] = args.sigma_min
     if args.exact_residual is not None:
         _OPT_OVERRIDES["exact_residual"] = args.exact_residual
+    if args.cg_tol is not None:
+        _OPT_OVERRIDES["cg_tol"] = args.cg_tol
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

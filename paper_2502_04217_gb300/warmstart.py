@@ -21,9 +21,10 @@ from .synth import lattice_mask, make_problem
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart.f32")
-# mu0 = MU_SCALE lambda^2 of the predicted start point: of {0.3, 0.5, 0.7, 1, 1.5, 2}
-# the value with the fewest IPM iterations on held-out 512^3 instances (8 vs 9-11
-# for the others and the cold start); 0.3 does as well on 256^3.
+# mu0 = MU_SCALE lambda^2 of the predicted start point.  Under the predictor-corrector
+# rule, of {0.05, 0.1, 0.2, 0.3, 0.5, 0.8, 1.2} on two held-out 512^3 instances (3 and
+# 5 of the 512^3 workload, mixed precision, 1e-6 gap), 0.3 and 0.5 take 5 IPM
+# iterations and every other value 6 (the cold start 8 and 9).
 MU_SCALE = 0.5
 
 # (stored cin, stored cout, real cin, real cout) of the four convolutions
