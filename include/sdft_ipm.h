@@ -78,7 +78,11 @@ typedef enum { IPM_FP64 = 0, IPM_MIXED = 1 } ipm_precision;
 typedef struct {
   int precision;        /* ipm_precision; IPM_FP64 is the plain method                       */
   double gap_tol;       /* stop when (P - D) / max(1, |P|) <= gap_tol (default 1e-6)          */
-  double cg_tol;        /* PCG tolerance on sqrt(r^T P^{-1} r) (default 1e-10)                 */
+  double cg_tol;        /* PCG tolerance on sqrt(r^T P^{-1} r) (default 1e-6: an inexact Newton
+                           direction; measured, the same IPM iterations and certified gaps as
+                           1e-10 from gap_tol 1e-6 down to 1e-10 with 40-45 % fewer PCG
+                           iterations; at gap_tol 1e-12 it may cost one or two more IPM
+                           iterations, where 1e-10 suits better)                             */
   int cg_relative;      /* 1: relative to the initial residual (default); 0: absolute,
                            as the paper's 1e-12 rule (Sec. 5)                                  */
   int max_ipm;          /* IPM iteration cap (default 200)                                     */
@@ -161,6 +165,18 @@ typedef struct {
                            count in kkt_products).  With 1 or 2, G beta is recomputed every
                            iteration and refine_every must be 0.  Changing the method with
                            ipm_set_options allocates its vectors (4 x 4H doubles at most). */
+  int tile_kstage;      /* (fixed at ipm_create, like the tile shape) how the last FFT pass of
+                           a product with K (2D and 3D grids) brings
+                           the FP64 operands of its epilogue (p on both blocks, Lambda1,
+                           Lambda2: 64 bytes per slot).  0 (default): with autotune, the
+                           fastest of the three forms below for the tuned tile, else 1;
+                           1: per-slot loads after the tile's transform; 2: one L2 bulk
+                           prefetch (cp.async.bulk.prefetch) of the tile's operands when the
+                           block starts; 3: bulk copies (cp.async.bulk) of them into shared
+                           memory when the block starts, completing on an mbarrier that the
+                           epilogue waits on (bounded: IPM_TIMEOUT).  2 and 3 apply to the
+                           shared-memory engine and where the stage fits a block's shared
+                           memory, else 1 is used                                             */
 } ipm_options;
 
 typedef struct {
@@ -216,14 +232,24 @@ ipm_status ipm_solve(sdft_ipm* h, ipm_result* res);
 ipm_status ipm_sizes(const sdft_ipm* h, int64_t* nslots, int64_t* n);
 
 /* q = M_perp^T M_perp p for a beta-layout vector (Sec. 3.1); device pointers,
- * 2H doubles each; p's ghost coordinates must be 0, q's are written as 0. */
+ * 2H doubles each, 16-byte aligned; p's ghost coordinates must be 0, q's are
+ * written as 0. */
 ipm_status gapply(sdft_ipm* h, const double* p, double* q);
 
 /* q = K p with K = [G + Lambda1, Lambda2; Lambda2, Lambda1] (Eq. (condensedkkt)),
  * G = M_perp^T M_perp, Lambda1 = Sigma1 + Sigma2, Lambda2 = Sigma1 - Sigma2
  * for the Sigma set by ipm_set_sigma (or the last IPM iterate).  Device
- * pointers, 4H doubles each ([beta block | z block]). */
+ * pointers, 4H doubles each ([beta block | z block]), 16-byte aligned. */
 ipm_status kkt_apply(sdft_ipm* h, const double* p, double* q);
+
+/* Failure-detection test of the staged K epilogue (not for production use): the
+ * NEXT kkt_apply on h leaves out, in every block of its last pass, the fourth of
+ * the four operand copies that its mbarrier expects, and every wait on that
+ * barrier gives up after 2^wait_log2 polls (8..24).  That call must return
+ * IPM_TIMEOUT without hanging (q is then incomplete) and the handle stays usable.
+ * IPM_ERR_ARG for an out-of-range wait_log2 or when the last pass of h's product
+ * does not stage its operands in shared memory (tile_kstage = 3 forces that). */
+ipm_status ipm_test_stage_stall(sdft_ipm* h, int wait_log2);
 
 /* z = P^{-1} r by the closed form Eq. (invprecond1) with D = Sigma1 + Sigma2 +
  * 4 Sigma1 Sigma2 (Prop. exprbd).  Device pointers, 4H doubles each. */

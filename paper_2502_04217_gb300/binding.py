@@ -32,7 +32,7 @@ class ipm_options(ctypes.Structure):
                 ("refine_every", ctypes.c_int), ("tile_engine", ctypes.c_int),
                 ("sigma_rule", ctypes.c_int), ("sigma_min", ctypes.c_double), ("exact_residual", ctypes.c_int),
                 ("precond_rho", ctypes.c_double), ("pdl", ctypes.c_int),
-                ("krylov", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("tile_kstage", ctypes.c_int)]
 
 
 class ipm_result(ctypes.Structure):
@@ -63,6 +63,7 @@ _SIGNATURES = {
     "ipm_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "gapply": (ctypes.c_int, [_P, _P, _P]),
     "kkt_apply": (ctypes.c_int, [_P, _P, _P]),
+    "ipm_test_stage_stall": (ctypes.c_int, [_P, ctypes.c_int]),
     "precond_apply": (ctypes.c_int, [_P, _P, _P]),
     "ipm_set_sigma": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "ipm_set_point": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
@@ -197,6 +198,11 @@ def gapply(h, p, q):
 
 def kkt_apply(h, p, q):
     return _check(load().kkt_apply(h, addr(p), addr(q)), h)
+
+
+def ipm_test_stage_stall(h, wait_log2):
+    """Failure-detection test hook: the next kkt_apply on h drops one staged operand copy."""
+    return _check(load().ipm_test_stage_stall(h, int(wait_log2)), h)
 
 
 def precond_apply(h, r, z):

@@ -3,6 +3,7 @@
 // (Sec. 3.3-3.5): every arithmetic step runs in the kernels of
 // fft_passes.cu and ipm_kernels.cu; the host only queues launches and reads
 // the device scalars where it has to decide (IPM stop, PCG chunk boundaries).
+#include <algorithm>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -47,6 +48,9 @@ struct PassCfg {
   const void* tw = nullptr;
   const void* twN = nullptr;
   int reg = 0;              // 1: register engine (fft_reg.cuh)
+  int kstage = 0;           // forward row pass: staging of the K epilogue's operands (PassArgs::kstage)
+  unsigned kst_off = 0;     // kstage 2: byte offset of the staged operands in shared memory
+  size_t smem_staged = 0;   // shared memory of a launch with kstage 2
 };
 
 struct PassSet {
@@ -104,6 +108,7 @@ struct sdft_ipm {
   Layout lay{};
   int dims[3] = {0, 0, 0};
   std::string err;
+  int stall_log2 = 0;               // ipm_test_stage_stall: the next kkt_apply drops a staged copy
   double lambda_in = 0.0;
   // device memory
   std::vector<void*> allocs;
@@ -273,6 +278,25 @@ bool make_cfg_reg(PassCfg& c, int kind, int L, long long npen, bool fp32, int P)
   return true;
 }
 
+// Staging of the K epilogue's FP64 operands in a forward row pass of the shared-memory
+// engine (kstage 1: L2 prefetch; 2: shared memory, 64 bytes per slot of the tile after the
+// transform's rows, 128-byte aligned).  False when the stage does not fit in the 227 KB
+// a block can have.
+bool stage_cfg(PassCfg& c, int kstage) {
+  c.kstage = 0;
+  c.kst_off = 0;
+  c.smem_staged = c.smem;
+  if (kstage == 0) return true;
+  if (c.reg) return false;
+  c.kstage = kstage;
+  if (kstage == 2) {
+    c.kst_off = (unsigned)((c.smem + 127) & ~(size_t)127);
+    c.smem_staged = c.kst_off + (size_t)64 * ((size_t)1 << c.lgP) * (size_t)c.plan.L;
+    if (c.smem_staged > 227 * 1024) return false;
+  }
+  return true;
+}
+
 // Default choice without timing: E = 8 (12 with a factor 3), P as large as keeps
 // two tiles per SM, at least 2 (FP64) or 4 (FP32); failing that, the first
 // launchable (E, P).  Returns false when no shape fits the pass.
@@ -350,6 +374,7 @@ struct TuneKey {
 std::mutex g_tune_mu;
 struct TuneVal {
   int E, P, reg;
+  int kstage;
 };
 std::map<TuneKey, TuneVal> g_tuned;
 
@@ -357,8 +382,8 @@ std::map<TuneKey, TuneVal> g_tuned;
 // SDFT_TUNE_CACHE names a file, tuned shapes are read from it (first use) and
 // every new choice is appended, so that a later process (for instance one run
 // under a profiler, whose launch timings are perturbed) launches the same tiles.
-// One line per shape: engine kind L rows fp32 npen E P reg.  Lines that do not
-// parse are ignored.  Called with g_tune_mu held.
+// One line per shape: engine kind L rows fp32 npen E P reg kstage.  Lines that do
+// not parse are ignored.  Called with g_tune_mu held.
 const char* tune_cache_path() {
   const char* p = std::getenv("SDFT_TUNE_CACHE");
   return (p && *p) ? p : nullptr;
@@ -371,11 +396,14 @@ void tune_cache_load() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  TuneKey k{};
-  TuneVal v{};
-  while (std::fscanf(f, "%d %d %d %d %d %lld %d %d %d", &k.engine, &k.kind, &k.L, &k.rows, &k.fp32, &k.npen, &v.E, &v.P,
-                     &v.reg) == 9)
-    g_tuned[k] = v;
+  char line[256];
+  while (std::fgets(line, sizeof(line), f)) {
+    TuneKey k{};
+    TuneVal v{};
+    if (std::sscanf(line, "%d %d %d %d %d %lld %d %d %d %d", &k.engine, &k.kind, &k.L, &k.rows, &k.fp32, &k.npen, &v.E,
+                    &v.P, &v.reg, &v.kstage) == 10)
+      g_tuned[k] = v;
+  }
   std::fclose(f);
 }
 void tune_cache_append(const TuneKey& k, const TuneVal& v) {
@@ -383,15 +411,16 @@ void tune_cache_append(const TuneKey& k, const TuneVal& v) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d %d %lld %d %d %d\n", k.engine, k.kind, k.L, k.rows, k.fp32, k.npen, v.E, v.P, v.reg);
+  std::fprintf(f, "%d %d %d %d %d %lld %d %d %d %d\n", k.engine, k.kind, k.L, k.rows, k.fp32, k.npen, v.E, v.P, v.reg,
+               v.kstage);
   std::fclose(f);
 }
 
 // `last`: for a row pass, tune the forward (last) pass of a product instead of the
 // inverse (first) one.  Row passes are timed in the form the PCG loop runs them
-// (first: p = z + beta p and the beta map; last: the K epilogue), on operands
-// filled with a non-zero pattern by the caller; column and middle passes on the
-// work buffer alone.
+// (first: p = z + beta p and the beta map; last: the K epilogue with the p^T q
+// reduction and the (G p)_beta store), on operands filled with a non-zero pattern by
+// the caller; column and middle passes on the work buffer alone.
 ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long long npen, bool fp32,
                      bool last = false, bool beta_form = false) {
   c.kind = kind;
@@ -432,6 +461,7 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
     if (it != g_tuned.end()) {
       if (it->second.reg) make_cfg_reg(c, kind, L, npen, fp32, it->second.P);
       else make_cfg(c, L, rows, npen, fp32, it->second.E, it->second.P);
+      if (!stage_cfg(c, it->second.kstage)) stage_cfg(c, 0);
       c.grid = pass_grid(h->lay, kind, npen, c.lgP);
       return IPM_OK;
     }
@@ -441,74 +471,102 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  PassCfg best_c = c;
-  // candidates: the shared-memory engine at every (E, P), the register engine at every P
-  std::vector<std::pair<int, int>> cands;     // (E, P); E = 0 marks the register engine
+  // candidates: the shared-memory engine at every (E, P), the register engine at every P;
+  // the forward row pass (K epilogue) also with the L2 prefetch of its operands (the
+  // shared-memory stage, 64 bytes per slot, lowers the blocks per SM and measured 11-30 %
+  // slower on this pass: it runs only when tile_kstage forces it)
+  struct Cand {
+    int E, P, kstage;     // E = 0 marks the register engine
+  };
+  std::vector<Cand> cands;
+  const int nstage = (kind == 0 && last) ? 2 : 1;
   if (h->opt.tile_engine != 2)
     for (int E : Es)
       if (E != 0)
-        for (int P = 1; P <= 32; P *= 2) cands.push_back({E, P});
+        for (int P = 1; P <= 32; P *= 2)
+          for (int ks = 0; ks < nstage; ++ks) cands.push_back({E, P, ks});
   if (h->opt.tile_engine != 1)
-    for (int P = 1; P <= 32; P *= 2) cands.push_back({0, P});
-  for (const auto& cand : cands) {
-    const int E = cand.first, P = cand.second;
-    {
-      PassCfg t = c;
-      if (E == 0 ? !make_cfg_reg(t, kind, L, npen, fp32, P) : !make_cfg(t, L, rows, npen, fp32, E, P)) continue;
-      t.grid = pass_grid(h->lay, kind, npen, t.lgP);
-      PassArgs a{};
-      a.lay = h->lay;
-      a.plan = t.plan;
-      a.lgP = t.lgP;
-      a.PP = t.PP;
-      a.nwork = t.nwork;
-      a.npencils = npen;
-      a.tw = t.tw;
-      a.twN = t.twN;
-      a.buf = h->d_U;
-      a.maskw = h->d_maskw;
-      a.inv_n = 1.0 / (double)h->lay.n;
-      a.out_scale = 1.0;
-      a.sc = h->d_sc;
-      a.reg = t.reg;
-      const bool inv = (kind == 0 && last) ? false : (kind != 2);
-      if (kind == 0 && !last && beta_form) {
-        a.mapin = MAPIN_BETA;
-        a.src = h->w.p;
-      } else if (kind == 0 && !last) {
-        a.mapin = MAPIN_PCG;
-        a.p = h->w.p;
-        a.zv = h->w.zv;
-      } else if (kind == 0) {
-        a.mapout = MAPOUT_K;
-        a.p = h->w.p;
-        a.q = h->w.q;
-        a.lam1 = h->w.lam1;
-        a.lam2 = h->w.lam2;
-      }
-      auto once = [&]() -> cudaError_t { return launch_pass(kind, inv, fp32, t.E, a, t.threads, t.smem, t.grid, h->st); };
-      CK(once());     // warm-up
-      // best of three rounds of five launches (one round alone was noisy enough to
-      // flip close choices between processes)
-      float ms = 1e30f;
-      for (int round = 0; round < 3; ++round) {
-        CK(cudaEventRecord(e0, h->st));
-        for (int r = 0; r < 5; ++r) CK(once());
-        CK(cudaEventRecord(e1, h->st));
-        CK(cudaEventSynchronize(e1));
-        float m = 0.f;
-        CK(cudaEventElapsedTime(&m, e0, e1));
-        if (m < ms) ms = m;
-      }
-      if (ms < best) { best = ms; best_c = t; }
+    for (int P = 1; P <= 32; P *= 2) cands.push_back({0, P, 0});
+  struct Trial {
+    PassCfg t;
+    PassArgs a;
+    size_t smem;
+    bool inv;
+    float ms;
+  };
+  std::vector<Trial> trials;
+  for (const Cand& cand : cands) {
+    const int E = cand.E, P = cand.P;
+    PassCfg t = c;
+    if (E == 0 ? !make_cfg_reg(t, kind, L, npen, fp32, P) : !make_cfg(t, L, rows, npen, fp32, E, P)) continue;
+    if (!stage_cfg(t, cand.kstage)) continue;
+    t.grid = pass_grid(h->lay, kind, npen, t.lgP);
+    PassArgs a{};
+    a.lay = h->lay;
+    a.plan = t.plan;
+    a.lgP = t.lgP;
+    a.PP = t.PP;
+    a.nwork = t.nwork;
+    a.npencils = npen;
+    a.tw = t.tw;
+    a.twN = t.twN;
+    a.buf = h->d_U;
+    a.maskw = h->d_maskw;
+    a.inv_n = 1.0 / (double)h->lay.n;
+    a.out_scale = 1.0;
+    a.sc = h->d_sc;
+    a.reg = t.reg;
+    const bool inv = (kind == 0 && last) ? false : (kind != 2);
+    if (kind == 0 && !last && beta_form) {
+      a.mapin = MAPIN_BETA;
+      a.src = h->w.p;
+    } else if (kind == 0 && !last) {
+      a.mapin = MAPIN_PCG;
+      a.p = h->w.p;
+      a.zv = h->w.zv;
+    } else if (kind == 0) {
+      a.mapout = MAPOUT_K;
+      a.p = h->w.p;
+      a.q = h->w.q;
+      a.lam1 = h->w.lam1;
+      a.lam2 = h->w.lam2;
+      a.kstage = t.kstage;
+      a.kst_off = t.kst_off;
+      // the form PCG runs: with the p^T q grid reduction and, when G beta is carried, (G p)_beta
+      a.pcg_mode = 1;
+      a.partials = h->d_partials;
+      a.counter = h->d_counter;
+      a.gp_out = incremental_gb(h) ? h->w.Gp : nullptr;
+    }
+    trials.push_back({t, a, a.kstage == 2 ? t.smem_staged : t.smem, inv, 1e30f});
+  }
+  auto once = [&](const Trial& tr) -> cudaError_t {
+    return launch_pass(kind, tr.inv, fp32, tr.t.E, tr.a, tr.t.threads, tr.smem, tr.t.grid, h->st);
+  };
+  for (const Trial& tr : trials) CK(once(tr));     // warm-up
+  // three rounds over all candidates, five launches each, best round per candidate:
+  // candidates interleaved in time, so that a drift of the clocks or of the memory
+  // state during tuning does not favour the ones timed first
+  for (int round = 0; round < 3; ++round) {
+    for (Trial& tr : trials) {
+      CK(cudaEventRecord(e0, h->st));
+      for (int r = 0; r < 5; ++r) CK(once(tr));
+      CK(cudaEventRecord(e1, h->st));
+      CK(cudaEventSynchronize(e1));
+      float m = 0.f;
+      CK(cudaEventElapsedTime(&m, e0, e1));
+      if (m < tr.ms) tr.ms = m;
     }
   }
+  float best = 1e30f;
+  PassCfg best_c = c;
+  for (const Trial& tr : trials)
+    if (tr.ms < best) { best = tr.ms; best_c = tr.t; }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c = best_c;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[key] = {c.E, 1 << c.lgP, c.reg};
+  g_tuned[key] = {c.E, 1 << c.lgP, c.reg, c.kstage};
   tune_cache_append(key, g_tuned[key]);
   return IPM_OK;
 }
@@ -543,6 +601,13 @@ ipm_status plan_passes(sdft_ipm* h, PassSet& ps, bool fp32) {
     PassCfg f = c, b = c;
     if ((s = tune_tile(h, c, 0, Lr, Lr, nrows, fp32)) != IPM_OK) return s;
     if ((s = tune_tile(h, f, 0, Lr, Lr, nrows, fp32, true)) != IPM_OK) return s;
+    if (h->opt.tile_kstage > 0) {
+      PassCfg t = f;
+      if (stage_cfg(t, h->opt.tile_kstage - 1)) f = t;
+      else stage_cfg(f, 0);
+    } else if (!h->opt.autotune) {
+      stage_cfg(f, 0);
+    }
     if ((s = tune_tile(h, b, 0, Lr, Lr, nrows, fp32, false, true)) != IPM_OK) return s;
     ps.row_inv = c;
     ps.row_fwd = f;
@@ -581,9 +646,23 @@ PassArgs base_args(sdft_ipm* h, const PassCfg& c) {
   return a;
 }
 
-ipm_status launch(sdft_ipm* h, const PassCfg& c, bool inv, bool fp32, const PassArgs& a) {
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// A forward row pass with the K epilogue runs with its tuned operand staging (the
+// operand pointers are 16-byte aligned on every path; checked all the same, since the
+// bulk copies require it); every other launch of the same tile without.
+ipm_status launch(sdft_ipm* h, const PassCfg& c, bool inv, bool fp32, PassArgs a) {
   ProfScope ps(h, c.kind);
-  CK(launch_pass(c.kind, inv, fp32, c.E, a, c.threads, c.smem, c.grid, h->st));
+  size_t smem = c.smem;
+  a.kstage = 0;
+  a.kst_off = 0;
+  if (c.kstage && c.kind == 0 && !inv && a.mapout == MAPOUT_K && aligned16(a.p) && aligned16(a.lam1) &&
+      aligned16(a.lam2)) {
+    a.kstage = c.kstage;
+    a.kst_off = c.kst_off;
+    if (c.kstage == 2) smem = c.smem_staged;
+  }
+  CK(launch_pass(c.kind, inv, fp32, c.E, a, c.threads, smem, c.grid, h->st));
   return IPM_OK;
 }
 
@@ -602,6 +681,7 @@ struct GSpec {
   double* cr_out = nullptr;
   const double* p_in = nullptr;  // kkt_apply: p and q given by the caller
   double* q_out = nullptr;
+  int stall_log2 = 0;            // failure-detection test of the staged K epilogue (ipm_test_stage_stall)
 };
 
 // One application of G = A^T diag(m) A (with the chosen prologue/epilogue).
@@ -640,6 +720,7 @@ ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
     a.check_refine = g.refine ? 1 : 0;
     a.check_exact = g.exact ? 1 : 0;
     if (last) a.gp_out = (g.pcg && incremental_gb(h)) ? h->w.Gp : nullptr;
+    if (last) a.kst_wait_log2 = g.stall_log2;
   };
   ipm_status s;
   if (L.d == 1) {
@@ -751,6 +832,7 @@ ipm_status check_options(sdft_ipm* h, const ipm_options& o) {
   if (!(o.precond_rho >= 0.0) || !std::isfinite(o.precond_rho)) return fail_arg(h, "precond_rho must be >= 0 and finite");
   if (o.pdl < 0 || o.pdl > 1) return fail_arg(h, "pdl must be 0 or 1");
   if (o.krylov < 0 || o.krylov > 2) return fail_arg(h, "krylov must be 0 (CG), 1 (CR) or 2 (CAr)");
+  if (o.tile_kstage < 0 || o.tile_kstage > 3) return fail_arg(h, "tile_kstage must be 0 (tuned), 1, 2 or 3");
   if (o.krylov >= 1 && o.refine_every > 0) return fail_arg(h, "krylov = 1 (CR) or 2 (CAr) does not combine with refine_every");
   if (o.sigma_rule == 1 && !(o.sigma_min > 0 && o.sigma_min <= o.sigma_slow))
     return fail_arg(h, "sigma_min must lie in (0, sigma_slow]");
@@ -769,7 +851,7 @@ void ipm_default_options(ipm_options* o) {
   if (!o) return;
   o->precision = IPM_FP64;
   o->gap_tol = 1e-6;
-  o->cg_tol = 1e-10;
+  o->cg_tol = 1e-6;
   o->cg_relative = 1;
   o->max_ipm = 200;
   o->max_cg = 500;
@@ -790,6 +872,7 @@ void ipm_default_options(ipm_options* o) {
   o->precond_rho = 1.0;
   o->pdl = 1;
   o->krylov = 0;
+  o->tile_kstage = 0;
 }
 
 ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8_t* mask, const double* y, double lambda,
@@ -865,20 +948,21 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   // non-zero values (every byte 0x3F) until the vectors are cleared below
   for (double* p : {h->w.p, h->w.zv, h->w.lam1, h->w.lam2})
     CKC(cudaMemsetAsync(p, 0x3F, (p == h->w.lam1 || p == h->w.lam2) ? v2 : v4, h->st));
-  if ((s = plan_passes(h, h->pass64, false)) != IPM_OK) return cleanup_fail(s);
-  if ((s = plan_passes(h, h->pass32, true)) != IPM_OK) return cleanup_fail(s);
-  // partials: 4 values per elementwise block, 1 per FFT block
+  // partials of the grid reductions: 4 values per elementwise block, 1 per block of an FFT
+  // pass that reduces (the last pass of a PCG product, p^T q), whose tiles hold at least
+  // one pencil: allocated before the tuner, which times that pass with its reduction
   size_t cap = 4 * (size_t)kMaxElementwiseBlocks;
-  for (const PassSet* ps : {&h->pass64, &h->pass32}) {
-    for (const PassCfg* c : {&ps->row_fwd, &ps->mid}) {
-      const size_t nb = (size_t)c->grid.x * c->grid.y * c->grid.z;
-      if (nb > cap) cap = nb;
-    }
-  }
+  if (L.d >= 2) cap = std::max(cap, (size_t)(L.H / ((L.d == 3) ? L.N1 : L.N0)));
+  cap = std::max(cap, (size_t)L.M);
   h->partial_cap = cap;
   CKC(dalloc(h, &h->d_partials, cap * sizeof(double)));
   CKC(dalloc(h, &h->d_counter, 64 * sizeof(unsigned)));
   CKC(cudaMemsetAsync(h->d_counter, 0, 64 * sizeof(unsigned), h->st));
+  if ((s = plan_passes(h, h->pass64, false)) != IPM_OK) return cleanup_fail(s);
+  if ((s = plan_passes(h, h->pass32, true)) != IPM_OK) return cleanup_fail(s);
+  for (const PassSet* ps : {&h->pass64, &h->pass32})
+    for (const PassCfg* c : {&ps->row_fwd, &ps->mid})
+      if ((size_t)c->grid.x * c->grid.y * c->grid.z > cap) return cleanup_fail(fail_arg(h, "reduction partials too small"));
   // vectors start at 0 (ghosts stay 0 from here on)
   for (double** p : vec2) CKC(cudaMemsetAsync(*p, 0, v2, h->st));
   for (double** p : vec4) CKC(cudaMemsetAsync(*p, 0, v4, h->st));
@@ -1151,6 +1235,7 @@ ipm_status fill_result(sdft_ipm* h, ipm_result* res, double seconds) {
   const DevScalars& sc = *h->h_sc;
   ipm_status final_status = sc.ipm_status == 0 ? IPM_OK : (sc.ipm_status == 4 ? IPM_MAXITER : IPM_NUMERICAL);
   if (final_status == IPM_OK && sc.cg_cap_hit) final_status = IPM_KRYLOV_MAXITER;
+  if (sc.wait_expired) final_status = IPM_TIMEOUT;
   if (res) {
     res->status = final_status;
     res->ipm_iters = sc.ipm_it;
@@ -1169,6 +1254,7 @@ ipm_status fill_result(sdft_ipm* h, ipm_result* res, double seconds) {
   }
   if (final_status == IPM_NUMERICAL) h->err = "non-finite value or breakdown of positive definiteness";
   if (final_status == IPM_MAXITER) h->err = "IPM iteration cap reached before gap_tol";
+  if (final_status == IPM_TIMEOUT) h->err = "a bounded device-side wait expired (staged K operands)";
   return final_status;
 }
 
@@ -1218,6 +1304,7 @@ ipm_status ipm_solve(sdft_ipm* h, ipm_result* res) {
 
 ipm_status gapply(sdft_ipm* h, const double* p, double* q) {
   if (!h || !p || !q) return fail_arg(h, "NULL argument");
+  if (!aligned16(p) || !aligned16(q)) return fail_arg(h, "p and q must be 16-byte aligned");
   GSpec g;
   g.src = p;
   g.dst = q;
@@ -1232,17 +1319,39 @@ ipm_status gapply(sdft_ipm* h, const double* p, double* q) {
 ipm_status kkt_apply(sdft_ipm* h, const double* p, double* q) {
   if (!h || !p || !q) return fail_arg(h, "NULL argument");
   if (!h->sigma_ready) return fail_arg(h, "Sigma is not set: call ipm_set_sigma or ipm_solve first");
+  if (!aligned16(p) || !aligned16(q)) return fail_arg(h, "p and q must be 16-byte aligned");
   GSpec g;
   g.mapin = MAPIN_BETA;
   g.src = p;
   g.mapout = MAPOUT_K;
   g.p_in = p;
   g.q_out = q;
+  g.stall_log2 = h->stall_log2;
+  h->stall_log2 = 0;
+  const bool fp32 = h->opt.precision == IPM_MIXED;
+  // a last pass that stages its operands on an mbarrier reports an expired wait
+  const bool staged = h->lay.d >= 2 && (fp32 ? h->pass32 : h->pass64).row_fwd.kstage == 2;
+  int* flag = &h->d_sc->wait_expired;
+  if (staged) CK(cudaMemsetAsync(flag, 0, sizeof(int), h->st));
   PdlScope pdl(h->opt.pdl != 0);
-  ipm_status s = run_g(h, h->opt.precision == IPM_MIXED, g);
+  ipm_status s = run_g(h, fp32, g);
   if (s != IPM_OK) return s;
+  if (staged) CK(cudaMemcpyAsync(&h->h_sc->wait_expired, flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   prof_collect(h);
+  if (staged && h->h_sc->wait_expired) {
+    h->err = "a bounded device-side wait expired (staged K operands)";
+    return IPM_TIMEOUT;
+  }
+  return IPM_OK;
+}
+
+ipm_status ipm_test_stage_stall(sdft_ipm* h, int wait_log2) {
+  if (!h) return fail_arg(nullptr, "handle is NULL");
+  if (wait_log2 < 8 || wait_log2 > 24) return fail_arg(h, "wait_log2 must be in 8..24");
+  const PassCfg& f = (h->opt.precision == IPM_MIXED ? h->pass32 : h->pass64).row_fwd;
+  if (h->lay.d < 2 || f.kstage != 2) return fail_arg(h, "the last pass does not stage its operands in shared memory");
+  h->stall_log2 = wait_log2;
   return IPM_OK;
 }
 
@@ -1360,8 +1469,8 @@ int ipm_describe(const sdft_ipm* h, char* buf, int len) {
   auto one = [&](const char* name, const PassCfg& c) {
     char tmp[256];
     snprintf(tmp, sizeof(tmp), "\"%s\": {\"L\": %d, \"E\": %d, \"P\": %d, \"threads\": %d, \"blocks\": %u, "
-             "\"smem\": %zu, \"engine\": \"%s\"}", name, c.plan.L, c.E, 1 << c.lgP, c.threads, c.grid.x * c.grid.y,
-             c.smem, c.reg ? "register" : "shared");
+             "\"smem\": %zu, \"engine\": \"%s\", \"kstage\": %d}", name, c.plan.L, c.E, 1 << c.lgP, c.threads,
+             c.grid.x * c.grid.y, c.kstage == 2 ? c.smem_staged : c.smem, c.reg ? "register" : "shared", c.kstage);
     if (out.size() > 1) out += ", ";
     out += tmp;
   };

@@ -39,6 +39,7 @@
 #include <cstdint>
 
 #include "conv_tc.h"
+#include "mbarrier.cuh"
 
 namespace sdft {
 namespace {
@@ -60,46 +61,8 @@ struct Ring {
   static constexpr int kPlaneBytes = kSlots * kTripleBytes;
 };
 constexpr int kThreads = 192;
-constexpr unsigned kWaitLimit = 1u << 24;   // polls of one mbarrier wait (with back-off: seconds)
 
 __device__ unsigned g_conv_tc_error;        // 0, or the code of the first wait that expired
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the phase of parity `parity` to complete; false after `limit` polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned limit = kWaitLimit) {
-  for (unsigned i = 0; i < limit; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if (i >= 32) __nanosleep(128);
-  }
-  return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
 
 // 4D tiled TMA load (coordinates: channel, z, i1, i0; out-of-range -> zeros)
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
@@ -279,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_tc_kernel(const __grid_const
     for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&accf_b[i]), 1); mbar_init(smem_u32(&acce_b[i]), 128); }
     mbar_init(smem_u32(done_b), 1);
     s_abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_fence_init();
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights: generic writes -> MMA reads
   if (warp == 1) {

@@ -25,6 +25,7 @@
 
 #include "fft_reg.cuh"
 #include "internal.h"
+#include "mbarrier.cuh"
 
 namespace sdft {
 
@@ -104,6 +105,48 @@ __device__ __forceinline__ KIn k_load(const PassArgs& a, long long g) {
   return k;
 }
 
+// The same operands for a whole tile of n consecutive slots g0 .. g0 + n - 1, staged in
+// shared memory as four arrays of n double2 (p_beta, p_z, Lambda1, Lambda2).
+struct KStage {
+  const double2* s = nullptr;
+  long long g0 = 0;
+  int n = 0;
+};
+
+__device__ __forceinline__ KIn k_load_staged(const KStage& ks, long long g) {
+  const int i = (int)(g - ks.g0);
+  KIn k;
+  k.pb = ks.s[i];
+  k.pz = ks.s[ks.n + i];
+  k.l1 = ks.s[2 * ks.n + i];
+  k.l2 = ks.s[3 * ks.n + i];
+  return k;
+}
+
+// Thread 0 of a forward row pass with the K epilogue, before the tile is loaded:
+// start moving the tile's operands (kstage 1: into L2; kstage 2: into shared memory at
+// dst, completing on the mbarrier bar).  The operand rows are contiguous (a row pass
+// tile is P consecutive rows), so each of the four arrays is one bulk copy of 16 n bytes;
+// the launcher guarantees 16-byte aligned operand pointers.
+__device__ __forceinline__ void k_stage_issue(const PassArgs& a, const KStage& ks, unsigned char* dst,
+                                              unsigned long long* bar) {
+  const uint32_t bytes = (uint32_t)ks.n * 16u;
+  const double2* p2 = reinterpret_cast<const double2*>(a.p);
+  const void* src[4] = {p2 + ks.g0, p2 + a.lay.H + ks.g0, reinterpret_cast<const double2*>(a.lam1) + ks.g0,
+                        reinterpret_cast<const double2*>(a.lam2) + ks.g0};
+  if (a.kstage == 1) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bulk_prefetch_l2(src[j], bytes);
+    return;
+  }
+  const uint32_t b = smem_u32(bar);
+  mbar_init(b, 1);
+  mbar_fence_init();
+  mbar_expect_tx(b, 4u * bytes);
+  const int ncopy = a.kst_wait_log2 ? 3 : 4;     // the failure-detection test leaves one out
+  for (int j = 0; j < ncopy; ++j) bulk_load(smem_u32(dst) + (uint32_t)j * bytes, src[j], bytes, b);
+}
+
 // q = [G p_b + L1 p_b + L2 p_z ; L2 p_b + L1 p_z] for slot g from (G p_b)_g = w;
 // inside PCG also adds this slot's share of p^T q to acc.
 template <typename V, bool PQ>
@@ -131,7 +174,8 @@ __device__ __forceinline__ void k_store(const PassArgs& a, long long g, V w, con
 // Store the complex value of slot g for the last pass (one slot at a time:
 // used where the operands need no batching).
 template <typename V, bool PQ>
-__device__ __forceinline__ void store_slot(const PassArgs& a, long long g, V w, double& acc) {
+__device__ __forceinline__ void store_slot(const PassArgs& a, long long g, V w, double& acc,
+                                           const KStage* ks = nullptr) {
   if (a.mapout == MAPOUT_NONE) {
     reinterpret_cast<V*>(a.buf)[g] = w;
     return;
@@ -142,7 +186,7 @@ __device__ __forceinline__ void store_slot(const PassArgs& a, long long g, V w, 
     __stcs(reinterpret_cast<double2*>(a.dst) + g, make_double2(o0, o1));
     return;
   }
-  k_store<V, PQ>(a, g, w, k_load(a, g), acc);
+  k_store<V, PQ>(a, g, w, ks ? k_load_staged(*ks, g) : k_load(a, g), acc);
 }
 
 // Loads of the E elements b = 0..E-1 of a thread: `elem(b, g)` gives the global
@@ -219,11 +263,12 @@ __device__ __forceinline__ void load_vals(const PassArgs& a, F&& elem, S&& sink)
 // loads of four slots before their stores was measured: it raised the forward row
 // kernel from 48 to 112 registers and made the 256^3 product slower (0.324 -> 0.379 ms).
 template <typename V, int E, bool PQ, typename F, typename S>
-__device__ __forceinline__ void store_vals(const PassArgs& a, double& acc, F&& elem, S&& src) {
+__device__ __forceinline__ void store_vals(const PassArgs& a, double& acc, F&& elem, S&& src,
+                                           const KStage* ks = nullptr) {
 #pragma unroll
   for (int b = 0; b < E; ++b) {
     long long g;
-    if (elem(b, g)) store_slot<V, PQ>(a, g, src(b), acc);
+    if (elem(b, g)) store_slot<V, PQ>(a, g, src(b), acc, ks);
   }
 }
 
@@ -252,12 +297,27 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) row_pass_kernel(PassAr
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double scratch[32];
+  __shared__ __align__(8) unsigned long long kbar;   // staged K operands (kstage 2)
   pdl_wait();
   count_launch(a.sc);
   if (pass_skipped(a)) return;
   V* buf = reinterpret_cast<V*>(smem_raw);
   const int PP = a.PP, L = LC > 0 ? LC : a.plan.L, nwork = a.nwork, tid = threadIdx.x;
   const long long row0 = (long long)blockIdx.x << a.lgP;
+  // forward pass with the K epilogue: the tile's FP64 operands start moving now and
+  // arrive while the tile is loaded and transformed
+  int kst = 0;
+  KStage ks;
+  if constexpr (!INV) {
+    if (a.mapout == MAPOUT_K && a.kstage != 0) {
+      kst = a.kstage;
+      const long long rows = min((long long)1 << a.lgP, a.npencils - row0);
+      ks.g0 = row0 * L;
+      ks.n = (int)(rows * L);
+      ks.s = reinterpret_cast<const double2*>(smem_raw + a.kst_off);
+      if (tid == 0) k_stage_issue(a, ks, smem_raw + a.kst_off, &kbar);
+    }
+  }
   // element b of a working thread: idx = tid + b nwork, pencil idx / L, position idx % L
   // (consecutive threads walk one row: coalesced global access)
   auto sidx = [&](int b) {
@@ -277,10 +337,23 @@ __global__ void __launch_bounds__(E == 16 ? 256 : 512, 1) row_pass_kernel(PassAr
   __syncthreads();
   fft_tile_l<E, INV, LC>(buf, a.plan, a.lgP, PP, reinterpret_cast<const V*>(a.tw), tid, nwork);
   double acc = 0.0;
-  if (tid < nwork) {
+  // staged operands: wait (bounded) for the copies; if the wait gives up, the tile
+  // writes nothing, records the expiry for the host (IPM_TIMEOUT) and waits once more,
+  // again bounded, so that no copy is still landing in shared memory when it exits
+  bool ready = true;
+  if (kst == 2 && tid < nwork) {
+    const unsigned limit = a.kst_wait_log2 ? (1u << a.kst_wait_log2) : kWaitLimit;
+    ready = mbar_wait(smem_u32(&kbar), 0, limit);
+    if (!ready) {
+      a.sc->wait_expired = 1;
+      mbar_wait(smem_u32(&kbar), 0, limit);
+    }
+  }
+  if (tid < nwork && ready) {
     auto src = [&](int b) { return buf[sidx(b)]; };
-    if (a.pcg_mode) store_vals<V, E, true>(a, acc, elem, src);
-    else store_vals<V, E, false>(a, acc, elem, src);
+    const KStage* kp = kst == 2 ? &ks : nullptr;
+    if (a.pcg_mode) store_vals<V, E, true>(a, acc, elem, src, kp);
+    else store_vals<V, E, false>(a, acc, elem, src, kp);
   }
   if (a.mapout == MAPOUT_K && a.pcg_mode) finish_pq(a, acc, scratch);
 }

@@ -58,7 +58,7 @@ struct DevScalars {
                      // takes the fixed centring rule and no second-order term
   int confirming;    // (incr) this iteration's exact product confirms a stop test passed on the
                      // carried G beta; if it fails, G beta is recomputed every iteration from then on
-  int pad1;
+  int wait_expired;  // a bounded device-side wait gave up (staged K operands): the solve reports IPM_TIMEOUT
   unsigned long long launches;   // kernels launched by the library (every kernel adds 1)
 };
 
@@ -104,6 +104,13 @@ struct PassArgs {
   unsigned* counter;
   DevScalars* sc;
   int reg;               // 1: register-engine kernels (fft_reg.cuh), E = 16
+  int kstage;            // forward row pass with MAPOUT_K: how its FP64 operands (p, Lambda1, Lambda2)
+                         // reach the epilogue: 0 per-slot loads after the transform, 1 an L2 bulk
+                         // prefetch of the tile's operands when the block starts, 2 bulk copies
+                         // into shared memory (at byte offset kst_off) completing on an mbarrier
+  unsigned kst_off;
+  int kst_wait_log2;     // failure-detection test: 0 normally; else leave out the fourth operand copy
+                         // and give up each wait after 2^kst_wait_log2 polls
 };
 
 // Launch with programmatic stream serialization while g_pdl is set (by the

@@ -94,6 +94,7 @@ __device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double 
   sc->refine_now = 0;
   sc->refine_exit = 0;
   sc->refinements = 0;
+  sc->wait_expired = 0;
 }
 
 // Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu; control reset
@@ -242,16 +243,15 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
       const double b = w.beta[i], z = w.z[i], s1 = w.s1[i], s2 = w.s2[i], n1 = w.nu1[i], n2_ = w.nu2[i];
       is1 = rcp1(s1);
       is2 = rcp1(s2);
-      const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
-      const double r_z = lam - n1 - n2_;
       const double r_p1 = z + b - s1, r_p2 = z - b - s2;
-      // r_c_i / s_i + Sigma_i r_p_i = nu_i + (nu_i r_p_i - sigma mu) / s_i
-      const double A1 = fma(is1, fma(n1, r_p1, -smu), n1);
-      const double A2 = fma(is2, fma(n2_, r_p2, -smu), n2_);
-      rb = -r_d - A1 + A2;
-      rc = -r_z - A1 - A2;
+      const double S1 = n1 * is1, S2 = n2_ * is2;                // Sigma_i = S_i^{-1} V_i
+      // r_c_i / s_i + Sigma_i r_p_i = nu_i + Sigma_i r_p_i - sigma mu / s_i; the nu terms
+      // cancel against those of r_d = G beta - c - nu1 + nu2 and r_z = lambda - nu1 - nu2:
+      // with e_i = Sigma_i r_p_i - sigma mu / s_i, rb = (c - G beta) - e1 + e2, rc = -lambda - e1 - e2
+      const double e1 = fma(S1, r_p1, -smu * is1), e2 = fma(S2, r_p2, -smu * is2);
+      rb = (w.c[i] - w.Gb[i]) - e1 + e2;
+      rc = -lam - e1 - e2;
       {
-        const double S1 = n1 * is1, S2 = n2_ * is2;              // Sigma_i = S_i^{-1} V_i
         l1 = S1 + S2;
         l2 = S1 - S2;
         const double iD = rcp1(fma(4.0 * S1, S2, prho * l1));   // D = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2
@@ -339,13 +339,12 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(Layout lay, IpmVect
       pa = l1 * iD;
       pb = l2 * iD;
       pc = (prho + l1) * iD;
-      const double r_d = w.Gb[i] - w.c[i] - n1 + n2_;
-      const double r_z = lam - n1 - n2_;
       const double r_p1 = z + b - s1, r_p2 = z - b - s2;
-      // sigma = 0: r_c_i / s_i + Sigma_i r_p_i = nu_i + Sigma_i r_p_i
-      const double A1 = fma(S1, r_p1, n1), A2 = fma(S2, r_p2, n2_);
-      rb = -r_d - A1 + A2;
-      rc = -r_z - A1 - A2;
+      // sigma = 0: r_c_i / s_i + Sigma_i r_p_i = nu_i + Sigma_i r_p_i, and the nu terms
+      // cancel against those of r_d = G beta - c - nu1 + nu2 and r_z = lambda - nu1 - nu2:
+      // rb = (c - G beta) - Sigma1 r_p1 + Sigma2 r_p2, rc = -lambda - Sigma1 r_p1 - Sigma2 r_p2
+      rb = fma(S2, r_p2, fma(-S1, r_p1, w.c[i] - w.Gb[i]));
+      rc = fma(-S2, r_p2, fma(-S1, r_p1, -lam));
       const double db = fma(pa, rb, -pb * rc), dz = fma(pc, rc, -pb * rb);
       const double ds1 = dz + db + r_p1, ds2 = dz - db + r_p2;
       const double dn1 = -fma(S1, ds1, n1), dn2 = -fma(S2, ds2, n2_);
@@ -724,8 +723,8 @@ __device__ __forceinline__ Dir direction(const IpmVectors& w, long long i, long 
   Dir d;
   d.ds1 = dz + db + (z + b - s1);
   d.ds2 = dz - db + (z - b - s2);
-  d.dn1 = -fma(c1 - smu, is1, n1) - (n1 * is1) * d.ds1;
-  d.dn2 = -fma(c2 - smu, is2, n2_) - (n2_ * is2) * d.ds2;
+  d.dn1 = -fma(is1, fma(n1, d.ds1, c1 - smu), n1);     // -nu1 - (c1 - sigma mu + nu1 ds1) / s1
+  d.dn2 = -fma(is2, fma(n2_, d.ds2, c2 - smu), n2_);
   return d;
 }
 
@@ -763,8 +762,8 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
       auto g = [&](const double2& v) { return k ? v.y : v.x; };
       const double ds1 = g(dz) + g(db) + (g(z) + g(b) - g(s1));
       const double ds2 = g(dz) - g(db) + (g(z) - g(b) - g(s2));
-      const double dn1 = -fma(g(c1) - smu, g(is1), g(n1)) - (g(n1) * g(is1)) * ds1;
-      const double dn2 = -fma(g(c2) - smu, g(is2), g(n2_)) - (g(n2_) * g(is2)) * ds2;
+      const double dn1 = -fma(g(is1), fma(g(n1), ds1, g(c1) - smu), g(n1));
+      const double dn2 = -fma(g(is2), fma(g(n2_), ds2, g(c2) - smu), g(n2_));
       if (!is_ghost(lay, 2 * j + k)) {
         consider(g(s1), ds1);
         consider(g(s2), ds2);

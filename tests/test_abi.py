@@ -47,7 +47,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_default_options(lib):
     o = binding.default_options()
     assert o.precision == binding.IPM_FP64
-    assert o.gap_tol == 1e-6 and o.cg_relative == 1 and o.tau == 0.995 and o.sigma == 0.1
+    assert o.gap_tol == 1e-6 and o.cg_tol == 1e-6 and o.cg_relative == 1 and o.tau == 0.995 and o.sigma == 0.1
 
 
 @pytest.mark.parametrize("dims,why", [((22,), "factor 11"), ((13,), "prime 13"), ((8, 33), "factor 11"),
@@ -87,14 +87,15 @@ def test_null_handle_calls_fail_cleanly(lib):
 def test_default_options_of_the_solver_variants(lib):
     o = binding.default_options()
     assert o.tile_engine == 0 and o.sigma_rule == 2 and o.sigma_min == 0.01
-    assert o.exact_residual == 0 and o.precond_rho == 1.0 and o.pdl == 1 and o.krylov == 0
+    assert o.exact_residual == 0 and o.precond_rho == 1.0 and o.pdl == 1 and o.krylov == 0 and o.tile_kstage == 0
 
 
 @pytest.mark.parametrize("field,value,extra", [("tile_engine", 3, {}), ("sigma_rule", 3, {}), ("sigma_rule", -1, {}),
                                                ("sigma_min", -0.1, {}), ("sigma_min", 1.0, {}),
                                                ("sigma_min", 0.0, {"sigma_rule": 1}), ("sigma_min", 0.9, {"sigma_rule": 1}),
                                                ("exact_residual", 2, {}), ("precond_rho", -1.0, {}), ("pdl", 2, {}),
-                                               ("krylov", 3, {}), ("krylov", -1, {}), ("precond_rho", float("inf"), {})])
+                                               ("krylov", 3, {}), ("krylov", -1, {}), ("precond_rho", float("inf"), {}),
+                                               ("tile_kstage", 4, {}), ("tile_kstage", -1, {})])
 def test_create_rejects_bad_variant_options(lib, field, value, extra):
     h = ctypes.c_void_p()
     d = (ctypes.c_int64 * 1)(8)

@@ -158,6 +158,99 @@ def test_kkt_and_precond_match_oracle(dims, precision):
         binding.ipm_destroy(h)
 
 
+# Operand staging of the last pass (tile_kstage 1: per-slot loads, 2: L2 bulk prefetch,
+# 3: bulk copies into shared memory on an mbarrier) only changes where the epilogue reads
+# its operands: products and solves are bit-identical.  Forced tiles make every handle
+# launch the same shapes; (48, 64) has 33 rows of 48 and (15, 16, 10) 90 rows of 16, so a
+# tile of 4 rows leaves a ragged last tile; (32, 24, 16) runs its tuned tile.
+KSTAGE_CASES = [((48, 64), {"tile_e": 8, "tile_p": 4}), ((15, 16, 10), {"tile_e": 8, "tile_p": 4}),
+                ((32, 24, 16), {})]
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+@pytest.mark.parametrize("dims,tile", KSTAGE_CASES)
+def test_staged_k_operands_give_identical_products(dims, tile, precision):
+    w = _workload(dims, seed=6)
+    n = int(np.prod(dims))
+    prob = _oracle(w, 1.0)
+    rng = np.random.default_rng(7)
+    s1, nu1, s2, nu2 = _interior(n, rng)
+    S1, S2 = oipm.sigmas(s1, nu1, s2, nu2)
+    pb, pz = rng.standard_normal(n), rng.standard_normal(n)
+    qs = []
+    for ks in (1, 2, 3):
+        h = _handle(w, precision, tile_kstage=ks, **tile)
+        try:
+            row = binding.ipm_describe(h)["fp32_row" if precision == binding.IPM_MIXED else "fp64_row"]
+            assert row["kstage"] == ks - 1, row
+            binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+            p = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
+            q = torch.full_like(p, float("nan"))
+            binding.kkt_apply(h, p, q)
+            if ks == 3:
+                _check_kkt(h, prob, dims, precision, S1, S2, pb, pz, q)
+            qs.append(q)
+        finally:
+            binding.ipm_destroy(h)
+    assert torch.equal(qs[0], qs[1]) and torch.equal(qs[0], qs[2])
+
+
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+def test_staged_k_operands_give_identical_solves(precision):
+    w = _workload((15, 16, 10), seed=8)
+    prob = _oracle_rel(w, 0.1)
+    out = []
+    for ks in (1, 3):
+        h = _handle(w, precision, prob=prob, gap_tol=1e-8, tile_kstage=ks, tile_e=8, tile_p=4)
+        try:
+            res = binding.ipm_solve(h)
+            H, _ = binding.ipm_sizes(h)
+            v = torch.empty(2 * H, dtype=torch.float64, device="cuda")
+            binding.ipm_get_spectrum(h, v)
+            out.append((res, v))
+        finally:
+            binding.ipm_destroy(h)
+    (r1, v1), (r3, v3) = out
+    assert r1["status"] == binding.IPM_OK and r3["status"] == binding.IPM_OK
+    for k in ("ipm_iters", "cg_iters_total", "kkt_products", "primal", "dual", "rel_gap"):
+        assert r1[k] == r3[k], k
+    assert torch.equal(v1, v3)
+
+
+def test_staged_wait_expiry_reports_timeout():
+    """Failure detection: the next product leaves out one operand copy per block of its last
+    pass and waits at most 2^10 polls; the call returns IPM_TIMEOUT, the context and the
+    handle stay usable, and the next product is exact again."""
+    dims = (48, 64)
+    w = _workload(dims, seed=9)
+    n = int(np.prod(dims))
+    rng = np.random.default_rng(10)
+    s1, nu1, s2, nu2 = _interior(n, rng)
+    h = _handle(w, binding.IPM_MIXED, tile_kstage=3, tile_e=8, tile_p=4)
+    try:
+        binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+        p = torch.cat([oracle_to_lib(h, rng.standard_normal(n), dims), oracle_to_lib(h, rng.standard_normal(n), dims)])
+        q_ref = torch.empty_like(p)
+        binding.kkt_apply(h, p, q_ref)
+        binding.ipm_test_stage_stall(h, 10)
+        q = torch.zeros_like(p)
+        with pytest.raises(binding.IpmError) as e:
+            binding.kkt_apply(h, p, q)
+        assert e.value.status == binding.IPM_TIMEOUT
+        assert "wait expired" in binding.ipm_last_error(h)
+        binding.kkt_apply(h, p, q)
+        assert torch.equal(q, q_ref)
+    finally:
+        binding.ipm_destroy(h)
+    h = _handle(w, binding.IPM_MIXED, tile_kstage=1)
+    try:
+        with pytest.raises(binding.IpmError) as e:
+            binding.ipm_test_stage_stall(h, 10)
+        assert e.value.status == binding.IPM_ERR_ARG
+    finally:
+        binding.ipm_destroy(h)
+
+
 def _solve_both(w, lam_rel, gap_tol, precision=binding.IPM_FP64, **opt):
     """GPU solve of w with the oracle's lambda; returns (result, GPU spectrum, oracle problem)."""
     prob = _oracle_rel(w, lam_rel)
@@ -257,9 +350,10 @@ def test_mixed_precision_solve_reaches_gap():
     assert np.abs(v32 - v64).max() <= 1e-4 * np.abs(v64).max()
 
 
+@pytest.mark.parametrize("cg_tol", [1e-10, 1e-6])
 @pytest.mark.parametrize("exact", [0, 1])
 @pytest.mark.parametrize("dims", [(512,), (64, 48), (32, 24, 16)])
-def test_mixed_cg_matches_fp64_pcg(dims, exact):
+def test_mixed_cg_matches_fp64_pcg(dims, exact, cg_tol):
     """Mixed precision runs the same PCG with FP32 FFT products and FP64 Krylov
     vectors and barrier terms; the IPM takes the FP64 solve's path: same IPM
     iterations (+-1) and the same solution.  With G beta recomputed by an FP64
@@ -267,8 +361,8 @@ def test_mixed_cg_matches_fp64_pcg(dims, exact):
     with G beta carried through the FP32 products between exact confirmations (the
     default) the IPM residual carries their rounding, and to 25 %."""
     w = _workload(dims, seed=21)
-    r64, v64, _ = _solve_both(w, 0.1, 1e-8, exact_residual=exact)
-    r32, v32, _ = _solve_both(w, 0.1, 1e-8, precision=binding.IPM_MIXED, exact_residual=exact)
+    r64, v64, _ = _solve_both(w, 0.1, 1e-8, exact_residual=exact, cg_tol=cg_tol)
+    r32, v32, _ = _solve_both(w, 0.1, 1e-8, precision=binding.IPM_MIXED, exact_residual=exact, cg_tol=cg_tol)
     assert r32["status"] == binding.IPM_OK and r32["rel_gap"] <= 1e-8
     assert abs(r32["ipm_iters"] - r64["ipm_iters"]) <= 1
     frac = 0.1 if exact else 0.25
@@ -468,7 +562,7 @@ def test_adaptive_centring_matches_oracle(dims):
     and the oracle with the same rule take the same IPM iterations to the same optimum."""
     w = _workload(dims, seed=25)
     prob = _oracle_rel(w, 0.1)
-    h = _handle(w, binding.IPM_FP64, prob=prob, gap_tol=1e-8, sigma_rule=1, sigma_min=0.03)
+    h = _handle(w, binding.IPM_FP64, prob=prob, gap_tol=1e-8, sigma_rule=1, sigma_min=0.03, cg_tol=1e-10)
     try:
         res = binding.ipm_solve(h)
     finally:
@@ -483,7 +577,7 @@ def test_fixed_centring_matches_oracle():
     """sigma_rule = 0 (sigma = 0.1, 0.5 after a step alpha < 0.1): same iterations as the oracle's default."""
     w = _workload((32, 24, 16), seed=26)
     prob = _oracle_rel(w, 0.1)
-    h = _handle(w, binding.IPM_FP64, prob=prob, gap_tol=1e-8, sigma_rule=0)
+    h = _handle(w, binding.IPM_FP64, prob=prob, gap_tol=1e-8, sigma_rule=0, cg_tol=1e-10)
     try:
         res = binding.ipm_solve(h)
     finally:
@@ -590,7 +684,7 @@ def test_tile_cache_file_reproduces_tiles(tmp_path):
                                  check=True).stdout.strip().splitlines()[-1]
     first = run()
     lines = (tmp_path / "tiles.txt").read_text().splitlines()
-    assert len(lines) >= 6 and all(len(ln.split()) == 9 for ln in lines)
+    assert len(lines) >= 6 and all(len(ln.split()) == 10 for ln in lines)
     assert run() == first
     assert (tmp_path / "tiles.txt").read_text().splitlines() == lines      # nothing re-tuned
 
@@ -802,7 +896,7 @@ def test_conjugate_a_residuals_match_oracle(precision, dims):
     two sides may restart one iteration apart (one FP64 case came out 105 vs 106)."""
     w = _workload(dims, seed=37)
     prob = _oracle_rel(w, 0.1)
-    h = _handle(w, precision, prob=prob, gap_tol=1e-8, krylov=2)
+    h = _handle(w, precision, prob=prob, gap_tol=1e-8, krylov=2, cg_tol=1e-10)
     try:
         res = binding.ipm_solve(h)
     finally:
@@ -844,7 +938,7 @@ def test_conjugate_residuals_match_oracle(precision, dims):
     CR solve, and in FP64 the same IPM and Krylov iteration counts."""
     w = _workload(dims, seed=35)
     prob = _oracle_rel(w, 0.1)
-    h = _handle(w, precision, prob=prob, gap_tol=1e-8, krylov=1)
+    h = _handle(w, precision, prob=prob, gap_tol=1e-8, krylov=1, cg_tol=1e-10)
     try:
         res = binding.ipm_solve(h)
     finally:
@@ -861,8 +955,9 @@ def test_conjugate_residuals_match_oracle(precision, dims):
         assert abs(res["cg_iters_total"] - total) <= 2 + 0.02 * total
 
 
+@pytest.mark.parametrize("cg_tol", [1e-10, 1e-6])
 @pytest.mark.parametrize("dims,sigma_min", [((32, 24, 16), 0.01), ((64, 48), 0.01), ((15, 21), 0.03), ((512,), 0.01)])
-def test_predictor_corrector_matches_oracle(dims, sigma_min):
+def test_predictor_corrector_matches_oracle(dims, sigma_min, cg_tol):
     """sigma_rule = 2, the single-step predictor-corrector (affine predictor P^{-1} rhs_aff,
     Mehrotra's sigma and second-order term, one Krylov solve): the library and the oracle's
     "single" rule take the same IPM iterations to the same optimum in FP64.  The Krylov
@@ -870,12 +965,12 @@ def test_predictor_corrector_matches_oracle(dims, sigma_min):
     (as the step's), so sigma differs from the oracle's in its last digits."""
     w = _workload(dims, seed=71)
     prob = _oracle_rel(w, 0.1)
-    h = _handle(w, binding.IPM_FP64, prob=prob, gap_tol=1e-9, sigma_rule=2, sigma_min=sigma_min)
+    h = _handle(w, binding.IPM_FP64, prob=prob, gap_tol=1e-9, sigma_rule=2, sigma_min=sigma_min, cg_tol=cg_tol)
     try:
         res = binding.ipm_solve(h)
     finally:
         binding.ipm_destroy(h)
-    ora = oipm.solve(prob, gap_tol=1e-9, sigma_rule="single", sigma_min=sigma_min)
+    ora = oipm.solve(prob, gap_tol=1e-9, sigma_rule="single", sigma_min=sigma_min, cg_tol=cg_tol)
     assert res["status"] == binding.IPM_OK and ora["status"] == "converged"
     assert res["ipm_iters"] == ora["ipm_iters"]
     total = sum(ora["cg_counts"])
