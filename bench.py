@@ -938,17 +938,24 @@ def run_warm512(args):
     spec_h = torch.empty(2 * H, dtype=torch.float64).pin_memory()
     e2e_steps = min(args.steps, 5)
     e2e_t = []
+    split = [0.0, 0.0, 0.0]
     for i in range(e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        binding.ipm_set_problem(h32, mask_h, y_h, w.lam_rel)
+        binding.ipm_set_problem(h32, mask_h, y_h, w.lam_rel)      # returns after its work (reads lambda_max)
+        ta = time.perf_counter()
         warm()
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
         binding.ipm_get_spectrum(h32, spec_h)
         t1 = time.perf_counter()
         if i > 0:
             e2e_t.append(t1 - t0)
+            split = [split[0] + ta - t0, split[1] + tb - ta, split[2] + t1 - tb]
     e2e = {"value": sum(e2e_t) / len(e2e_t), "unit": "s", "h2d_bytes_per_step": int(mask_h.numel() + y_h.numel() * 8),
            "d2h_bytes_per_step": int(spec_h.numel() * 8), "steps": e2e_steps,
+           "split_s": {"set_problem": split[0] / e2e_steps, "predict_and_solve": split[1] / e2e_steps,
+                       "get_spectrum": split[2] / e2e_steps},
            "path": "ipm_set_problem (pinned host mask and signal) + ws_predict + ipm_solve + ipm_get_spectrum "
                    "(pinned host), wall clock"}
     binding.ipm_destroy(h64)

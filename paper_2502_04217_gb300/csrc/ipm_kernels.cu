@@ -157,13 +157,18 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
   const double2* b2 = reinterpret_cast<const double2*>(beta);
   const double2* g2 = reinterpret_cast<const double2*>(Gb);
   const double2* c2 = reinterpret_cast<const double2*>(c);
+  // ||c - G beta||_inf on the integer pipe: the bit patterns of non-negative doubles
+  // order like the numbers (a non-finite G beta also makes the sum v[1] non-finite)
+  unsigned long long m3 = 0ull;
+  auto abs_bits = [](double x) { return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull; };
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < (n2 >> 1); j += (long long)gridDim.x * blockDim.x) {
     const double2 b = b2[j], g = g2[j], ci = c2[j];
     v[0] += ci.x * b.x + ci.y * b.y;
     v[1] += b.x * g.x + b.y * g.y;
     v[2] += fabs(b.x) + fabs(b.y);
-    v[3] = fmax(v[3], fmax(fabs(ci.x - g.x), fabs(ci.y - g.y)));
+    m3 = max(m3, max(abs_bits(ci.x - g.x), abs_bits(ci.y - g.y)));
   }
+  v[3] = __longlong_as_double((long long)m3);
   if (grid_reduce<4>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
     const double lam = sc->lambda;
     const double th2 = fmax(sc->yy - 2.0 * v[0] + v[1], 0.0);
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Layout lay, IpmVector
         const double iD = rcp1(fma(4.0 * S1, S2, prho * l1));   // D = rho (Sigma1 + Sigma2) + 4 Sigma1 Sigma2
         pa = l1 * iD;
         pb = l2 * iD;
-        pc_ = (prho + l1) * iD;
+        pc_ = fma(prho, iD, pa);                                   // (rho + Lambda1) / D
       }
       zb = pa * rb - pb * rc;
       zz = -pb * rb + pc_ * rc;
@@ -320,6 +325,7 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(Layout lay, IpmVect
   const long long n2 = 2 * lay.H;
   const double lam = sc->lambda;
   const double prho = precond_scale(rho_opt, lay, sc);
+  const bool rho_one = prho == 1.0;        // the paper's P: no multiply by rho
   const bool skip = sc->pc_skip != 0;
   float best = __int_as_float(0x7f800000);   // +inf
   auto consider = [&](double wv, double dw) {
@@ -335,10 +341,10 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(Layout lay, IpmVect
       const double S1 = n1 * is1, S2 = n2_ * is2;
       l1 = S1 + S2;
       l2 = S1 - S2;
-      const double iD = rcp1(fma(4.0 * S1, S2, prho * l1));
+      const double iD = rcp1(fma(4.0 * S1, S2, rho_one ? l1 : prho * l1));
       pa = l1 * iD;
       pb = l2 * iD;
-      pc = (prho + l1) * iD;
+      pc = fma(prho, iD, pa);             // (rho + Lambda1) / D
       const double r_p1 = z + b - s1, r_p2 = z - b - s2;
       // sigma = 0: r_c_i / s_i + Sigma_i r_p_i = nu_i + Sigma_i r_p_i, and the nu terms
       // cancel against those of r_d = G beta - c - nu1 + nu2 and r_z = lambda - nu1 - nu2:

@@ -263,17 +263,29 @@ __global__ void bgrad_reduce_kernel(const float* __restrict__ part, int nblocks,
 
 __device__ __forceinline__ double soft1(double u) { return u > 1.0 ? u - 1.0 : (u < -1.0 ? u + 1.0 : 0.0); }
 
+__device__ __forceinline__ float soft1f(float u) { return u > 1.f ? u - 1.f : (u < -1.f ? u + 1.f : 0.f); }
+
 // Input features of every slot (16 channels, 8 used), from c = M_perp^T b and lambda.
+// They feed BF16 convolutions, so they are formed in FP32 (the FP64 operands converted
+// on the integer pipe, the slot's grid indices by the layout's multiply-high divisions):
+// nothing of this kernel runs on the FP64 pipe.
 __global__ void features_kernel(Layout lay, const double* __restrict__ c, const DevScalars* sc, bf16* __restrict__ x) {
-  const double il = 1.0 / sc->lambda;
+  const float il = d2f_int(1.0 / sc->lambda);
   const int D1 = lay.d == 3 ? lay.N0 : 1, D2 = lay.d == 3 ? lay.N1 : (lay.d == 2 ? lay.N0 : 1);
+  const float sl = lay.Hl > 1 ? 1.f / (float)(lay.Hl - 1) : 0.f, s1 = 2.f / (float)D1, s2 = 2.f / (float)D2;
+  const double2* c2 = reinterpret_cast<const double2*>(c);
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < lay.H; s += (long long)gridDim.x * blockDim.x) {
-    const double c0 = c[2 * s] * il, c1 = c[2 * s + 1] * il;
-    const int k2 = (int)(s % D2), k1 = (int)((s / D2) % D1), kl = (int)(s / ((long long)D1 * D2));
-    const float f0 = lay.d == 3 ? (float)min(k1, lay.N0 - k1) / (0.5f * lay.N0) : 0.f;
-    const float f1 = lay.d >= 2 ? (float)min(k2, D2 - k2) / (0.5f * D2) : 0.f;
-    float f[8] = {(float)c0, (float)c1, (float)soft1(c0), (float)soft1(c1), (float)sqrt(c0 * c0 + c1 * c1),
-                  lay.Hl > 1 ? (float)kl / (float)(lay.Hl - 1) : 0.f, f0, f1};
+    const double2 cv = c2[s];
+    const float c0 = d2f_int(cv.x) * il, c1 = d2f_int(cv.y) * il;
+    // slot = kl * M + k' with k' = k1 * D2 + k2 (k1 = 0 for d < 3; H < 2^31)
+    const unsigned su = (unsigned)s;
+    const int kl = (int)fast_div(su, lay.divM);
+    const int kp = (int)(su - (unsigned)kl * (unsigned)lay.M);
+    const int k1 = lay.d == 3 ? (int)fast_div((unsigned)kp, lay.divN1) : 0;
+    const int k2 = lay.d == 3 ? kp - k1 * lay.N1 : (lay.d == 2 ? kp : 0);
+    const float f0 = lay.d == 3 ? (float)min(k1, lay.N0 - k1) * s1 : 0.f;
+    const float f1 = lay.d >= 2 ? (float)min(k2, D2 - k2) * s2 : 0.f;
+    float f[8] = {c0, c1, soft1f(c0), soft1f(c1), sqrtf(c0 * c0 + c1 * c1), (float)kl * sl, f0, f1};
     uint32_t w[8];
 #pragma unroll
     for (int k = 0; k < 4; ++k) w[k] = pack2(__float2bfloat16_rn(f[2 * k]), __float2bfloat16_rn(f[2 * k + 1]));
