@@ -158,6 +158,33 @@ def test_kkt_and_precond_match_oracle(dims, precision):
         binding.ipm_destroy(h)
 
 
+@pytest.mark.parametrize("precision", [binding.IPM_FP64, binding.IPM_MIXED])
+@pytest.mark.parametrize("dims", [(256,), (48, 64), (16, 12, 8), (32, 24, 16)])
+def test_kkt_diagonal_terms_over_wide_ranges(dims, precision):
+    """The K epilogue's FP64 diagonal terms beside an FP64 or FP32 G part, with Sigma spread
+    over 1e-8 .. 1e8 and p over 1e-6 .. 1e6 with random signs: every element within the
+    1e-13 relative allowance of the diagonal terms against the oracle's FP64 K, the G part
+    within its FFT bound."""
+    w = _workload(dims, seed=12)
+    n = int(np.prod(dims))
+    prob = _oracle(w, 1.0)
+    rng = np.random.default_rng(13)
+    s1, s2 = 10.0 ** rng.uniform(-4, 4, n), 10.0 ** rng.uniform(-4, 4, n)
+    nu1, nu2 = 10.0 ** rng.uniform(-4, 4, n), 10.0 ** rng.uniform(-4, 4, n)
+    S1, S2 = oipm.sigmas(s1, nu1, s2, nu2)
+    pb = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-6, 6, n)
+    pz = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-6, 6, n)
+    h = _handle(w, precision)
+    try:
+        binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
+        p = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
+        q = torch.full_like(p, float("nan"))
+        binding.kkt_apply(h, p, q)
+        _check_kkt(h, prob, dims, precision, S1, S2, pb, pz, q)
+    finally:
+        binding.ipm_destroy(h)
+
+
 # Operand staging of the last pass (tile_kstage 1: per-slot loads, 2: L2 bulk prefetch,
 # 3: bulk copies into shared memory on an mbarrier) only changes where the epilogue reads
 # its operands: products and solves are bit-identical.  Forced tiles make every handle
