@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
   auto abs_bits = [](double x) { return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull; };
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < (n2 >> 1); j += (long long)gridDim.x * blockDim.x) {
     const double2 b = b2[j], g = g2[j], ci = c2[j];
-    v[0] += ci.x * b.x + ci.y * b.y;
-    v[1] += b.x * g.x + b.y * g.y;
+    v[0] = fma(ci.y, b.y, fma(ci.x, b.x, v[0]));     // FMAs into the running sums: the FP64
+    v[1] = fma(b.y, g.y, fma(b.x, g.x, v[1]));       // pipe bounds this kernel
     v[2] += fabs(b.x) + fabs(b.y);
     m3 = max(m3, max(abs_bits(ci.x - g.x), abs_bits(ci.y - g.y)));
   }
