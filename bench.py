@@ -33,6 +33,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "IPM solve time to 1e-6 rel. duality gap; KKT matvecs/s and HBM GB/s vs FP64 plain"
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 rate (no measured FP64 entry in the peaks file)
+# FP64 pipe operations per second (an FMA, an add or a multiply is one operation): the
+# nominal rate counts an FMA as two flops, so the pipe issues 1.25e12 / 2 = 6.25e11 per
+# second, about 2 per clock per SM at 152 SMs and 2.07 GHz
+FP64_PIPE_TOPS = FP64_PEAK_TFLOPS / 2
+# FP64 pipe operations per coordinate of the Newton-system kernels (counted from their
+# code): the predictor 40 (three Newton reciprocals, Sigma, Lambda, P^{-1}, the residuals,
+# the affine direction and its second-order terms), prepare after it 14 (the corrector's
+# right-hand side, z = P^{-1} r, r^T z); prepare alone (no predictor) 31
+FP64_OPS_PREDICTOR, FP64_OPS_PREPARE_PC, FP64_OPS_PREPARE = 40, 14, 31
 GAP_TOL = 1e-6
 WORKLOADS = {
     "1d": ("1d n=256 FP64 plain IPM: 8 N(0,1) frequencies, noise 0.01, 10% missing at random, "
@@ -294,7 +303,8 @@ def _class_model(dims, prec, res, opt):
         product also writes (G p)_beta (16 B), pcg_update updates G x (48 B), prepare
         clears G x (16 B), step_update updates G beta (32 B).
     FLOPs: 5 L log2 L per complex transform of length L, 2.5 L log2 L per real one.
-    Returns {class: (working launches, flops, bytes)} for one solve.
+    FP64 pipe operations of the Newton-system class: FP64_OPS_* per coordinate (2H).
+    Returns {class: (working launches, flops, bytes[, FP64 pipe operations])} for one solve.
     """
     import math
     d = len(dims)
@@ -335,9 +345,10 @@ def _class_model(dims, prec, res, opt):
     gx = 16 * H if incr else 0
     rhs = 32 * H if (mixed and opt.refine_every > 0) else 0
     if pc:
-        out["prepare"] = (2 * it, 0.0, it * ((128 + 176) * H + (144 + 128) * H + rhs + gx))
+        out["prepare"] = (2 * it, 0.0, it * ((128 + 176) * H + (144 + 128) * H + rhs + gx),
+                          it * 2 * H * (FP64_OPS_PREDICTOR + FP64_OPS_PREPARE_PC))
     else:
-        out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 128 * H + rhs + gx))
+        out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 128 * H + rhs + gx), it * 2 * H * FP64_OPS_PREPARE)
     # with the predictor-corrector step_length also reads the two terms and writes the direction
     # (+32 + 64 B); step_update reads the direction instead of 1/s and the terms (same count)
     out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (32 * H if incr else 0) + (96 * H if pc else 0)))
@@ -354,7 +365,7 @@ def _rooflines(dims, prec, res, breakdown, steps, opt):
     Hn = _sizes(dims)[0]
     model["certificate"] = (cert["launches"] // max(steps, 1), 0.0, (cert["launches"] // max(steps, 1)) * 48 * Hn)
     classes = {}
-    for nm, (work, flops, nbytes) in model.items():
+    for nm, (work, flops, nbytes, *ops) in model.items():
         b = breakdown.get(nm)
         if not b or not b["launches"] or b["ms"] <= 0:
             continue
@@ -365,6 +376,10 @@ def _rooflines(dims, prec, res, breakdown, steps, opt):
         if flops:
             c["algorithmic_flops"] = flops * steps
             c["tflops"] = flops * steps / t / 1e12
+        if ops:
+            c["fp64_ops"] = ops[0] * steps
+            c["fp64_tops"] = ops[0] * steps / t / 1e12
+            c["frac_of_fp64_pipe"] = c["fp64_tops"] / FP64_PIPE_TOPS
         classes[nm] = c
     dom = max(classes, key=lambda k: classes[k]["ms"])
     return classes, dom
@@ -380,6 +395,12 @@ def _roofline_line(dims, prec, res, breakdown, steps, workload, opt):
         r = {"bound": "alu", "achieved": c["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
              "frac": c["tflops"] / FP64_PEAK_TFLOPS,
              "peak_source": "nominal GB300 FP64 rate (profiling recipe; no FP64 entry in MEASURED_PEAKS.json)"}
+    elif c.get("frac_of_fp64_pipe", 0.0) > c["frac_of_hbm"]:
+        r = {"bound": "alu", "achieved": c["fp64_tops"], "peak": FP64_PIPE_TOPS,
+             "unit": "T FP64 pipe operations/s (FMA, add, multiply: one each)", "frac": c["frac_of_fp64_pipe"],
+             "algorithmic_fp64_ops": c["fp64_ops"],
+             "peak_source": "nominal GB300 FP64 rate 1.25 TFLOP/s (profiling recipe) / 2 flops per FMA; "
+                            "the class's HBM fraction is in classes"}
     else:
         r = {"bound": "hbm", "achieved": c["gbs"], "peak": peak, "unit": "GB/s", "frac": c["frac_of_hbm"],
              "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
