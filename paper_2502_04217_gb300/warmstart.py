@@ -21,11 +21,12 @@ from .synth import lattice_mask, make_problem
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart.f32")
-# mu0 = MU_SCALE lambda^2 of the predicted start point.  Under the predictor-corrector
-# rule, of {0.05, 0.1, 0.2, 0.3, 0.5, 0.8, 1.2} on two held-out 512^3 instances (3 and
-# 5 of the 512^3 workload, mixed precision, 1e-6 gap), 0.3 and 0.5 take 5 IPM
-# iterations and every other value 6 (the cold start 8 and 9).
-MU_SCALE = 0.5
+# mu0 = MU_SCALE lambda^2 of the predicted start point, chosen on held-out 512^3
+# instances (1 to 5 of the 512^3 workload; mixed precision, 1e-6 gap, the library's
+# defaults): of {0.1, 0.2, 0.3, 0.5, 0.8} every value takes 6 IPM iterations (the cold
+# start 8 to 10), and 0.3 the fewest PCG iterations (18 on three of the five instances,
+# 19 on the others; the rest 19 to 20).
+MU_SCALE = 0.3
 
 # (stored cin, stored cout, real cin, real cout) of the four convolutions
 LAYERS = [(16, 32, 8, 32), (32, 32, 32, 32), (32, 32, 32, 32), (32, 8, 32, 4)]
