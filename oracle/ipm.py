@@ -338,9 +338,15 @@ def next_sigma(alpha, rule, sigma0, sigma_slow, sigma_min):
 
 
 def solve(prob, gap_tol=1e-6, cg_tol=1e-10, max_ipm=200, max_cg=500, cg_relative=True,
-          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=0.03,
+          sigma0=0.1, sigma_slow=0.5, tau=0.995, w0=None, log=None, sigma_rule="fixed", sigma_min=None,
           precond_rho=1.0, krylov="cg", sigma_max=1.0):
-    """Run the IPM; returns a dict with the point, counts and the certificate."""
+    """Run the IPM; returns a dict with the point, counts and the certificate.
+
+    sigma_min (the lower clamp of the adaptive and predictor-corrector rules) defaults to
+    the value the library documents for the rule: 0.03 for "adaptive", 0.01 for
+    "single" and "mehrotra"."""
+    if sigma_min is None:
+        sigma_min = 0.03 if sigma_rule == "adaptive" else 0.01
     w = [np.array(v, dtype=np.float64, copy=True) for v in (w0 or starting_point(prob))]
     sigma = sigma0
     cg_counts, pred_counts, sigmas_used = [], [], []
