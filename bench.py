@@ -737,7 +737,7 @@ def run_batch(args):
     # aggregate algorithmic bytes of all FFT passes of all members, per batch
     nbytes = 0.0
     for w, r in zip(ws, res):
-        for cls, (_, _, by) in _class_model(w.dims, "mixed", r, opt).items():
+        for cls, (_, _, by, *_ops) in _class_model(w.dims, "mixed", r, opt).items():
             if cls.startswith("fft"):
                 nbytes += by
     peak = _peaks().get("hbm_gbs", 6800.0)
@@ -757,7 +757,7 @@ def run_batch(args):
         serial += e0.elapsed_time(e1) / 1e3
     all_bytes = 0.0
     for w, r in zip(ws, res):
-        all_bytes += sum(by for _, _, by in _class_model(w.dims, "mixed", r, opt).values())
+        all_bytes += sum(v[2] for v in _class_model(w.dims, "mixed", r, opt).values())
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         t_cpu, solved, extrap = 0.0, 0, 0
