@@ -10,6 +10,9 @@
 // (condition written by prepare_kernel and pcg_update_kernel).  Every kernel
 // that writes a condition writes it from exactly one thread, on every path,
 // and both loops are bounded by their iteration caps.
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 #include "kernels.h"
 
@@ -745,7 +748,6 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
   __shared__ double scratch[32];
   count_launch(sc);
   if (sc->ipm_done || (sc->incr && sc->exact_now)) return;
-  const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu;
   // ratio test min over {w / (-dw) : dw < 0} in FP32 (operands converted on the
   // integer pipe): alpha_max is then known to ~1e-7 relative, far inside the
@@ -926,6 +928,44 @@ int grid_for(long long n) {
   return (int)g;
 }
 
+// grid_for's count rounded to whole waves of fn's resident blocks (the SMs times the
+// blocks of kThreads threads one SM holds at fn's register use), at most
+// kMaxElementwiseBlocks.  Every block of these grid-stride kernels has the same work,
+// so a last wave that is partly empty idles SMs: at 1216 blocks a kernel with room for
+// 3 (or 6) blocks per SM ran 2.67 (1.33) waves.  The occupancy is looked up once per
+// kernel (a query, allowed during stream capture) and the grid stays fixed for a given
+// kernel and device, which keeps the reductions' block order and results reproducible.
+template <typename... KArgs>
+int waves_for(void (*fn)(KArgs...), long long n) {
+  const int g = grid_for(n);
+  static std::mutex mu;
+  static std::map<const void*, int> per_sm;
+  static int sms = 0;
+  int bps = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (sms == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = -1;
+    }
+    auto it = per_sm.find((const void*)fn);
+    if (it != per_sm.end()) {
+      bps = it->second;
+    } else {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kThreads, 0) != cudaSuccess) bps = 0;
+      per_sm[(const void*)fn] = bps;
+    }
+  }
+  if (bps <= 0 || sms <= 0) return g;
+  const int wave = bps * sms;
+  if (g <= wave) return g;
+  int k = (g + wave / 2) / wave;          // the nearest whole number of waves
+  while (k > 1 && k * wave > kMaxElementwiseBlocks) --k;
+  return k * wave <= kMaxElementwiseBlocks ? k * wave : g;
+}
+
 }  // namespace
 
 cudaError_t k_pack_mask(const uint8_t* mask, uint32_t* words, int Nl, int M, DevScalars* sc, cudaStream_t st) {
@@ -940,45 +980,45 @@ cudaError_t k_cmax(const double* c, long long n2, double lam, int relative, Redu
 }
 cudaError_t k_init_point(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr,
                          cudaStream_t st) {
-  return launch_k(init_point_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, w.Gb, red.partials, red.counter, sc, sigma0, incr);
+  return launch_k(init_point_kernel, dim3(waves_for(init_point_kernel, 2 * lay.H)), dim3(kThreads), 0, st, lay, w.beta, w.z, w.s1, w.s2, w.nu1, w.nu2, w.Gb, red.partials, red.counter, sc, sigma0, incr);
 }
 cudaError_t k_mu(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, int incr, cudaStream_t st) {
-  return launch_k(mu_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, sigma0, incr);
+  return launch_k(mu_kernel, dim3(waves_for(mu_kernel, 2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, sigma0, incr);
 }
 cudaError_t k_certificate(const Layout& lay, const double* beta, const double* Gb, const double* c, Reduce red,
                           DevScalars* sc, double gap_tol, int max_ipm, LoopCtl loop, cudaStream_t st) {
-  return launch_k(certificate_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, beta, Gb, c, red.partials, red.counter, sc, gap_tol, max_ipm, loop);
+  return launch_k(certificate_kernel, dim3(waves_for(certificate_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, beta, Gb, c, red.partials, red.counter, sc, gap_tol, max_ipm, loop);
 }
 cudaError_t k_prepare(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double cg_tol, int cg_relative,
                       LoopCtl loop, double rho, int car, int pc, int keep_rhs, cudaStream_t st) {
-  return launch_k(prepare_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho, car, pc, keep_rhs);
+  return launch_k(prepare_kernel, dim3(waves_for(prepare_kernel, 2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, cg_tol, cg_relative, loop, rho, car, pc, keep_rhs);
 }
 cudaError_t k_predictor(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double rho, double sigma_min,
                         double sigma_max, cudaStream_t st) {
-  return launch_k(predictor_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter,
+  return launch_k(predictor_kernel, dim3(waves_for(predictor_kernel, 2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter,
                   sc, rho, sigma_min, sigma_max);
 }
 cudaError_t k_sigma_coef(const Layout& lay, const double* s1, const double* nu1, const double* s2, const double* nu2,
                          IpmVectors w, DevScalars* sc, double rho, cudaStream_t st) {
-  return launch_k(sigma_coef_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc, sc, rho);
+  return launch_k(sigma_coef_kernel, dim3(waves_for(sigma_coef_kernel, 2 * lay.H)), dim3(kThreads), 0, st, lay, s1, nu1, s2, nu2, w.lam1, w.lam2, w.pa, w.pb, w.pc, sc, rho);
 }
 cudaError_t k_precond(const Layout& lay, IpmVectors w, const double* r, double* z, DevScalars* sc, cudaStream_t st) {
-  return launch_k(precond_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w.pa, w.pb, w.pc, r, z, sc);
+  return launch_k(precond_kernel, dim3(waves_for(precond_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w.pa, w.pb, w.pc, r, z, sc);
 }
 cudaError_t k_pcg_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, int refine_every,
                          LoopCtl loop, cudaStream_t st) {
-  return launch_k(pcg_update_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials, red.counter, sc, max_cg, refine_every, loop);
+  return launch_k(pcg_update_kernel, dim3(waves_for(pcg_update_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials, red.counter, sc, max_cg, refine_every, loop);
 }
 cudaError_t k_refine(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st) {
-  return launch_k(refine_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials, red.counter, sc, loop);
+  return launch_k(refine_kernel, dim3(waves_for(refine_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials, red.counter, sc, loop);
 }
 cudaError_t k_cr_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, LoopCtl loop, cudaStream_t st) {
-  return launch_k(cr_update_a_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+  return launch_k(cr_update_a_kernel, dim3(waves_for(cr_update_a_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
                   red.counter, sc, loop);
 }
 cudaError_t k_cr_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
                           cudaStream_t st) {
-  return launch_k(cr_update_b_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+  return launch_k(cr_update_b_kernel, dim3(waves_for(cr_update_b_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
                   red.counter, sc, max_cg, loop);
 }
 cudaError_t k_car_start(const Layout& lay, IpmVectors w, DevScalars* sc, cudaStream_t st) {
@@ -986,21 +1026,21 @@ cudaError_t k_car_start(const Layout& lay, IpmVectors w, DevScalars* sc, cudaStr
 }
 cudaError_t k_car_update_a(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double restart_eps, LoopCtl loop,
                            cudaStream_t st) {
-  return launch_k(car_update_a_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+  return launch_k(car_update_a_kernel, dim3(waves_for(car_update_a_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
                   red.counter, sc, restart_eps, loop);
 }
 cudaError_t k_car_update_b(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, int max_cg, LoopCtl loop,
                            cudaStream_t st) {
-  return launch_k(car_update_b_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
+  return launch_k(car_update_b_kernel, dim3(waves_for(car_update_b_kernel, 2 * lay.H)), dim3(kThreads), 0, st, 2 * lay.H, w, red.partials,
                   red.counter, sc, max_cg, loop);
 }
 cudaError_t k_step_length(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double tau, int pc,
                           cudaStream_t st) {
-  return launch_k(step_length_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, tau, pc);
+  return launch_k(step_length_kernel, dim3(waves_for(step_length_kernel, 2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, tau, pc);
 }
 cudaError_t k_step_update(const Layout& lay, IpmVectors w, Reduce red, DevScalars* sc, double sigma0, double sigma_slow,
                           int sigma_rule, double sigma_min, cudaStream_t st) {
-  return launch_k(step_update_kernel, dim3(grid_for(2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, sigma0, sigma_slow, sigma_rule, sigma_min);
+  return launch_k(step_update_kernel, dim3(waves_for(step_update_kernel, 2 * lay.H)), dim3(kThreads), 0, st, lay, w, red.partials, red.counter, sc, sigma0, sigma_slow, sigma_rule, sigma_min);
 }
 cudaError_t k_unpack(const Layout& lay, const double* beta, double* vh, DevScalars* sc, cudaStream_t st) {
   return launch_k(unpack_kernel, dim3(grid_for(lay.H)), dim3(kThreads), 0, st, lay, beta, vh, sc);
