@@ -70,7 +70,7 @@ typedef enum {
   IPM_NUMERICAL = 6,        /* non-finite value or loss of positive definiteness */
   IPM_TIMEOUT = 7           /* a bounded device-side wait expired: the kernel gave up,
                                released what it held and returned; the context stays
-                               usable (see ws_test_conv_stall)                      */
+                               usable (see ws_test_conv_stall, ipm_test_stage_stall) */
 } ipm_status;
 
 typedef enum { IPM_FP64 = 0, IPM_MIXED = 1 } ipm_precision;
