@@ -6,7 +6,7 @@ seeded generator, solved by the library's own IPM (the targets are its
 solutions), and the network is trained by the library's forward/backward
 kernels (``ws_train_step``).  This module only orchestrates.
 
-    python -m paper_2502_04217_gb300.warmstart --side 128 --count 2000 --epochs 3 \
+    python -m paper_2502_04217_gb300.warmstart --side 128 --count 2000 --epochs 8 \
         --out paper_2502_04217_gb300/weights/warmstart.f32
 """
 
@@ -120,7 +120,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--side", type=int, default=128)
     ap.add_argument("--count", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args()
