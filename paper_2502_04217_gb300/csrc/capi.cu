@@ -56,6 +56,8 @@ struct PassCfg {
 struct PassSet {
   PassCfg row_inv, row_fwd, col_inv, col_fwd, mid;
   PassCfg row_inv_beta;     // first row pass reading a plain beta-layout vector (G and K products, residuals)
+  PassCfg row_fwd_k;        // last row pass of a product with K outside PCG (kkt_apply, residual replacement):
+                            // tuned without PCG's p^T q reduction and (G p)_beta store
 };
 
 // Kernel classes of the per-launch timing (ipm_profile_get): 0 row, 1 column and
@@ -420,7 +422,9 @@ void tune_cache_append(const TuneKey& k, const TuneVal& v) {
 // inverse (first) one.  Row passes are timed in the form the PCG loop runs them
 // (first: p = z + beta p and the beta map; last: the K epilogue with the p^T q
 // reduction and the (G p)_beta store), on operands filled with a non-zero pattern by
-// the caller; column and middle passes on the work buffer alone.
+// the caller; column and middle passes on the work buffer alone.  `beta_form`: the
+// first pass reading a plain beta-layout vector, or the last pass with the K epilogue
+// alone (the products with K outside PCG).
 ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long long npen, bool fp32,
                      bool last = false, bool beta_form = false) {
   c.kind = kind;
@@ -532,11 +536,13 @@ ipm_status tune_tile(sdft_ipm* h, PassCfg& c, int kind, int L, int rows, long lo
       a.lam2 = h->w.lam2;
       a.kstage = t.kstage;
       a.kst_off = t.kst_off;
-      // the form PCG runs: with the p^T q grid reduction and, when G beta is carried, (G p)_beta
-      a.pcg_mode = 1;
-      a.partials = h->d_partials;
-      a.counter = h->d_counter;
-      a.gp_out = incremental_gb(h) ? h->w.Gp : nullptr;
+      if (!beta_form) {
+        // the form PCG runs: with the p^T q grid reduction and, when G beta is carried, (G p)_beta
+        a.pcg_mode = 1;
+        a.partials = h->d_partials;
+        a.counter = h->d_counter;
+        a.gp_out = incremental_gb(h) ? h->w.Gp : nullptr;
+      }
     }
     trials.push_back({t, a, a.kstage == 2 ? t.smem_staged : t.smem, inv, 1e30f});
   }
@@ -598,19 +604,23 @@ ipm_status plan_passes(sdft_ipm* h, PassSet& ps, bool fp32) {
     PassCfg c;
     if ((s = make_tables(h, Lr, &t64, &t32)) != IPM_OK) return s;
     c.tw = fp32 ? t32 : t64;
-    PassCfg f = c, b = c;
+    PassCfg f = c, b = c, k = c;
     if ((s = tune_tile(h, c, 0, Lr, Lr, nrows, fp32)) != IPM_OK) return s;
     if ((s = tune_tile(h, f, 0, Lr, Lr, nrows, fp32, true)) != IPM_OK) return s;
-    if (h->opt.tile_kstage > 0) {
-      PassCfg t = f;
-      if (stage_cfg(t, h->opt.tile_kstage - 1)) f = t;
-      else stage_cfg(f, 0);
-    } else if (!h->opt.autotune) {
-      stage_cfg(f, 0);
+    if ((s = tune_tile(h, k, 0, Lr, Lr, nrows, fp32, true, true)) != IPM_OK) return s;
+    for (PassCfg* q : {&f, &k}) {
+      if (h->opt.tile_kstage > 0) {
+        PassCfg t = *q;
+        if (stage_cfg(t, h->opt.tile_kstage - 1)) *q = t;
+        else stage_cfg(*q, 0);
+      } else if (!h->opt.autotune) {
+        stage_cfg(*q, 0);
+      }
     }
     if ((s = tune_tile(h, b, 0, Lr, Lr, nrows, fp32, false, true)) != IPM_OK) return s;
     ps.row_inv = c;
     ps.row_fwd = f;
+    ps.row_fwd_k = k;
     ps.row_inv_beta = b;
   }
   if (L.d == 3) {
@@ -749,9 +759,10 @@ ipm_status run_g(sdft_ipm* h, bool fp32, const GSpec& g) {
     fill(a, false, false);
     if ((s = launch(h, ps.col_fwd, false, fp32, a)) != IPM_OK) return s;
   }
-  PassArgs a = base_args(h, ps.row_fwd);
+  const PassCfg& lastc = (g.mapout == MAPOUT_K && !g.pcg && !g.cr) ? ps.row_fwd_k : ps.row_fwd;
+  PassArgs a = base_args(h, lastc);
   fill(a, false, true);
-  return launch(h, ps.row_fwd, false, fp32, a);
+  return launch(h, lastc, false, fp32, a);
 }
 
 // c = M_perp^T b = B DFT(b_hat) / sqrt(n) scaling, in FP64 (Eq. (xi)).
@@ -961,7 +972,7 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   if ((s = plan_passes(h, h->pass64, false)) != IPM_OK) return cleanup_fail(s);
   if ((s = plan_passes(h, h->pass32, true)) != IPM_OK) return cleanup_fail(s);
   for (const PassSet* ps : {&h->pass64, &h->pass32})
-    for (const PassCfg* c : {&ps->row_fwd, &ps->mid})
+    for (const PassCfg* c : {&ps->row_fwd, &ps->row_fwd_k, &ps->mid})
       if ((size_t)c->grid.x * c->grid.y * c->grid.z > cap) return cleanup_fail(fail_arg(h, "reduction partials too small"));
   // vectors start at 0 (ghosts stay 0 from here on)
   for (double** p : vec2) CKC(cudaMemsetAsync(*p, 0, v2, h->st));
@@ -1330,7 +1341,7 @@ ipm_status kkt_apply(sdft_ipm* h, const double* p, double* q) {
   h->stall_log2 = 0;
   const bool fp32 = h->opt.precision == IPM_MIXED;
   // a last pass that stages its operands on an mbarrier reports an expired wait
-  const bool staged = h->lay.d >= 2 && (fp32 ? h->pass32 : h->pass64).row_fwd.kstage == 2;
+  const bool staged = h->lay.d >= 2 && (fp32 ? h->pass32 : h->pass64).row_fwd_k.kstage == 2;
   int* flag = &h->d_sc->wait_expired;
   if (staged) CK(cudaMemsetAsync(flag, 0, sizeof(int), h->st));
   PdlScope pdl(h->opt.pdl != 0);
@@ -1349,7 +1360,7 @@ ipm_status kkt_apply(sdft_ipm* h, const double* p, double* q) {
 ipm_status ipm_test_stage_stall(sdft_ipm* h, int wait_log2) {
   if (!h) return fail_arg(nullptr, "handle is NULL");
   if (wait_log2 < 8 || wait_log2 > 24) return fail_arg(h, "wait_log2 must be in 8..24");
-  const PassCfg& f = (h->opt.precision == IPM_MIXED ? h->pass32 : h->pass64).row_fwd;
+  const PassCfg& f = (h->opt.precision == IPM_MIXED ? h->pass32 : h->pass64).row_fwd_k;
   if (h->lay.d < 2 || f.kstage != 2) return fail_arg(h, "the last pass does not stage its operands in shared memory");
   h->stall_log2 = wait_log2;
   return IPM_OK;
@@ -1479,6 +1490,7 @@ int ipm_describe(const sdft_ipm* h, char* buf, int len) {
     const std::string pre = t ? "fp32_" : "fp64_";
     one((pre + "middle").c_str(), ps.mid);
     if (h->lay.d >= 2) one((pre + "row").c_str(), ps.row_fwd);
+    if (h->lay.d >= 2) one((pre + "row_k").c_str(), ps.row_fwd_k);
     if (h->lay.d >= 2) one((pre + "row_first").c_str(), ps.row_inv);
     if (h->lay.d >= 2) one((pre + "row_first_beta").c_str(), ps.row_inv_beta);
     if (h->lay.d == 3) one((pre + "col").c_str(), ps.col_fwd);

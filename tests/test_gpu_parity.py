@@ -208,8 +208,10 @@ def test_staged_k_operands_give_identical_products(dims, tile, precision):
     for ks in (1, 2, 3):
         h = _handle(w, precision, tile_kstage=ks, **tile)
         try:
-            row = binding.ipm_describe(h)["fp32_row" if precision == binding.IPM_MIXED else "fp64_row"]
-            assert row["kstage"] == ks - 1, row
+            desc = binding.ipm_describe(h)
+            pre = "fp32_" if precision == binding.IPM_MIXED else "fp64_"
+            for name in ("row", "row_k"):       # the PCG product's last pass and kkt_apply's
+                assert desc[pre + name]["kstage"] == ks - 1, (name, desc[pre + name])
             binding.ipm_set_sigma(h, *[oracle_to_lib(h, v, dims) for v in (s1, nu1, s2, nu2)])
             p = torch.cat([oracle_to_lib(h, pb, dims), oracle_to_lib(h, pz, dims)])
             q = torch.full_like(p, float("nan"))
