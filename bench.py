@@ -350,8 +350,9 @@ def _class_model(dims, prec, res, opt):
     else:
         out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 128 * H + rhs + gx), it * 2 * H * FP64_OPS_PREPARE)
     # with the predictor-corrector step_length also reads the two terms and writes the direction
-    # (+32 + 64 B); step_update reads the direction instead of 1/s and the terms (same count)
-    out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (32 * H if incr else 0) + (96 * H if pc else 0)))
+    # (+32 + 64 B); step_update reads the direction instead of 1/s and the terms (same count);
+    # with G beta carried step_update also reads c (16 B) for the certificate's sums
+    out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (48 * H if incr else 0) + (96 * H if pc else 0)))
     return out
 
 
@@ -363,7 +364,14 @@ def _rooflines(dims, prec, res, breakdown, steps, opt):
     peak = _peaks().get("hbm_gbs", 6800.0)
     cert = breakdown.get("certificate", {"launches": 0})
     Hn = _sizes(dims)[0]
-    model["certificate"] = (cert["launches"] // max(steps, 1), 0.0, (cert["launches"] // max(steps, 1)) * 48 * Hn)
+    # a certificate reads beta, G beta and c (48 B per slot) at the first point and after each
+    # exact G beta product; with G beta carried it otherwise takes step_update's sums
+    n_cert = cert["launches"] // max(steps, 1)
+    incr = not opt.exact_residual and opt.krylov == 0 and opt.refine_every == 0
+    if incr:
+        exact = res["kkt_products"] - res["cg_iters_total"] - res.get("refinements", 0)
+        n_cert = min(n_cert, exact + (0 if res.get("warm_start") else 1))
+    model["certificate"] = (n_cert, 0.0, n_cert * 48 * Hn)
     classes = {}
     for nm, (work, flops, nbytes, *ops) in model.items():
         b = breakdown.get(nm)
@@ -959,7 +967,7 @@ def run_warm512(args):
     # ---- per-launch CUDA events of one warm solve: classes and the dominant one --------
     binding.ipm_profile_enable(h32, True)
     binding.ws_predict(net, h32, wsm.MU_SCALE)
-    rp = binding.ipm_solve(h32)
+    rp = dict(binding.ipm_solve(h32), warm_start=True)
     breakdown = _breakdown(binding, h32)
     binding.ipm_profile_enable(h32, False)
     roofline = _roofline_line(w.dims, "mixed", rp, breakdown, 1, "warm512", o32)

@@ -959,10 +959,11 @@ ipm_status ipm_create(sdft_ipm** out, int ndim, const int64_t* dims, const uint8
   // non-zero values (every byte 0x3F) until the vectors are cleared below
   for (double* p : {h->w.p, h->w.zv, h->w.lam1, h->w.lam2})
     CKC(cudaMemsetAsync(p, 0x3F, (p == h->w.lam1 || p == h->w.lam2) ? v2 : v4, h->st));
-  // partials of the grid reductions: 4 values per elementwise block, 1 per block of an FFT
-  // pass that reduces (the last pass of a PCG product, p^T q), whose tiles hold at least
-  // one pencil: allocated before the tuner, which times that pass with its reduction
-  size_t cap = 4 * (size_t)kMaxElementwiseBlocks;
+  // partials of the grid reductions: up to 5 values per elementwise block (step_update:
+  // mu and the certificate's four sums), 1 per block of an FFT pass that reduces (the
+  // last pass of a PCG product, p^T q), whose tiles hold at least one pencil: allocated
+  // before the tuner, which times that pass with its reduction
+  size_t cap = 5 * (size_t)kMaxElementwiseBlocks;
   if (L.d >= 2) cap = std::max(cap, (size_t)(L.H / ((L.d == 3) ? L.N1 : L.N0)));
   cap = std::max(cap, (size_t)L.M);
   h->partial_cap = cap;

@@ -59,6 +59,10 @@ struct DevScalars {
   int confirming;    // (incr) this iteration's exact product confirms a stop test passed on the
                      // carried G beta; if it fails, G beta is recomputed every iteration from then on
   int wait_expired;  // a bounded device-side wait gave up (staged K operands): the solve reports IPM_TIMEOUT
+  int cert_ready;    // cert_sum holds the certificate's sums at the current point (left by step_update;
+                     // not after an exact G beta product, which changes G beta)
+  int pad2;
+  double cert_sum[4];  // c^T beta, beta^T G beta, ||beta||_1, ||c - G beta||_inf
   unsigned long long launches;   // kernels launched by the library (every kernel adds 1)
 };
 

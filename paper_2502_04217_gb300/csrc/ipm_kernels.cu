@@ -24,6 +24,11 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ bool first_thread() { return threadIdx.x == 0 && blockIdx.x == 0; }
 
+// |x| as the bit pattern of a non-negative double (orders like the numbers)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
 __device__ __forceinline__ void set_cond(const LoopCtl& c, unsigned v) {
   if (c.use) cudaGraphSetConditional(c.handle, v);
 }
@@ -98,6 +103,7 @@ __device__ __forceinline__ void reset_control(DevScalars* sc, double mu, double 
   sc->refine_exit = 0;
   sc->refinements = 0;
   sc->wait_expired = 0;
+  sc->cert_ready = 0;
 }
 
 // Start point: beta = 0, z = s1 = s2 = zeta, nu1 = nu2 = lambda/2 (ghosts 0); mu; control reset
@@ -147,6 +153,44 @@ __global__ void __launch_bounds__(kThreads) mu_kernel(Layout lay, IpmVectors w, 
 //   D = s b^T theta - s^2 ||theta||^2 / 2 with s = min(1, lambda / ||M_perp^T theta||_inf).
 // Stop when the relative gap (P - D) / max(1, |P|) <= gap_tol, at the iteration cap,
 // or on a non-finite value; the IPM loop condition is !ipm_done.
+// The objective, the scaled dual point and the stop decision from the four sums
+// v = (c^T beta, beta^T G beta, ||beta||_1, ||c - G beta||_inf); one thread.
+__device__ void certify(DevScalars* sc, const double (&v)[4], double gap_tol, int max_ipm, LoopCtl ipm_loop) {
+  const double lam = sc->lambda;
+  const double th2 = fmax(sc->yy - 2.0 * v[0] + v[1], 0.0);
+  const double bth = sc->yy - v[0];
+  const double P = 0.5 * th2 + lam * v[2];
+  const double s = (v[3] <= lam) ? 1.0 : lam / v[3];
+  const double D = s * bth - 0.5 * s * s * th2;
+  const double gap = (P - D) / fmax(1.0, fabs(P));
+  sc->theta2 = th2;
+  sc->corr = v[3];
+  sc->l1 = v[2];
+  sc->primal = P;
+  sc->dual = D;
+  sc->gap = gap;
+  // incremental G beta: a stop test passed on the updated G beta is confirmed
+  // by an exact FP64 product first (this iteration takes no step).  A confirmation
+  // that fails shows the carried value is not accurate enough at this gap any more:
+  // from then on G beta is recomputed by an FP64 product every iteration (incr = 0,
+  // exact_now = 1: the residual product runs and the iteration steps as usual).
+  const bool exact = !sc->incr || sc->exact_now;           // an FP64 product formed G beta
+  const bool confirm = sc->confirming != 0;
+  sc->confirming = 0;
+  if (exact) sc->gb_products += 1;
+  if (!isfinite(gap) || !isfinite(sc->mu)) { sc->ipm_done = 1; sc->ipm_status = 6; }
+  else if (gap <= gap_tol && exact) { sc->ipm_done = 1; sc->ipm_status = 0; }
+  else if (gap <= gap_tol) { sc->exact_now = 1; sc->confirming = 1; }
+  else if (sc->ipm_it >= max_ipm) { sc->ipm_done = 1; sc->ipm_status = 4; }
+  else if (confirm) { sc->incr = 0; sc->exact_now = 1; }
+  else sc->exact_now = sc->incr ? 0 : 1;
+  set_cond(ipm_loop, sc->ipm_done ? 0u : 1u);
+}
+
+// Certificate and stop test (once per IPM iteration).  When step_update left the four
+// sums at this point and G beta is the carried one (no exact product since), one
+// thread takes the decision from them; otherwise (the first point, after an exact FP64
+// product of G beta) the kernel forms the sums in a pass over beta, G beta and c.
 __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, const double* __restrict__ beta,
                                                                const double* __restrict__ Gb, const double* __restrict__ c,
                                                                double* partials, unsigned* counter, DevScalars* sc,
@@ -154,6 +198,23 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
   pdl_wait();
   __shared__ double scratch[4 * 32];
   count_launch(sc);
+  const bool exact = !sc->incr || sc->exact_now;
+  if (sc->cert_ready && !exact) {
+    // the decision rewrites the flags just read, so it waits until every block has
+    // read them: each block arrives on the grid counter and the last one decides
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      const double v[4] = {sc->cert_sum[0], sc->cert_sum[1], sc->cert_sum[2], sc->cert_sum[3]};
+      sc->cert_ready = 0;
+      certify(sc, v, gap_tol, max_ipm, ipm_loop);
+      *counter = 0u;
+    }
+    return;
+  }
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   const int ops[4] = {RED_SUM, RED_SUM, RED_SUM, RED_MAX};
   // one half-spectrum slot (two coordinates, 16-byte loads) per step
@@ -163,7 +224,6 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
   // ||c - G beta||_inf on the integer pipe: the bit patterns of non-negative doubles
   // order like the numbers (a non-finite G beta also makes the sum v[1] non-finite)
   unsigned long long m3 = 0ull;
-  auto abs_bits = [](double x) { return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull; };
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < (n2 >> 1); j += (long long)gridDim.x * blockDim.x) {
     const double2 b = b2[j], g = g2[j], ci = c2[j];
     v[0] = fma(ci.y, b.y, fma(ci.x, b.x, v[0]));     // FMAs into the running sums: the FP64
@@ -173,35 +233,8 @@ __global__ void __launch_bounds__(kThreads) certificate_kernel(long long n2, con
   }
   v[3] = __longlong_as_double((long long)m3);
   if (grid_reduce<4>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
-    const double lam = sc->lambda;
-    const double th2 = fmax(sc->yy - 2.0 * v[0] + v[1], 0.0);
-    const double bth = sc->yy - v[0];
-    const double P = 0.5 * th2 + lam * v[2];
-    const double s = (v[3] <= lam) ? 1.0 : lam / v[3];
-    const double D = s * bth - 0.5 * s * s * th2;
-    const double gap = (P - D) / fmax(1.0, fabs(P));
-    sc->theta2 = th2;
-    sc->corr = v[3];
-    sc->l1 = v[2];
-    sc->primal = P;
-    sc->dual = D;
-    sc->gap = gap;
-    // incremental G beta: a stop test passed on the updated G beta is confirmed
-    // by an exact FP64 product first (this iteration takes no step).  A confirmation
-    // that fails shows the carried value is not accurate enough at this gap any more:
-    // from then on G beta is recomputed by an FP64 product every iteration (incr = 0,
-    // exact_now = 1: the residual product runs and the iteration steps as usual).
-    const bool exact = !sc->incr || sc->exact_now;           // an FP64 product formed G beta
-    const bool confirm = sc->confirming != 0;
-    sc->confirming = 0;
-    if (exact) sc->gb_products += 1;
-    if (!isfinite(gap) || !isfinite(sc->mu)) { sc->ipm_done = 1; sc->ipm_status = 6; }
-    else if (gap <= gap_tol && exact) { sc->ipm_done = 1; sc->ipm_status = 0; }
-    else if (gap <= gap_tol) { sc->exact_now = 1; sc->confirming = 1; }
-    else if (sc->ipm_it >= max_ipm) { sc->ipm_done = 1; sc->ipm_status = 4; }
-    else if (confirm) { sc->incr = 0; sc->exact_now = 1; }
-    else sc->exact_now = sc->incr ? 0 : 1;
-    set_cond(ipm_loop, sc->ipm_done ? 0u : 1u);
+    sc->cert_ready = 0;
+    certify(sc, v, gap_tol, max_ipm, ipm_loop);
   }
 }
 
@@ -796,18 +829,22 @@ __global__ void __launch_bounds__(kThreads) step_length_kernel(Layout lay, IpmVe
 }
 
 // Take the step, form the new duality measure mu, count the iteration
-__global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
+__global__ void __launch_bounds__(kThreads, 4) step_update_kernel(Layout lay, IpmVectors w, double* partials, unsigned* counter,
                                                                DevScalars* sc, double sigma0, double sigma_slow,
                                                                int sigma_rule, double sigma_min) {
   pdl_wait();
-  __shared__ double scratch[32];
+  __shared__ double scratch[5 * 32];
   count_launch(sc);
   if (sc->ipm_done || (sc->incr && sc->exact_now)) return;
   const long long n2 = 2 * lay.H;
   const double smu = sc->sigma * sc->mu, alpha = sc->alpha;
   const bool incr = sc->incr;
-  double v[1] = {0.0};
-  const int ops[1] = {RED_SUM};
+  // mu's sum, and with G beta carried the certificate's sums at the new point (c^T beta,
+  // beta^T G beta, ||beta||_1, ||c - G beta||_inf; ghost coordinates are 0 in beta,
+  // G beta and c), so that the next stop test needs no pass of its own
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int ops[5] = {RED_SUM, RED_SUM, RED_SUM, RED_SUM, RED_MAX};
+  unsigned long long m3 = 0ull;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
     if (is_ghost(lay, i)) continue;
     Dir d;
@@ -819,15 +856,26 @@ __global__ void __launch_bounds__(kThreads) step_update_kernel(Layout lay, IpmVe
     } else {
       d = direction(w, i, n2, smu, 0);
     }
-    w.beta[i] += alpha * w.x[i];
-    if (incr) w.Gb[i] += alpha * w.Gx[i];        // G beta follows beta (G is linear)
+    const double b = w.beta[i] + alpha * w.x[i];
+    w.beta[i] = b;
+    if (incr) {                          // G beta follows beta (G is linear)
+      const double g = w.Gb[i] + alpha * w.Gx[i], ci = w.c[i];
+      w.Gb[i] = g;
+      v[1] = fma(ci, b, v[1]);
+      v[2] = fma(b, g, v[2]);
+      v[3] += fabs(b);
+      m3 = max(m3, abs_bits(ci - g));
+    }
     w.z[i] += alpha * w.x[n2 + i];
     const double s1 = w.s1[i] + alpha * d.ds1, s2 = w.s2[i] + alpha * d.ds2;
     const double n1 = w.nu1[i] + alpha * d.dn1, n2_ = w.nu2[i] + alpha * d.dn2;
     w.s1[i] = s1; w.s2[i] = s2; w.nu1[i] = n1; w.nu2[i] = n2_;
     v[0] += n1 * s1 + n2_ * s2;
   }
-  if (grid_reduce<1>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+  v[4] = __longlong_as_double((long long)m3);
+  if (grid_reduce<5>(v, ops, partials, counter, scratch) && threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) sc->cert_sum[k] = v[k + 1];
+    sc->cert_ready = incr ? 1 : 0;
     sc->mu = v[0] / (2.0 * (double)lay.n);
     if (sigma_rule == 1 && sc->cg_status != 1) {
       // adaptive centring: (1 - alpha)^3 stands in for Mehrotra's (mu_aff / mu)^3;

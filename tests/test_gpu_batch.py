@@ -85,6 +85,33 @@ def test_batch_with_odd_members_equals_standalone_solves(precision):
         assert np.array_equal(vb, v)
 
 
+def test_batch_of_multi_wave_members_equals_standalone_solves():
+    """Members of 32^3 to 128^3 (grids of many blocks, several waves) in mixed precision
+    with G beta carried through PCG: concurrent members delay one another's blocks, so a
+    kernel whose blocks disagree on a flag that the same launch rewrites shows up here as
+    a trajectory that differs from the standalone solve."""
+    from paper_2502_04217_gb300.synth import batch_workloads
+    picked = {}
+    for w in batch_workloads(48):
+        picked.setdefault(w.dims[0], w)
+    ws = [picked[s] for s in sorted(picked)]
+    opt = binding.default_options(precision=binding.IPM_MIXED, lambda_relative=1, gap_tol=1e-6)
+    assert opt.exact_residual == 0
+    b = binding.ipm_create_batch([(w.dims, w.mask, w.y, w.lam_rel) for w in ws], opt)
+    try:
+        res_b = binding.ipm_solve_batch(b)
+    finally:
+        binding.ipm_destroy_batch(b)
+    for w, rb in zip(ws, res_b):
+        h = binding.ipm_create(w.dims, w.mask, w.y, w.lam_rel, opt)
+        try:
+            r = binding.ipm_solve(h)
+        finally:
+            binding.ipm_destroy(h)
+        assert rb["status"] == binding.IPM_OK and rb["rel_gap"] <= 1e-6
+        assert (rb["ipm_iters"], rb["cg_iters_total"], rb["primal"]) == (r["ipm_iters"], r["cg_iters_total"], r["primal"])
+
+
 def test_batch_members_match_oracle():
     ws = _problems()[:4]
     probs = []
