@@ -301,7 +301,9 @@ def _class_model(dims, prec, res, opt):
       certificate: reads beta, G beta, c (48 B);
       G beta carried (exact_residual 0, CG, no refinement): the last pass of a PCG
         product also writes (G p)_beta (16 B), pcg_update updates G x (48 B), prepare
-        clears G x (16 B), step_update updates G beta (32 B).
+        clears G x (16 B), step_update updates G beta (reads G beta and G x, writes G beta:
+        48 B) and reads c (16 B) for the certificate's four sums, so that the certificate
+        reads beta, G beta and c only at the first point and after an exact product.
     FLOPs: 5 L log2 L per complex transform of length L, 2.5 L log2 L per real one.
     FP64 pipe operations of the Newton-system class: FP64_OPS_* per coordinate (2H).
     Returns {class: (working launches, flops, bytes[, FP64 pipe operations])} for one solve.
@@ -351,8 +353,8 @@ def _class_model(dims, prec, res, opt):
         out["prepare"] = (it, 0.0, it * (128 * H + 112 * H + 128 * H + rhs + gx), it * 2 * H * FP64_OPS_PREPARE)
     # with the predictor-corrector step_length also reads the two terms and writes the direction
     # (+32 + 64 B); step_update reads the direction instead of 1/s and the terms (same count);
-    # with G beta carried step_update also reads c (16 B) for the certificate's sums
-    out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (48 * H if incr else 0) + (96 * H if pc else 0)))
+    # with G beta carried step_update also updates G beta (48 B) and reads c (16 B)
+    out["step"] = (2 * it, 0.0, it * (160 * H + 160 * H + 96 * H + (64 * H if incr else 0) + (96 * H if pc else 0)))
     return out
 
 

@@ -37,8 +37,25 @@ def test_class_model_bytes_and_operations():
     assert ops == 6 * 2 * H * (bench.FP64_OPS_PREDICTOR + bench.FP64_OPS_PREPARE_PC)
     # pcg_update: 272 bytes per slot, 48 more for the carried G x
     assert m["pcg_update"] == (20, 0.0, 20 * (272 * H + 48 * H))
+    # step_length + step_update with the predictor-corrector's direction, G beta carried
+    # (G beta and G x read, G beta written) and c read for the certificate's sums
+    assert m["step"] == (12, 0.0, 6 * ((160 + 160 + 96) * H + (48 + 16) * H + 96 * H))
     # every other class is (work, flops, bytes)
     assert all(len(v) == 3 for k, v in m.items() if k != "prepare")
+
+
+def test_certificate_counts_only_its_reducing_launches():
+    """With G beta carried the certificate reads beta, G beta and c at the first point and
+    after each exact product only; its other launches decide from step_update's sums."""
+    dims = (64, 64, 64)
+    H = 64 * 64 * 33
+    res = _res(cg=20, exact=2, it=6)
+    r = bench._roofline_line(dims, "mixed", res, _breakdown(10.0, 2.0), 1, "none", _opt())
+    assert r["classes"]["certificate"]["algorithmic_bytes"] == 3 * 48 * H
+    r = bench._roofline_line(dims, "mixed", dict(res, warm_start=True), _breakdown(10.0, 2.0), 1, "none", _opt())
+    assert r["classes"]["certificate"]["algorithmic_bytes"] == 2 * 48 * H
+    r = bench._roofline_line(dims, "mixed", res, _breakdown(10.0, 2.0), 1, "none", _opt(exact_residual=1))
+    assert r["classes"]["certificate"]["algorithmic_bytes"] == 8 * 48 * H
 
 
 def test_prepare_without_predictor_counts_its_own_operations():
